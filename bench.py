@@ -1,0 +1,415 @@
+"""Benchmark: exactly k-sparse sFFT transforms/s at n = 2^22, k = 64 on GB300 (one JSON line).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--batch 256]
+
+A step is one pass of the whole path (every round of Algorithm 1: gather, window, fold, bin FFT,
+subtraction, decode, merge) over a batch of 256 distinct synthetic signals (n = 2^22 complex64, 8 GiB,
+resident in HBM: larger than L2, so no flush is needed between steps).  ``value`` is transforms/s of
+the whole job (all ranks), timed with CUDA events on the launching stream between a barrier and a
+synchronisation on both sides, max over ranks.  ``e2e`` is the same metric through the host entry
+point (pinned host signals copied in, results copied out, every step).  ``--impl reference`` times the
+FP64 CPU oracle on the host cores instead (the only other place this script runs ``oracle/``).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_LOG2 = 22
+K = 64
+DELTA = 1e-6
+SEED = 0x5EED2000
+WORKLOAD = "exactly 64-sparse spectrum, n=2^22 complex64 time signal, unit magnitudes, uniform phases, B=4k, delta=1e-6"
+METRIC = "sFFT transforms/s at n=2^22,k=64 vs cuFFT & plain GPU sFFT; p50/p99 latency"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def algorithmic_bytes_per_transform(plan):
+    """Distinct samples one transform gathers (2T+1 taps plus the largest ladder shift, per round),
+    each costing one 32-byte HBM sector (sigma-strided addresses share no sector)."""
+    samples = 0
+    for t in range(plan.rounds):
+        info = plan.round_info(t)
+        samples += 2 * info["T"] + 1 + max(info["shifts"])
+    return samples * 32, samples
+
+
+# ------------------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on the host cores
+# ------------------------------------------------------------------------------------------------
+def _oracle_worker(args):
+    inst, n_log2, k = args
+    import oracle
+    from paper_1201_2501_gb300 import workloads
+    from tests.common import exact_fields, oracle_params
+
+    n = 1 << n_log2
+    P = oracle_params(exact_fields(n, k, delta=DELTA))
+    sig = workloads.exact_sparse(n, k, workloads.seed_for(2, inst), dtype=np.complex64)
+    x = sig.x.astype(np.complex128)
+    t0 = time.perf_counter()
+    zi, zv, flag = oracle.sfft_exact(P, x, SEED, inst)
+    dt = time.perf_counter() - t0
+    return dt, bool(np.array_equal(zi.astype(np.int64), sig.support))
+
+
+def oracle_pool(cores):
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(cores)
+
+
+def oracle_rate(pool, cores, per_core, offset=0):
+    """Transforms/s of the oracle with `cores` processes each running `per_core` transforms."""
+    jobs = [(offset + i, N_LOG2, K) for i in range(cores * per_core)]
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_worker, jobs, chunksize=per_core)
+    wall = time.perf_counter() - t0
+    busy = sum(r[0] for r in res)
+    return len(jobs) / wall, len(jobs), wall, busy, sum(r[1] for r in res)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    pool = oracle_pool(cores)
+    for w in range(args.warmup):
+        oracle_rate(pool, cores, 1, offset=10_000 + w * cores)
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(args.steps):
+        r, cnt, wall, busy, ok = oracle_rate(pool, cores, 1, offset=s * cores)
+        done += cnt
+    el = time.perf_counter() - t0
+    pool.close()
+    value = done / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + "; FP64 CPU oracle, one transform per core per step",
+                   "n": 1 << N_LOG2, "k": K, "transforms_per_step": cores},
+        "cpu_baseline": {"value": value, "unit": "transforms/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} transforms per step (one per core), {args.steps} steps"},
+        "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    # the oracle pool for the CPU baseline is started before the first GPU call (spawn)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    pool = None
+    cores = os.cpu_count() or 1
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        pool = oracle_pool(cores)
+
+    rank, world, local = dist_setup(args.gpus)
+    from paper_1201_2501_gb300 import build, sfft, workloads
+
+    if rank == 0 or world > 1:
+        build.build()
+    barrier(world)
+    n, k, batch = 1 << N_LOG2, K, args.batch
+    params = sfft.sfft_params_default(n, k, sfft.SFFT_EXACT, delta=DELTA)
+    plan = sfft.Plan(params, batch)
+    cap = params.z_cap
+    seeds = [workloads.seed_for(2, rank * batch + i) for i in range(batch)]
+    x, sup, val = workloads.exact_sparse_batch_device(n, k, seeds, "cuda")
+    stream = torch.cuda.current_stream()
+    outs = (torch.empty((batch, cap), dtype=torch.int32, device="cuda"),
+            torch.empty((batch, cap, 2), dtype=torch.float64, device="cuda"),
+            torch.empty((batch,), dtype=torch.int32, device="cuda"),
+            torch.empty((batch,), dtype=torch.int32, device="cuda"))
+
+    def step():
+        sfft.sfft_execute(plan, x, SEED, cap, outs, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    # accuracy of the timed configuration: recovered support vs planted support
+    cnt = outs[2].cpu().numpy()
+    idx = outs[0].cpu().numpy()
+    exact = sum(np.array_equal(np.sort(idx[r, :cnt[r]].astype(np.int64)), sup[r]) for r in range(batch))
+
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world)
+    value = batch * world * args.steps / (ms_max / 1000.0)
+    ms_step = ms_max / args.steps
+    bytes_tr, samples_tr = algorithmic_bytes_per_transform(plan)
+    hbm_peak, peak_kind = _peaks()
+    achieved = bytes_tr * batch / (ms_step / 1000.0) / 1e9
+
+    # end to end through the host entry point
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        hx.copy_(x)
+        host_outs = (torch.empty((batch, cap), dtype=torch.int32).pin_memory(),
+                     torch.empty((batch, cap, 2), dtype=torch.float64).pin_memory(),
+                     torch.empty((batch,), dtype=torch.int32).pin_memory(),
+                     torch.empty((batch,), dtype=torch.int32).pin_memory())
+        for _ in range(2):
+            sfft.sfft_execute_host(plan, hx, SEED, cap, host_outs, stream)
+        e2e_steps = max(3, min(args.steps, args.e2e_steps))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            sfft.sfft_execute_host(plan, hx, SEED, cap, host_outs, stream)
+        el = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": batch * world * e2e_steps / el, "unit": "transforms/s",
+               "h2d_bytes_per_step": int(hx.numel() * hx.element_size()),
+               "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in host_outs)),
+               "steps": e2e_steps}
+        del hx
+
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_context:
+        extra = context_measurements(sfft, plan, x, cap, stream, args)
+
+    cpu = None
+    if pool is not None:
+        per_core = 1
+        r, cnt_o, wall, busy, ok = oracle_rate(pool, cores, per_core, offset=50_000)
+        if wall < 8.0:  # aim for 10-30 s of CPU work in total
+            r2, cnt2, wall2, busy2, ok2 = oracle_rate(pool, cores, 2, offset=60_000)
+            r, cnt_o, wall = (cnt_o + cnt2) / (wall + wall2), cnt_o + cnt2, wall + wall2
+        pool.close()
+        cpu = {"value": r, "unit": "transforms/s", "cores": cores, "kind": "oracle",
+               "sample": f"{cnt_o} transforms of the same workload (n=2^22, k=64), one process per core, "
+                         f"{wall:.1f} s wall"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "k": k, "batch_per_gpu": batch, "rounds": plan.rounds,
+                       "precision": "complex64 gather/fold/bin FFT, FP64 subtraction and decode",
+                       "l2": "inputs (8 GiB per GPU) exceed L2; no flush", "parallelism": f"replicas x{world}",
+                       "support_exact_fraction": exact / batch},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "kernel": "k_exact_round (all rounds of a step)",
+                         "bytes_per_transform": bytes_tr, "samples_per_transform": samples_tr,
+                         "peak_kind": peak_kind},
+            "e2e": e2e, "clocks": clk.summary(), "gpu_launches": plan.rounds * args.steps,
+            "cpu_baseline": cpu,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def context_measurements(sfft, plan, x, cap, stream, args):
+    """cuFFT dense FFT of the same signals, the plain one-request-at-a-time GPU sFFT and latency."""
+    import torch
+
+    out = {}
+    n = x.shape[1]
+    # single-request latency (p50/p99) of this library, one request per call
+    p1 = sfft.Plan(plan.params, 1)
+    o1 = (torch.empty((1, cap), dtype=torch.int32, device="cuda"),
+          torch.empty((1, cap, 2), dtype=torch.float64, device="cuda"),
+          torch.empty((1,), dtype=torch.int32, device="cuda"), torch.empty((1,), dtype=torch.int32, device="cuda"))
+    lat = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.lat_runs)]
+    for i in range(10):
+        sfft.sfft_execute(p1, x[i % x.shape[0]: i % x.shape[0] + 1], SEED, cap, o1, stream)
+    torch.cuda.synchronize()
+    for i, (a, b) in enumerate(ev):
+        r = i % x.shape[0]
+        a.record(stream)
+        sfft.sfft_execute(p1, x[r:r + 1], SEED, cap, o1, stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    lat = sorted(a.elapsed_time(b) * 1000 for a, b in ev)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    out["latency_us"] = {"p50": p50, "p99": p99, "runs": len(lat), "what": "one request per call, device time"}
+    # plain GPU sFFT: the same kernels, one request at a time, no batching
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = min(x.shape[0], 256)
+    e0.record(stream)
+    for r in range(reps):
+        sfft.sfft_execute(p1, x[r:r + 1], SEED, cap, o1, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["plain_gpu_sfft"] = {"value": reps / (e0.elapsed_time(e1) / 1000), "unit": "transforms/s",
+                             "what": "same kernels, one request per call, sequential"}
+    p1.close()
+    # cuFFT C2C forward of the same n, batched over the same signals
+    chunk = 16
+    y = torch.empty((chunk, n), dtype=torch.complex64, device="cuda")
+    for _ in range(3):
+        torch.fft.fft(x[:chunk], out=y)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    reps_c = 0
+    for c0 in range(0, x.shape[0], chunk):
+        torch.fft.fft(x[c0:c0 + chunk], out=y)
+        reps_c += chunk
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["cufft"] = {"value": reps_c / (e0.elapsed_time(e1) / 1000), "unit": "transforms/s",
+                    "what": f"cuFFT C2C forward n=2^22 complex64, batches of {chunk} (torch.fft.fft)"}
+    del y
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--lat-runs", type=int, default=1000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-context", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

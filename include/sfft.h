@@ -1,0 +1,185 @@
+/*
+ * sfft.h -- C ABI of libsfft.so, a GB300 (sm_103a) implementation of the sparse Fourier transform of
+ * Hassanieh, Indyk, Katabi and Price, "Nearly Optimal Sparse Fourier Transform" (2012).
+ *
+ * Problem (Sec. 1, Eq. (1); Sec. 2 "Assumptions"): given time-domain access to x in C^n, n a power of
+ * two, return a sparse vector zhat approximating the spectrum X = DFT(x).  In the exactly k-sparse case
+ * (Sec. 3, Algorithm 1) zhat = X with constant probability; in the general case (Sec. 4, Algorithms 2
+ * and 3) ||X - zhat||_2 <= (1 + eps) min_{k-sparse y} ||X - y||_2 + delta ||X||_2.
+ *
+ * Conventions shared by every entry point:
+ *   - X_f = sum_t x_t exp(-2 pi i f t / n) (unnormalised; the paper's unitary spectrum is X / sqrt(n)).
+ *   - Indices are 0-based, taken mod n.  n <= 2^30.
+ *   - Signals are arrays of interleaved (re, im) pairs: float for SFFT_FP32, double for SFFT_FP64.
+ *   - Recovered values are always double (re, im) pairs.
+ *   - "d_" pointers are device memory owned by the caller; they must stay valid until the work queued
+ *     on the given stream completes.  "h_" pointers are host memory.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).  Every call that
+ *     takes a stream only enqueues work: it never synchronises, never allocates, and can be captured
+ *     in a CUDA graph.
+ *   - Every call returns a status and never throws.  On SFFT_ERR_CUDA the CUDA error string is
+ *     available from sfft_last_error().
+ *   - Randomness: request r of a call with seed s draws its hashing parameters from Philox4x32-10
+ *     keyed by s, counter (round, sub-step, kind, r); the same (x, params, seed, r) gives bit-identical
+ *     output on every run.
+ */
+#ifndef SFFT_H
+#define SFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sfft_status {
+    SFFT_OK = 0,
+    SFFT_ERR_INVALID_ARG = 1,   /* a null pointer, a size out of range, an inconsistent parameter */
+    SFFT_ERR_N_NOT_POW2 = 2,    /* n is not a power of two in [2^6, 2^30] */
+    SFFT_ERR_K_RANGE = 3,       /* k == 0 or the schedule needs more bins than supported */
+    SFFT_ERR_OOM = 4,           /* device allocation failed (plan creation only) */
+    SFFT_ERR_CUDA = 5,          /* a CUDA call failed; see sfft_last_error() */
+    SFFT_ERR_TIMEOUT = 6,       /* a wait gave up */
+    SFFT_ERR_CAPACITY = 7,      /* a request's zhat outgrew its capacity; the largest-index entries were dropped */
+    SFFT_ERR_NOT_CONVERGED = 8, /* warning: the last round saw a bin above thr it could not decode */
+    SFFT_ERR_BUSY = 9           /* the plan or queue cannot take more work now */
+} sfft_status;
+
+typedef enum sfft_mode { SFFT_EXACT = 0, SFFT_GENERAL = 1 } sfft_mode;
+typedef enum sfft_precision { SFFT_FP32 = 0, SFFT_FP64 = 1 } sfft_precision;
+
+/*
+ * Parameters.  Fields the paper leaves as Theta(.) constants are explicit; sfft_params_default()
+ * fills the values used throughout this library's tests and benchmarks.
+ */
+typedef struct sfft_params {
+    uint64_t n;            /* signal length, a power of two */
+    uint32_t k;            /* sparsity */
+    uint32_t mode;         /* sfft_mode */
+    uint32_t precision;    /* sfft_precision: data path of gather, fold and bin FFT */
+    double delta;          /* flat-window tolerance (Sec. 2, Definition of a flat window) */
+    double alpha0;         /* alpha of the first round */
+    double bins_per_k;     /* B = pow2ceil(bins_per_k k_t) (exact), pow2ceil(bins_per_k k_r / eps) (general) */
+    uint32_t B_min;        /* smallest B of any round */
+    uint32_t extra_rounds; /* exact: rounds after t = ceil(log2 k) */
+    double thr;            /* exact: J = {j : |u_j| > thr} (Algorithm 1's 1/2) */
+    double tau_dec;        /* exact: smallest phase tolerance (rad) the location ladder may leave */
+    double iso_tol;        /* exact: shifted bins must keep |u_j| to within iso_tol |u_j| */
+    double gmin;           /* exact: a decode needs window gain W(-o) >= gmin */
+    double prune;          /* exact: after a round drop zhat_i with |zhat_i| < prune thr */
+    double ref_lo, ref_hi; /* exact: residual window (times thr) for re-estimating a known value */
+    double ref_tol;        /* exact: phase tolerance (rad) of that re-estimate */
+    uint32_t z_cap;        /* capacity of zhat per request */
+    double eps;            /* general: epsilon of Eq. (1) */
+    uint32_t t_regions;    /* general: t of Algorithm 3 (0 -> largest power of two <= log2 n) */
+    uint32_t R_loc;        /* general: rounds of LocateInner per level */
+    uint32_t R_est;        /* general: hashings of EstimateValues */
+    double s;              /* general: vote half-width s pi */
+    double est_gmin;       /* general: a hashing joins the median only if W(-o) >= est_gmin */
+} sfft_params;
+
+/* Fill *p with the library defaults for (n, k, mode); precision SFFT_FP32. */
+void sfft_params_default(sfft_params* p, uint64_t n, uint32_t k, uint32_t mode);
+
+/* Human-readable name of a status. */
+const char* sfft_status_str(sfft_status s);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* sfft_last_error(void);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Plans                                                                                          */
+/* ---------------------------------------------------------------------------------------------- */
+typedef struct sfft_plan_s* sfft_plan;
+
+/*
+ * Build a plan: the round schedule, the flat-window taps of every round (Sec. 7, Lemma on window
+ * construction), the exact window response table W(o), |o| <= n/2B, of every round, and a device
+ * workspace for max_batch requests.  The only call that allocates device memory.  Runs on the
+ * current CUDA device and synchronises it.
+ * Errors: INVALID_ARG (null, max_batch == 0, bad field), N_NOT_POW2, K_RANGE, OOM, CUDA.
+ */
+sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan* out);
+
+/* Release a plan and its device memory (synchronises the device). NULL is accepted. */
+sfft_status sfft_plan_destroy(sfft_plan plan);
+
+/* Number of rounds of the plan's schedule (exact: ceil(log2 k) + 1 + extra_rounds; general: R). */
+uint32_t sfft_plan_rounds(sfft_plan plan);
+
+/*
+ * Description of exact-mode round t (Algorithm 1, NoiselessSparseFFT loop): B, alpha, the window
+ * half-width T (2T+1 taps), the ladder shifts beta_l (finest first), and the hashing parameters
+ * (sigma, b) that request `request` of a call with `seed` draws for that round.
+ * shifts must hold 4 entries.  Host-only; never touches the device.
+ */
+sfft_status sfft_plan_round_info(sfft_plan plan, uint32_t t, uint64_t seed, uint32_t request, uint32_t* B,
+                                 double* alpha, int64_t* T, uint32_t* nshift, uint64_t* shifts, uint64_t* sigma,
+                                 uint64_t* b);
+
+/* Copy round t's window taps g_0..g_T (double, host) into h_taps (T+1 entries). */
+sfft_status sfft_plan_taps(sfft_plan plan, uint32_t t, double* h_taps, uint64_t cap);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Whole transforms                                                                               */
+/* ---------------------------------------------------------------------------------------------- */
+/*
+ * Run the sparse FFT on `batch` signals (batch <= max_batch) stored back to back in d_x
+ * (batch x n complex values of the plan's precision).  Request r uses seed `seed`, request index r.
+ * Outputs, per request r, in caller-owned device arrays:
+ *   d_idx[r*cap .. r*cap + count)  recovered frequencies, ascending (uint32)
+ *   d_val[...]                    their values X_f as (re, im) doubles
+ *   d_count[r]                    number of entries written (<= cap)
+ *   d_flag[r]                     sfft_status of the request: OK, NOT_CONVERGED or CAPACITY
+ * Exact mode follows Algorithm 1; general mode Algorithms 2 and 3.
+ * Errors: INVALID_ARG (null pointer, batch out of range, cap == 0), CUDA (launch failure).
+ */
+sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, void* stream,
+                         uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag);
+
+/*
+ * Same computation from host memory: copies h_x (batch x n) to a device staging buffer owned by the
+ * plan, runs sfft_execute, copies the outputs back into host arrays and synchronises the stream.
+ * h_x should be page-locked for full copy bandwidth.  The staging buffer is allocated on the first
+ * call with a given batch (it is the one call besides plan creation that may allocate).
+ */
+sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, uint64_t seed, void* stream,
+                              uint32_t* h_idx, double* h_val, uint32_t cap, uint32_t* h_count, int32_t* h_flag);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Single steps (for parity tests and for callers that drive the rounds themselves)               */
+/* ---------------------------------------------------------------------------------------------- */
+/*
+ * One HashToBins (Algorithm 1, procedure HashToBins; the four-step method of Lemma "hashtobins"),
+ * with exact-mode round t's window, explicit (sigma odd, a, b), on one signal d_x (n values):
+ *   u_j = sum_r (sum_{t' = r mod B} G_t' x_{sigma(t'-a)} w^{sigma b t'}) e^{-2 pi i j r / B}
+ *         - sum_{i in zhat} W(-o(i)) zhat_i w^{a sigma i} [h(i) = j]
+ * d_zidx / d_zval hold nz entries of zhat (nz may be 0); d_u receives B (re, im) doubles.
+ */
+sfft_status sfft_hash_to_bins(sfft_plan plan, uint32_t t, const void* d_x, uint64_t sigma, uint64_t a, uint64_t b,
+                              const uint32_t* d_zidx, const double* d_zval, uint32_t nz, double* d_u, void* stream);
+
+/*
+ * The location and estimation step of exact-mode round t (Algorithm 1, loop over J, with this
+ * library's readings: shift-ladder phase decode, value u_j / W(-o), isolation check, and the
+ * re-estimation of known values) on caller-supplied bins d_u ((1 + nshift) x B (re, im) doubles: the
+ * hashing at a = 0 first, then one per ladder shift of round t).  d_zidx lists the nz indices already
+ * in zhat.  Writes up to B entries (d_widx, d_wval) sorted by index, their number in *d_count, |J| in
+ * *d_nabove and the number of J decodes kept in *d_nkept.
+ */
+sfft_status sfft_exact_decode(sfft_plan plan, uint32_t t, uint64_t sigma, uint64_t b, const double* d_u,
+                              const uint32_t* d_zidx, uint32_t nz, uint32_t* d_widx, double* d_wval,
+                              uint32_t* d_count, uint32_t* d_nabove, uint32_t* d_nkept, void* stream);
+
+/*
+ * Philox4x32-10 as the device computes it (Salmon et al., SC 2011): for i < count, the four output
+ * words for key (key0, key1) and counter (ctr[0], ctr[1], ctr[2], ctr[3] + i), written to d_out[4 i..].
+ */
+sfft_status sfft_philox(uint32_t key0, uint32_t key1, const uint32_t* h_ctr, uint32_t count, uint32_t* d_out,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFFT_H */

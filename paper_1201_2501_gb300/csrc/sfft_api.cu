@@ -1,0 +1,366 @@
+// sfft_api.cu -- the C ABI of libsfft.so (declared in include/sfft.h): plans, whole transforms and
+// single steps.  Everything here is host code that validates arguments and enqueues kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "philox.cuh"
+#include "sfft_internal.h"
+
+using namespace sfft;
+
+namespace {
+
+sfft_status cuda_fail(cudaError_t e, const char* what) {
+    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return SFFT_ERR_CUDA;
+}
+
+#define SFFT_CUDA(call, what)                       \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
+
+sfft_status validate(const sfft_params* p) {
+    if (!p) return SFFT_ERR_INVALID_ARG;
+    if (!is_pow2(p->n) || p->n < 64 || p->n > (uint64_t(1) << 30)) return SFFT_ERR_N_NOT_POW2;
+    if (p->k == 0 || (uint64_t)p->k > p->n / 4) return SFFT_ERR_K_RANGE;
+    if (p->mode != SFFT_EXACT && p->mode != SFFT_GENERAL) return SFFT_ERR_INVALID_ARG;
+    if (p->precision != SFFT_FP32 && p->precision != SFFT_FP64) return SFFT_ERR_INVALID_ARG;
+    if (!(p->delta > 0 && p->delta < 0.5)) return SFFT_ERR_INVALID_ARG;
+    if (!(p->alpha0 > 0 && p->alpha0 < 1)) return SFFT_ERR_INVALID_ARG;
+    if (!(p->bins_per_k > 0) || p->B_min < 2 || !is_pow2(p->B_min)) return SFFT_ERR_INVALID_ARG;
+    if (!(p->thr > 0) || !(p->tau_dec > 0 && p->tau_dec < 1) || !(p->iso_tol > 0)) return SFFT_ERR_INVALID_ARG;
+    if (p->z_cap == 0 || p->z_cap > 4096) return SFFT_ERR_INVALID_ARG;
+    return SFFT_OK;
+}
+
+void free_plan(sfft_plan_s* pl) {
+    if (!pl) return;
+    cudaFree(pl->d_taps32);
+    cudaFree(pl->d_taps64);
+    cudaFree(pl->d_wtab);
+    cudaFree(pl->d_part);
+    cudaFree(pl->d_counter);
+    cudaFree(pl->d_zidx);
+    cudaFree(pl->d_zval);
+    cudaFree(pl->d_zcount);
+    cudaFree(pl->d_zflag);
+    cudaFree(pl->d_ubins);
+    cudaFree(pl->d_aux);
+    cudaFree(pl->d_stage);
+    cudaFree(pl->d_out_idx);
+    cudaFree(pl->d_out_val);
+    cudaFree(pl->d_out_count);
+    cudaFree(pl->d_out_flag);
+    delete pl;
+}
+
+ExactArgs base_args(const sfft_plan_s* pl, const ExactRound& r, uint32_t t) {
+    ExactArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const sfft_params& p = pl->p;
+    a.n = p.n;
+    a.nmask = (uint32_t)(p.n - 1);
+    a.round = t;
+    a.B = r.B;
+    a.logB = r.logB;
+    a.T = r.T;
+    a.H = 1 + r.nshift;
+    a.a_base = 0;
+    a.a[0] = 0;
+    a.shift64[0] = 0;
+    for (uint32_t l = 0; l < r.nshift; ++l) {
+        a.a[l + 1] = (uint32_t)r.shift[l];
+        a.shift64[l + 1] = r.shift[l];
+    }
+    a.chunks = r.chunks;
+    a.stage = r.stage;
+    a.maxshift = (uint32_t)r.shift[r.nshift - 1];
+    a.taps32 = pl->d_taps32 + r.taps_off;
+    a.taps64 = pl->d_taps64 + r.taps_off;
+    a.wtab = pl->d_wtab + r.wtab_off;
+    a.part = pl->d_part;
+    a.counter = pl->d_counter;
+    a.zidx = pl->d_zidx;
+    a.zval = pl->d_zval;
+    a.zcount = pl->d_zcount;
+    a.zflag = pl->d_zflag;
+    a.zcap = p.z_cap;
+    a.thr = p.thr;
+    a.iso_tol = p.iso_tol;
+    a.gmin = p.gmin;
+    a.prune = p.prune;
+    a.ref_lo = p.ref_lo;
+    a.ref_hi = p.ref_hi;
+    a.ref_tol = p.ref_tol;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan* out) {
+    if (!out) return SFFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    sfft_status st = validate(p);
+    if (st != SFFT_OK) return st;
+    if (max_batch == 0) return SFFT_ERR_INVALID_ARG;
+    if (p->mode != SFFT_EXACT) return SFFT_ERR_INVALID_ARG;  // the general mode has its own plan path
+    sfft_plan_s* pl = new (std::nothrow) sfft_plan_s();
+    if (!pl) return SFFT_ERR_OOM;
+    pl->p = *p;
+    pl->max_batch = max_batch;
+    cudaGetDevice(&pl->device);
+    st = build_exact_schedule(pl);
+    if (st != SFFT_OK) {
+        free_plan(pl);
+        return st;
+    }
+    const bool fp64 = p->precision == SFFT_FP64;
+    // taps (FP32 and FP64 copies) and the W tables
+    const size_t ntaps = pl->taps_host.size();
+    std::vector<float> t32(ntaps);
+    for (size_t i = 0; i < ntaps; ++i) t32[i] = (float)pl->taps_host[i];
+    size_t part_elems = 0, max_smem = 0;
+    uint32_t maxB = 0, maxH = 0;
+    for (const ExactRound& r : pl->rounds) {
+        const size_t e = (size_t)r.chunks * (1 + r.nshift) * r.B;
+        if (e > part_elems) part_elems = e;
+        if (r.smem > max_smem) max_smem = r.smem;
+        if (r.B > maxB) maxB = r.B;
+        if (1 + r.nshift > maxH) maxH = 1 + r.nshift;
+    }
+    pl->part_bytes = part_elems * (size_t)max_batch * (fp64 ? 16 : 8);
+    cudaError_t e = cudaSuccess;
+#define SFFT_ALLOC(ptr, bytes)                                        \
+    do {                                                              \
+        e = cudaMalloc((void**)&(ptr), (bytes));                      \
+        if (e != cudaSuccess) {                                       \
+            set_last_error(std::string("cudaMalloc: ") + cudaGetErrorString(e)); \
+            free_plan(pl);                                            \
+            return SFFT_ERR_OOM;                                      \
+        }                                                             \
+    } while (0)
+    SFFT_ALLOC(pl->d_taps32, ntaps * sizeof(float));
+    SFFT_ALLOC(pl->d_taps64, ntaps * sizeof(double));
+    SFFT_ALLOC(pl->d_wtab, pl->wtab_len * sizeof(double));
+    SFFT_ALLOC(pl->d_part, pl->part_bytes);
+    SFFT_ALLOC(pl->d_counter, (size_t)max_batch * sizeof(uint32_t));
+    SFFT_ALLOC(pl->d_zidx, (size_t)max_batch * p->z_cap * sizeof(uint32_t));
+    SFFT_ALLOC(pl->d_zval, (size_t)max_batch * p->z_cap * sizeof(double2));
+    SFFT_ALLOC(pl->d_zcount, (size_t)max_batch * sizeof(uint32_t));
+    SFFT_ALLOC(pl->d_zflag, (size_t)max_batch * sizeof(int32_t));
+    SFFT_ALLOC(pl->d_ubins, (size_t)maxB * kMaxHash * sizeof(double2));
+    SFFT_ALLOC(pl->d_aux, 64 * sizeof(uint32_t));
+#undef SFFT_ALLOC
+    auto fail = [&](cudaError_t err, const char* what) {
+        set_last_error(std::string(what) + ": " + cudaGetErrorString(err));
+        free_plan(pl);
+        return SFFT_ERR_CUDA;
+    };
+    if ((e = cudaMemcpy(pl->d_taps32, t32.data(), ntaps * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e, "upload taps");
+    if ((e = cudaMemcpy(pl->d_taps64, pl->taps_host.data(), ntaps * sizeof(double), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return fail(e, "upload taps");
+    if ((e = cudaMemcpy(pl->d_wtab, pl->wtab_host.data(), pl->wtab_len * sizeof(double), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return fail(e, "upload window table");
+    if ((e = cudaMemset(pl->d_counter, 0, (size_t)max_batch * sizeof(uint32_t))) != cudaSuccess)
+        return fail(e, "clear counters");
+    if ((e = set_exact_smem_limit(max_smem, fp64)) != cudaSuccess) return fail(e, "shared memory limit");
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "plan synchronise");
+    *out = pl;
+    return SFFT_OK;
+}
+
+sfft_status sfft_plan_destroy(sfft_plan plan) {
+    if (!plan) return SFFT_OK;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return SFFT_OK;
+}
+
+uint32_t sfft_plan_rounds(sfft_plan plan) { return plan ? (uint32_t)plan->rounds.size() : 0; }
+
+sfft_status sfft_plan_round_info(sfft_plan plan, uint32_t t, uint64_t seed, uint32_t request, uint32_t* B,
+                                 double* alpha, int64_t* T, uint32_t* nshift, uint64_t* shifts, uint64_t* sigma,
+                                 uint64_t* b) {
+    if (!plan || t >= plan->rounds.size()) return SFFT_ERR_INVALID_ARG;
+    const ExactRound& r = plan->rounds[t];
+    if (B) *B = r.B;
+    if (alpha) *alpha = r.alpha;
+    if (T) *T = r.T;
+    if (nshift) *nshift = r.nshift;
+    if (shifts)
+        for (uint32_t l = 0; l < 4; ++l) shifts[l] = l < r.nshift ? r.shift[l] : 0;
+    uint64_t s = 0, bb = 0;
+    draw_exact_host(seed, request, t, plan->p.n, &s, &bb);
+    if (sigma) *sigma = s;
+    if (b) *b = bb;
+    return SFFT_OK;
+}
+
+sfft_status sfft_plan_taps(sfft_plan plan, uint32_t t, double* h_taps, uint64_t cap) {
+    if (!plan || !h_taps || t >= plan->rounds.size()) return SFFT_ERR_INVALID_ARG;
+    const ExactRound& r = plan->rounds[t];
+    if (cap < (uint64_t)r.T + 1) return SFFT_ERR_INVALID_ARG;
+    std::memcpy(h_taps, plan->taps_host.data() + r.taps_off, sizeof(double) * ((size_t)r.T + 1));
+    return SFFT_OK;
+}
+
+sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, void* stream,
+                         uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag) {
+    if (!plan || !d_x || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
+    if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fp64 = plan->p.precision == SFFT_FP64;
+    SFFT_CUDA(cudaMemsetAsync(plan->d_zcount, 0, batch * sizeof(uint32_t), st), "clear zhat");
+    SFFT_CUDA(cudaMemsetAsync(plan->d_zflag, 0, batch * sizeof(int32_t), st), "clear flags");
+    const uint32_t R = (uint32_t)plan->rounds.size();
+    for (uint32_t t = 0; t < R; ++t) {
+        const ExactRound& r = plan->rounds[t];
+        ExactArgs a = base_args(plan, r, t);
+        a.x = d_x;
+        a.seed = seed;
+        a.first_round = t == 0;
+        a.last_round = t + 1 == R;
+        a.out_idx = d_idx;
+        a.out_val = reinterpret_cast<double2*>(d_val);
+        a.out_cap = cap;
+        a.out_count = d_count;
+        a.out_flag = d_flag;
+        SFFT_CUDA(launch_exact_round(a, batch, r.smem, st, fp64), "exact round");
+    }
+    return SFFT_OK;
+}
+
+sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, uint64_t seed, void* stream,
+                              uint32_t* h_idx, double* h_val, uint32_t cap, uint32_t* h_count, int32_t* h_flag) {
+    if (!plan || !h_x || !h_idx || !h_val || !h_count || !h_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
+    if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t elem = plan->p.precision == SFFT_FP64 ? 16 : 8;
+    const size_t xbytes = (size_t)batch * plan->p.n * elem;
+    if (plan->stage_bytes < xbytes || plan->out_cap < (size_t)batch * cap) {
+        SFFT_CUDA(cudaStreamSynchronize(st), "sync before staging");
+        cudaFree(plan->d_stage);
+        cudaFree(plan->d_out_idx);
+        cudaFree(plan->d_out_val);
+        cudaFree(plan->d_out_count);
+        cudaFree(plan->d_out_flag);
+        plan->d_stage = nullptr;
+        plan->d_out_idx = nullptr;
+        plan->d_out_val = nullptr;
+        plan->d_out_count = nullptr;
+        plan->d_out_flag = nullptr;
+        plan->stage_bytes = 0;
+        plan->out_cap = 0;
+        if (cudaMalloc(&plan->d_stage, xbytes) != cudaSuccess) return SFFT_ERR_OOM;
+        if (cudaMalloc((void**)&plan->d_out_idx, (size_t)batch * cap * 4) != cudaSuccess) return SFFT_ERR_OOM;
+        if (cudaMalloc((void**)&plan->d_out_val, (size_t)batch * cap * 16) != cudaSuccess) return SFFT_ERR_OOM;
+        if (cudaMalloc((void**)&plan->d_out_count, (size_t)batch * 4) != cudaSuccess) return SFFT_ERR_OOM;
+        if (cudaMalloc((void**)&plan->d_out_flag, (size_t)batch * 4) != cudaSuccess) return SFFT_ERR_OOM;
+        plan->stage_bytes = xbytes;
+        plan->out_cap = (size_t)batch * cap;
+    }
+    SFFT_CUDA(cudaMemcpyAsync(plan->d_stage, h_x, xbytes, cudaMemcpyHostToDevice, st), "copy x to device");
+    sfft_status s = sfft_execute(plan, plan->d_stage, batch, seed, stream, plan->d_out_idx, plan->d_out_val, cap,
+                                 plan->d_out_count, plan->d_out_flag);
+    if (s != SFFT_OK) return s;
+    SFFT_CUDA(cudaMemcpyAsync(h_count, plan->d_out_count, (size_t)batch * 4, cudaMemcpyDeviceToHost, st), "copy count");
+    SFFT_CUDA(cudaMemcpyAsync(h_flag, plan->d_out_flag, (size_t)batch * 4, cudaMemcpyDeviceToHost, st), "copy flag");
+    SFFT_CUDA(cudaMemcpyAsync(h_idx, plan->d_out_idx, (size_t)batch * cap * 4, cudaMemcpyDeviceToHost, st), "copy idx");
+    SFFT_CUDA(cudaMemcpyAsync(h_val, plan->d_out_val, (size_t)batch * cap * 16, cudaMemcpyDeviceToHost, st),
+              "copy values");
+    SFFT_CUDA(cudaStreamSynchronize(st), "synchronise");
+    return SFFT_OK;
+}
+
+sfft_status sfft_hash_to_bins(sfft_plan plan, uint32_t t, const void* d_x, uint64_t sigma, uint64_t a, uint64_t b,
+                              const uint32_t* d_zidx, const double* d_zval, uint32_t nz, double* d_u, void* stream) {
+    if (!plan || !d_x || !d_u || t >= plan->rounds.size()) return SFFT_ERR_INVALID_ARG;
+    if (nz > 0 && (!d_zidx || !d_zval)) return SFFT_ERR_INVALID_ARG;
+    if (!(sigma & 1) || sigma >= plan->p.n || a >= plan->p.n || b >= plan->p.n) return SFFT_ERR_INVALID_ARG;
+    if (nz > plan->p.z_cap) return SFFT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fp64 = plan->p.precision == SFFT_FP64;
+    ExactRound r = plan->rounds[t];
+    ExactArgs args = base_args(plan, r, t);
+    args.x = d_x;
+    args.H = 1;
+    args.a_base = (uint32_t)a;
+    args.a[0] = 0;
+    args.maxshift = 0;
+    args.stage = kChunkTaps;
+    args.bins_only = 1;
+    args.e_sigma = (uint32_t)sigma;
+    args.e_b = (uint32_t)b;
+    args.ubins = reinterpret_cast<double2*>(d_u);
+    args.zidx = const_cast<uint32_t*>(d_zidx);
+    args.zval = reinterpret_cast<double2*>(const_cast<double*>(d_zval));
+    args.zcap = nz > 0 ? nz : 1;
+    args.e_nz = nz;
+    const size_t gs = exact_gather_smem(args.stage, fp64) + (size_t)(r.B > (uint32_t)kThreads ? r.B : kThreads) *
+                                                                (fp64 ? 16 : 8);
+    const size_t fs = exact_finish_smem(r.B, 1, args.zcap, fp64);
+    const size_t smem = gs > fs ? gs : fs;
+    SFFT_CUDA(set_exact_smem_limit(smem > r.smem ? smem : r.smem, fp64), "shared memory limit");
+    SFFT_CUDA(launch_exact_round(args, 1, smem, st, fp64), "hash to bins");
+    return SFFT_OK;
+}
+
+sfft_status sfft_exact_decode(sfft_plan plan, uint32_t t, uint64_t sigma, uint64_t b, const double* d_u,
+                              const uint32_t* d_zidx, uint32_t nz, uint32_t* d_widx, double* d_wval,
+                              uint32_t* d_count, uint32_t* d_nabove, uint32_t* d_nkept, void* stream) {
+    if (!plan || !d_u || !d_widx || !d_wval || !d_count || !d_nabove || !d_nkept) return SFFT_ERR_INVALID_ARG;
+    if (t >= plan->rounds.size() || (nz > 0 && !d_zidx) || nz > 4096) return SFFT_ERR_INVALID_ARG;
+    if (!(sigma & 1) || sigma >= plan->p.n || b >= plan->p.n) return SFFT_ERR_INVALID_ARG;
+    const ExactRound& r = plan->rounds[t];
+    const sfft_params& p = plan->p;
+    DecodeArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n = p.n;
+    a.nmask = (uint32_t)(p.n - 1);
+    a.B = r.B;
+    a.logB = r.logB;
+    a.H = 1 + r.nshift;
+    for (uint32_t l = 0; l < r.nshift; ++l) a.shift64[l] = r.shift[l];
+    a.sigma = (uint32_t)sigma;
+    a.b = (uint32_t)b;
+    a.wtab = plan->d_wtab + r.wtab_off;
+    a.u = reinterpret_cast<const double2*>(d_u);
+    a.zidx = d_zidx;
+    a.nz = nz;
+    a.thr = p.thr;
+    a.iso_tol = p.iso_tol;
+    a.gmin = p.gmin;
+    a.ref_lo = p.ref_lo;
+    a.ref_hi = p.ref_hi;
+    a.ref_tol = p.ref_tol;
+    a.widx = d_widx;
+    a.wval = reinterpret_cast<double2*>(d_wval);
+    a.count = d_count;
+    a.nabove = d_nabove;
+    a.nkept = d_nkept;
+    SFFT_CUDA(launch_exact_decode(a, (cudaStream_t)stream), "exact decode");
+    return SFFT_OK;
+}
+
+sfft_status sfft_philox(uint32_t key0, uint32_t key1, const uint32_t* h_ctr, uint32_t count, uint32_t* d_out,
+                        void* stream) {
+    if (!h_ctr || (!d_out && count)) return SFFT_ERR_INVALID_ARG;
+    SFFT_CUDA(launch_philox(key0, key1, h_ctr[0], h_ctr[1], h_ctr[2], h_ctr[3], count, d_out, (cudaStream_t)stream),
+              "philox");
+    return SFFT_OK;
+}
+
+}  // extern "C"

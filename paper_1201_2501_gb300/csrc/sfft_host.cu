@@ -1,0 +1,231 @@
+// sfft_host.cu -- host-side plan construction: parameter defaults, the exact round schedule and the
+// flat-window design (Sec. 7 of the paper), all in double precision.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "philox.cuh"
+#include "sfft_internal.h"
+
+namespace sfft {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& s) { g_last_error = s; }
+
+static uint64_t pow2_at_least(double v) {
+    uint64_t p = 1;
+    while ((double)p < v) p <<= 1;
+    return p;
+}
+
+static uint32_t ceil_log2(uint64_t v) {
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < v) ++l;
+    return l;
+}
+
+// Sec. 7: the window is a Gaussian (frequency std sigma_f = alpha / (4 B z), z = sqrt(2 ln 1/delta))
+// convolved with a box-car of half width C = (1 - alpha/2) / (2B).  In time the Gaussian factor is
+// exp(-2 pi^2 sigma_f^2 t^2); it is cut where it falls to delta, at T = z / (2 pi sigma_f)
+// = 4 B ln(1/delta) / (pi alpha).
+int64_t window_halfwidth(uint32_t B, double alpha, double delta) {
+    const double T = 4.0 * (double)B * std::log(1.0 / delta) / (M_PI * alpha);
+    return (int64_t)std::floor(T);
+}
+
+// Taps g_t = n G*(t), t = 0..T, G*(t) = exp(-2 pi^2 sigma_f^2 t^2) sin(2 pi C t) / (pi t), G*(0) = 2C.
+// The factor n makes an isolated tone of amplitude X land in its bin with amplitude X W(-o).
+void window_taps_host(uint64_t n, uint32_t B, double alpha, double delta, int64_t T, double* g) {
+    const double z = std::sqrt(2.0 * std::log(1.0 / delta));
+    const double C = (1.0 - 0.5 * alpha) / (2.0 * (double)B);
+    const double sf = alpha / (4.0 * (double)B * z);
+    const double gauss_rate = 2.0 * M_PI * M_PI * sf * sf;
+    const double nn = (double)n;
+    g[0] = nn * 2.0 * C;
+    for (int64_t t = 1; t <= T; ++t) {
+        const double tt = (double)t;
+        g[t] = nn * std::exp(-gauss_rate * tt * tt) * std::sin(2.0 * M_PI * C * tt) / (M_PI * tt);
+    }
+}
+
+// Exact response of the truncated taps, W(o) = (1/n) (g_0 + 2 sum_{t=1}^{T} g_t cos(2 pi o t / n)),
+// for o = 0..len-1 (the gain HashToBins applies to a coefficient at offset o from its bin centre).
+// Offsets are processed in blocks; within a block cos(2 pi o t / n) advances by a complex rotation
+// per step of t and is re-anchored to an exactly reduced phase every 128 steps.  Blocks run on all
+// host cores.
+void window_table_host(uint64_t n, const double* g, int64_t T, uint64_t len, double* W) {
+    const uint64_t blk = 256;
+    const uint64_t nblk = (len + blk - 1) / blk;
+    std::atomic<uint64_t> next{0};
+    auto work = [&]() {
+        std::vector<double> c(blk), s(blk), cr(blk), sr(blk), acc(blk);
+        for (;;) {
+            const uint64_t bi = next.fetch_add(1);
+            if (bi >= nblk) break;
+            const uint64_t o0 = bi * blk;
+            const uint64_t m = std::min<uint64_t>(blk, len - o0);
+            for (uint64_t q = 0; q < m; ++q) {
+                const double th = 2.0 * M_PI * (double)(o0 + q) / (double)n;
+                cr[q] = std::cos(th);
+                sr[q] = std::sin(th);
+                acc[q] = 0.0;
+            }
+            for (int64_t t0 = 1; t0 <= T; t0 += 128) {
+                for (uint64_t q = 0; q < m; ++q) {  // exact anchor cos/sin(2 pi ((o t0) mod n) / n)
+                    const uint64_t e = ((o0 + q) * (uint64_t)t0) & (n - 1);
+                    const double ph = 2.0 * M_PI * (double)e / (double)n;
+                    c[q] = std::cos(ph);
+                    s[q] = std::sin(ph);
+                }
+                const int64_t t1 = std::min<int64_t>(T, t0 + 127);
+                for (int64_t t = t0; t <= t1; ++t) {
+                    const double gt = g[t];
+                    for (uint64_t q = 0; q < m; ++q) {
+                        acc[q] += gt * c[q];
+                        const double cn = c[q] * cr[q] - s[q] * sr[q];
+                        const double sn = s[q] * cr[q] + c[q] * sr[q];
+                        c[q] = cn;
+                        s[q] = sn;
+                    }
+                }
+            }
+            for (uint64_t q = 0; q < m; ++q) W[o0 + q] = (g[0] + 2.0 * acc[q]) / (double)n;
+        }
+    };
+    unsigned nth = std::thread::hardware_concurrency();
+    if (nth == 0) nth = 1;
+    if (nth > 64) nth = 64;
+    if ((uint64_t)nth > nblk) nth = (unsigned)nblk;
+    std::vector<std::thread> pool;
+    for (unsigned i = 1; i < nth; ++i) pool.emplace_back(work);
+    work();
+    for (auto& th : pool) th.join();
+}
+
+void draw_exact_host(uint64_t seed, uint32_t request, uint32_t round, uint64_t n, uint64_t* sigma, uint64_t* b) {
+    uint32_t s, bb;
+    exact_hash(seed, request, round, (uint32_t)(n - 1), &s, &bb);
+    *sigma = s;
+    *b = bb;
+}
+
+// Exact schedule (Algorithm 1, NoiselessSparseFFT): rounds t = 0..ceil(log2 k) (+ extra),
+// k_t = ceil(k / 2^t), B_t = pow2 >= bins_per_k k_t in [B_min, n/2], alpha_t = alpha0 2^{-t/2}.
+// Location ladder: shifts beta_l = B R_l, R_0 = 1, coarsest R = pow2 >= tau n / (pi B) (at most
+// n/(2B)), consecutive ratios at most the largest power of two rho with pi / rho >= tau.
+sfft_status build_exact_schedule(sfft_plan_s* pl) {
+    const sfft_params& p = pl->p;
+    const bool fp64 = p.precision == SFFT_FP64;
+    const uint32_t R = ceil_log2(p.k) + 1 + p.extra_rounds;
+    pl->rounds.clear();
+    pl->taps_host.clear();
+    pl->wtab_host.clear();
+    size_t taps_off = 0, wtab_off = 0;
+    for (uint32_t t = 0; t < R; ++t) {
+        ExactRound r;
+        uint64_t kt = ((uint64_t)p.k + (uint64_t(1) << t) - 1) >> t;
+        if (kt < 1) kt = 1;
+        uint64_t B = pow2_at_least(p.bins_per_k * (double)kt);
+        if (B < p.B_min) B = p.B_min;
+        if (B > p.n / 2) B = p.n / 2;
+        if (B > kMaxB) return SFFT_ERR_K_RANGE;
+        r.B = (uint32_t)B;
+        r.logB = ceil_log2(B);
+        r.alpha = std::ldexp(p.alpha0, -(int)(t / 2)) * ((t & 1u) ? M_SQRT1_2 : 1.0);
+        r.T = window_halfwidth(r.B, r.alpha, p.delta);
+        // ladder
+        const uint64_t Np = p.n / B;
+        uint64_t Rc = pow2_at_least(p.tau_dec * (double)p.n / (M_PI * (double)B));
+        if (Rc > Np / 2) Rc = Np / 2 > 0 ? Np / 2 : 1;
+        uint64_t rho = 1;
+        while (M_PI / (double)(rho * 2) >= p.tau_dec) rho *= 2;
+        if (rho < 2) rho = 2;
+        r.nshift = 0;
+        uint64_t Rl = 1;
+        r.shift[r.nshift++] = B * Rl;
+        while (Rl < Rc && r.nshift < 4) {
+            Rl = Rl * rho < Rc ? Rl * rho : Rc;
+            r.shift[r.nshift++] = B * Rl;
+        }
+        if (1 + r.nshift > (uint32_t)kMaxHash) return SFFT_ERR_K_RANGE;
+        const uint64_t maxshift = r.shift[r.nshift - 1];
+        if (maxshift > 8192) return SFFT_ERR_K_RANGE;
+        const uint64_t w = 2 * (uint64_t)r.T + 1;
+        r.chunks = (uint32_t)((w + kChunkTaps - 1) / kChunkTaps);
+        r.stage = (uint32_t)(kChunkTaps + maxshift);
+        r.taps_off = taps_off;
+        r.wtab_off = wtab_off;
+        const size_t gs = exact_gather_smem(r.stage, fp64) + (size_t)(1 + r.nshift) * (B > (uint64_t)kThreads ? B : kThreads) *
+                                                              (fp64 ? 16 : 8);
+        const size_t fs = exact_finish_smem(r.B, 1 + r.nshift, p.z_cap, fp64);
+        r.smem = gs > fs ? gs : fs;
+        if (r.smem > 200 * 1024) return SFFT_ERR_K_RANGE;
+        pl->taps_host.resize(taps_off + (size_t)r.T + 1);
+        window_taps_host(p.n, r.B, r.alpha, p.delta, r.T, pl->taps_host.data() + taps_off);
+        pl->wtab_host.resize(wtab_off + Np / 2 + 1);
+        window_table_host(p.n, pl->taps_host.data() + taps_off, r.T, Np / 2 + 1, pl->wtab_host.data() + wtab_off);
+        taps_off += (size_t)r.T + 1;
+        wtab_off += Np / 2 + 1;
+        pl->rounds.push_back(r);
+    }
+    pl->wtab_len = wtab_off;
+    return SFFT_OK;
+}
+
+}  // namespace sfft
+
+extern "C" {
+
+void sfft_params_default(sfft_params* p, uint64_t n, uint32_t k, uint32_t mode) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->n = n;
+    p->k = k;
+    p->mode = mode;
+    p->precision = SFFT_FP32;
+    p->delta = 1e-6;
+    p->alpha0 = 0.5;
+    p->bins_per_k = mode == SFFT_GENERAL ? 8.0 : 4.0;
+    p->B_min = 16;
+    p->extra_rounds = 0;
+    p->thr = 0.5;
+    p->tau_dec = 1e-4;
+    p->iso_tol = 1e-3;
+    p->gmin = 0.1;
+    p->prune = 0.5;
+    p->ref_lo = 1e-5;
+    p->ref_hi = 2e-3;
+    p->ref_tol = 0.1;
+    p->z_cap = mode == SFFT_GENERAL ? (k * 8 > 64 ? k * 8 : 64) : (k * 4 > 64 ? k * 4 : 64);
+    p->eps = 1.0;
+    p->t_regions = 0;
+    p->R_loc = mode == SFFT_GENERAL ? 7 : 5;
+    p->R_est = 5;
+    p->s = 0.25;
+    p->est_gmin = 0.25;
+}
+
+const char* sfft_status_str(sfft_status s) {
+    switch (s) {
+        case SFFT_OK: return "ok";
+        case SFFT_ERR_INVALID_ARG: return "invalid argument";
+        case SFFT_ERR_N_NOT_POW2: return "n is not a power of two in [2^6, 2^30]";
+        case SFFT_ERR_K_RANGE: return "k out of the supported range";
+        case SFFT_ERR_OOM: return "device out of memory";
+        case SFFT_ERR_CUDA: return "CUDA error";
+        case SFFT_ERR_TIMEOUT: return "timeout";
+        case SFFT_ERR_CAPACITY: return "zhat capacity exceeded";
+        case SFFT_ERR_NOT_CONVERGED: return "not converged";
+        case SFFT_ERR_BUSY: return "busy";
+    }
+    return "unknown status";
+}
+
+const char* sfft_last_error(void) { return sfft::g_last_error.c_str(); }
+
+}  // extern "C"

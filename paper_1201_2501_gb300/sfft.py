@@ -1,0 +1,271 @@
+"""ctypes binding of ``libsfft.so`` (C ABI in ``include/sfft.h``): same names, argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  There is no CPU fallback: if the library is
+missing or fails to load, the first call raises ``RuntimeError``.  PyTorch supplies device memory and
+the current stream; tensors are passed by ``data_ptr()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libsfft.so")
+
+SFFT_OK = 0
+SFFT_ERR_INVALID_ARG = 1
+SFFT_ERR_N_NOT_POW2 = 2
+SFFT_ERR_K_RANGE = 3
+SFFT_ERR_OOM = 4
+SFFT_ERR_CUDA = 5
+SFFT_ERR_TIMEOUT = 6
+SFFT_ERR_CAPACITY = 7
+SFFT_ERR_NOT_CONVERGED = 8
+SFFT_ERR_BUSY = 9
+
+SFFT_EXACT = 0
+SFFT_GENERAL = 1
+SFFT_FP32 = 0
+SFFT_FP64 = 1
+
+
+class SfftParams(ctypes.Structure):
+    """Mirror of ``sfft_params`` (include/sfft.h)."""
+
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("k", ctypes.c_uint32),
+        ("mode", ctypes.c_uint32),
+        ("precision", ctypes.c_uint32),
+        ("delta", ctypes.c_double),
+        ("alpha0", ctypes.c_double),
+        ("bins_per_k", ctypes.c_double),
+        ("B_min", ctypes.c_uint32),
+        ("extra_rounds", ctypes.c_uint32),
+        ("thr", ctypes.c_double),
+        ("tau_dec", ctypes.c_double),
+        ("iso_tol", ctypes.c_double),
+        ("gmin", ctypes.c_double),
+        ("prune", ctypes.c_double),
+        ("ref_lo", ctypes.c_double),
+        ("ref_hi", ctypes.c_double),
+        ("ref_tol", ctypes.c_double),
+        ("z_cap", ctypes.c_uint32),
+        ("eps", ctypes.c_double),
+        ("t_regions", ctypes.c_uint32),
+        ("R_loc", ctypes.c_uint32),
+        ("R_est", ctypes.c_uint32),
+        ("s", ctypes.c_double),
+        ("est_gmin", ctypes.c_double),
+    ]
+
+
+class SfftError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {sfft_status_str(status)} ({status}) {sfft_last_error()}")
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.POINTER(SfftParams)
+_vp = ctypes.c_void_p
+_u32, _u64, _i32, _dbl = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_dblp = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "sfft_params_default": (None, [_P, _u64, _u32, _u32]),
+    "sfft_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "sfft_last_error": (ctypes.c_char_p, []),
+    "sfft_plan_create": (ctypes.c_int, [_P, _u32, ctypes.POINTER(_vp)]),
+    "sfft_plan_destroy": (ctypes.c_int, [_vp]),
+    "sfft_plan_rounds": (_u32, [_vp]),
+    "sfft_plan_round_info": (ctypes.c_int, [_vp, _u32, _u64, _u32, _u32p, _dblp, _i64p, _u32p, _u64p, _u64p, _u64p]),
+    "sfft_plan_taps": (ctypes.c_int, [_vp, _u32, _dblp, _u64]),
+    "sfft_execute": (ctypes.c_int, [_vp, _vp, _u32, _u64, _vp, _vp, _vp, _u32, _vp, _vp]),
+    "sfft_execute_host": (ctypes.c_int, [_vp, _vp, _u32, _u64, _vp, _vp, _vp, _u32, _vp, _vp]),
+    "sfft_hash_to_bins": (ctypes.c_int, [_vp, _u32, _vp, _u64, _u64, _u64, _vp, _vp, _u32, _vp, _vp]),
+    "sfft_exact_decode": (ctypes.c_int, [_vp, _u32, _u64, _u64, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "sfft_philox": (ctypes.c_int, [_u32, _u32, _u32p, _u32, _vp, _vp]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def lib():
+    """Load libsfft.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1201_2501_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def sfft_status_str(status: int) -> str:
+    return lib().sfft_status_str(int(status)).decode()
+
+
+def sfft_last_error() -> str:
+    return lib().sfft_last_error().decode()
+
+
+def _check(status, what):
+    if status != SFFT_OK:
+        raise SfftError(status, what)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def sfft_params_default(n: int, k: int, mode: int = SFFT_EXACT, **over) -> SfftParams:
+    p = SfftParams()
+    lib().sfft_params_default(ctypes.byref(p), n, k, mode)
+    for key, v in over.items():
+        if not hasattr(p, key):
+            raise KeyError(key)
+        setattr(p, key, v)
+    return p
+
+
+class Plan:
+    """Owner of an ``sfft_plan`` (``sfft_plan_create`` / ``sfft_plan_destroy``)."""
+
+    def __init__(self, params: SfftParams, max_batch: int = 1):
+        self.params = params
+        self.max_batch = int(max_batch)
+        h = ctypes.c_void_p()
+        _check(lib().sfft_plan_create(ctypes.byref(params), self.max_batch, ctypes.byref(h)), "sfft_plan_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sfft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def rounds(self) -> int:
+        return int(lib().sfft_plan_rounds(self.handle))
+
+    def round_info(self, t: int, seed: int = 0, request: int = 0) -> dict:
+        B, ns = ctypes.c_uint32(), ctypes.c_uint32()
+        alpha, T = ctypes.c_double(), ctypes.c_int64()
+        shifts = (ctypes.c_uint64 * 4)()
+        sigma, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().sfft_plan_round_info(self.handle, t, seed, request, ctypes.byref(B), ctypes.byref(alpha),
+                                          ctypes.byref(T), ctypes.byref(ns), shifts, ctypes.byref(sigma),
+                                          ctypes.byref(b)), "sfft_plan_round_info")
+        return dict(B=B.value, alpha=alpha.value, T=T.value, shifts=[int(shifts[i]) for i in range(ns.value)],
+                    sigma=sigma.value, b=b.value)
+
+    def taps(self, t: int):
+        import numpy as np
+
+        T = self.round_info(t)["T"]
+        out = np.zeros(T + 1, dtype=np.float64)
+        _check(lib().sfft_plan_taps(self.handle, t, out.ctypes.data_as(_dblp), T + 1), "sfft_plan_taps")
+        return out
+
+
+def sfft_execute(plan: Plan, x, seed: int, cap: int, outputs=None, stream=None):
+    """Run the batch ``x`` (torch tensor [batch, n], complex64 or complex128 on the GPU).
+
+    Returns (idx uint32->int32 view [batch, cap], val float64 [batch, cap, 2], count int32 [batch],
+    flag int32 [batch]) as device tensors (allocated here unless ``outputs`` is given)."""
+    import torch
+
+    batch = x.shape[0] if x.dim() == 2 else 1
+    if outputs is None:
+        dev = x.device
+        outputs = (torch.empty((batch, cap), dtype=torch.int32, device=dev),
+                   torch.empty((batch, cap, 2), dtype=torch.float64, device=dev),
+                   torch.empty((batch,), dtype=torch.int32, device=dev),
+                   torch.empty((batch,), dtype=torch.int32, device=dev))
+    idx, val, count, flag = outputs
+    _check(lib().sfft_execute(plan.handle, _ptr(x), batch, seed, _stream_ptr(stream), _ptr(idx), _ptr(val), cap,
+                              _ptr(count), _ptr(flag)), "sfft_execute")
+    return outputs
+
+
+def sfft_execute_host(plan: Plan, x, seed: int, cap: int, outputs=None, stream=None):
+    """Same as sfft_execute from host (CPU, ideally pinned) tensors; returns CPU tensors."""
+    import torch
+
+    batch = x.shape[0] if x.dim() == 2 else 1
+    if outputs is None:
+        outputs = (torch.empty((batch, cap), dtype=torch.int32),
+                   torch.empty((batch, cap, 2), dtype=torch.float64),
+                   torch.empty((batch,), dtype=torch.int32),
+                   torch.empty((batch,), dtype=torch.int32))
+    idx, val, count, flag = outputs
+    _check(lib().sfft_execute_host(plan.handle, _ptr(x), batch, seed, _stream_ptr(stream), _ptr(idx), _ptr(val), cap,
+                                   _ptr(count), _ptr(flag)), "sfft_execute_host")
+    return outputs
+
+
+def sfft_hash_to_bins(plan: Plan, t: int, x, sigma: int, a: int, b: int, zidx=None, zval=None, out=None,
+                      stream=None):
+    """One HashToBins with round t's window; returns a float64 device tensor [B, 2]."""
+    import torch
+
+    B = plan.round_info(t)["B"]
+    if out is None:
+        out = torch.empty((B, 2), dtype=torch.float64, device=x.device)
+    nz = 0 if zidx is None else int(zidx.numel())
+    _check(lib().sfft_hash_to_bins(plan.handle, t, _ptr(x), sigma, a, b, _ptr(zidx), _ptr(zval), nz, _ptr(out),
+                                   _stream_ptr(stream)), "sfft_hash_to_bins")
+    return out
+
+
+def sfft_exact_decode(plan: Plan, t: int, sigma: int, b: int, u, zidx=None, stream=None):
+    """Decode of round t on device bins ``u`` (float64 [(1+L), B, 2]); returns (idx, val, count, nabove, nkept)."""
+    import torch
+
+    B = plan.round_info(t)["B"]
+    dev = u.device
+    widx = torch.empty((B,), dtype=torch.int32, device=dev)
+    wval = torch.empty((B, 2), dtype=torch.float64, device=dev)
+    aux = torch.zeros((3,), dtype=torch.int32, device=dev)
+    nz = 0 if zidx is None else int(zidx.numel())
+    _check(lib().sfft_exact_decode(plan.handle, t, sigma, b, _ptr(u), _ptr(zidx), nz, _ptr(widx), _ptr(wval),
+                                   ctypes.c_void_p(aux.data_ptr()), ctypes.c_void_p(aux.data_ptr() + 4),
+                                   ctypes.c_void_p(aux.data_ptr() + 8), _stream_ptr(stream)), "sfft_exact_decode")
+    return widx, wval, aux
+
+
+def sfft_philox(key0: int, key1: int, ctr, count: int, out, stream=None):
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    _check(lib().sfft_philox(key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF, c, count, _ptr(out), _stream_ptr(stream)),
+           "sfft_philox")
+    return out
