@@ -390,6 +390,28 @@ def context_measurements(sfft, plan, x, cap, stream, args):
     out["cufft"] = {"value": reps_c / (e0.elapsed_time(e1) / 1000), "unit": "transforms/s",
                     "what": f"cuFFT C2C forward n=2^22 complex64, batches of {chunk} (torch.fft.fft)"}
     del y
+    # ceiling of a plain random gather on this GPU: 8-byte elements at uniformly random positions of
+    # the same 8 GiB batch (torch.index_select), in 32-byte sectors per second
+    flat = x.view(-1).view(torch.int64)
+    m = 1 << 24
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    idx = torch.randint(0, flat.numel(), (m,), device="cuda", generator=gen)
+    dst = torch.empty(m, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        torch.index_select(flat, 0, idx, out=dst)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    reps_g = 10
+    for _ in range(reps_g):
+        torch.index_select(flat, 0, idx, out=dst)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1000 / reps_g
+    out["random_gather_ceiling"] = {"sectors_per_s": m / sec, "gbs_at_32B_per_sector": m * 32 / sec / 1e9,
+                                    "what": "torch.index_select of 2^24 random int64 from the 8 GiB batch; "
+                                            "includes the coalesced index read and output write"}
+    del idx, dst
     return out
 
 

@@ -77,6 +77,8 @@ typedef struct sfft_params {
     uint32_t R_est;        /* general: hashings of EstimateValues */
     double s;              /* general: vote half-width s pi */
     double est_gmin;       /* general: a hashing joins the median only if W(-o) >= est_gmin */
+    uint32_t streams;      /* a batch is split over this many internal streams (0 -> 4) so that one
+                              group's end-of-round work overlaps another group's gather */
 } sfft_params;
 
 /* Fill *p with the library defaults for (n, k, mode); precision SFFT_FP32. */

@@ -59,6 +59,11 @@ void free_plan(sfft_plan_s* pl) {
     cudaFree(pl->d_out_val);
     cudaFree(pl->d_out_count);
     cudaFree(pl->d_out_flag);
+    for (int i = 0; i < sfft_plan_s::kMaxStreams; ++i) {
+        if (pl->aux[i]) cudaStreamDestroy(pl->aux[i]);
+        if (pl->ev_join[i]) cudaEventDestroy(pl->ev_join[i]);
+    }
+    if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
     delete pl;
 }
 
@@ -87,6 +92,7 @@ ExactArgs base_args(const sfft_plan_s* pl, const ExactRound& r, uint32_t t) {
     a.taps64 = pl->d_taps64 + r.taps_off;
     a.wtab = pl->d_wtab + r.wtab_off;
     a.part = pl->d_part;
+    a.part_stride = pl->part_stride;
     a.counter = pl->d_counter;
     a.zidx = pl->d_zidx;
     a.zval = pl->d_zval;
@@ -138,6 +144,7 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
         if (r.B > maxB) maxB = r.B;
         if (1 + r.nshift > maxH) maxH = 1 + r.nshift;
     }
+    pl->part_stride = part_elems;
     pl->part_bytes = part_elems * (size_t)max_batch * (fp64 ? 16 : 8);
     cudaError_t e = cudaSuccess;
 #define SFFT_ALLOC(ptr, bytes)                                        \
@@ -176,7 +183,21 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
         return fail(e, "upload window table");
     if ((e = cudaMemset(pl->d_counter, 0, (size_t)max_batch * sizeof(uint32_t))) != cudaSuccess)
         return fail(e, "clear counters");
+    pl->nstreams = p->streams == 0 ? 4 : p->streams;
+    if (pl->nstreams > (uint32_t)sfft_plan_s::kMaxStreams) pl->nstreams = sfft_plan_s::kMaxStreams;
+    if ((e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(e, "create event");
+    for (uint32_t i = 0; i < pl->nstreams; ++i) {
+        if ((e = cudaStreamCreateWithFlags(&pl->aux[i], cudaStreamNonBlocking)) != cudaSuccess)
+            return fail(e, "create stream");
+        if ((e = cudaEventCreateWithFlags(&pl->ev_join[i], cudaEventDisableTiming)) != cudaSuccess)
+            return fail(e, "create event");
+    }
     if ((e = set_exact_smem_limit(max_smem, fp64)) != cudaSuccess) return fail(e, "shared memory limit");
+    // The gather reads one 8- or 16-byte sample per 32-byte sector at random; ask L2 not to widen
+    // its DRAM fetches beyond a sector (a per-context performance hint, ignored where unsupported).
+    cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32);
+    cudaGetLastError();
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "plan synchronise");
     *out = pl;
     return SFFT_OK;
@@ -226,19 +247,39 @@ sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64
     SFFT_CUDA(cudaMemsetAsync(plan->d_zcount, 0, batch * sizeof(uint32_t), st), "clear zhat");
     SFFT_CUDA(cudaMemsetAsync(plan->d_zflag, 0, batch * sizeof(int32_t), st), "clear flags");
     const uint32_t R = (uint32_t)plan->rounds.size();
-    for (uint32_t t = 0; t < R; ++t) {
-        const ExactRound& r = plan->rounds[t];
-        ExactArgs a = base_args(plan, r, t);
-        a.x = d_x;
-        a.seed = seed;
-        a.first_round = t == 0;
-        a.last_round = t + 1 == R;
-        a.out_idx = d_idx;
-        a.out_val = reinterpret_cast<double2*>(d_val);
-        a.out_cap = cap;
-        a.out_count = d_count;
-        a.out_flag = d_flag;
-        SFFT_CUDA(launch_exact_round(a, batch, r.smem, st, fp64), "exact round");
+    // Requests are independent, so the batch is cut into groups whose round chains run on separate
+    // streams: while one group's last requests finish a round, the others gather.  The groups fork
+    // from and join back into the caller's stream with events (capturable in a CUDA graph).
+    uint32_t groups = plan->nstreams;
+    if (groups > batch) groups = batch;
+    if (batch < 8) groups = 1;
+    if (groups > 1) {
+        SFFT_CUDA(cudaEventRecord(plan->ev_fork, st), "fork");
+        for (uint32_t g = 0; g < groups; ++g) SFFT_CUDA(cudaStreamWaitEvent(plan->aux[g], plan->ev_fork, 0), "fork");
+    }
+    for (uint32_t g = 0; g < groups; ++g) {
+        const uint32_t r0 = (uint32_t)((uint64_t)batch * g / groups);
+        const uint32_t r1 = (uint32_t)((uint64_t)batch * (g + 1) / groups);
+        cudaStream_t gs = groups > 1 ? plan->aux[g] : st;
+        for (uint32_t t = 0; t < R; ++t) {
+            const ExactRound& r = plan->rounds[t];
+            ExactArgs a = base_args(plan, r, t);
+            a.x = d_x;
+            a.seed = seed;
+            a.req_base = r0;
+            a.first_round = t == 0;
+            a.last_round = t + 1 == R;
+            a.out_idx = d_idx;
+            a.out_val = reinterpret_cast<double2*>(d_val);
+            a.out_cap = cap;
+            a.out_count = d_count;
+            a.out_flag = d_flag;
+            SFFT_CUDA(launch_exact_round(a, r1 - r0, r.smem, gs, fp64), "exact round");
+        }
+        if (groups > 1) {
+            SFFT_CUDA(cudaEventRecord(plan->ev_join[g], gs), "join");
+            SFFT_CUDA(cudaStreamWaitEvent(st, plan->ev_join[g], 0), "join");
+        }
     }
     return SFFT_OK;
 }
@@ -351,6 +392,7 @@ sfft_status sfft_exact_decode(sfft_plan plan, uint32_t t, uint64_t sigma, uint64
     a.count = d_count;
     a.nabove = d_nabove;
     a.nkept = d_nkept;
+    a.fp64 = p.precision == SFFT_FP64;
     SFFT_CUDA(launch_exact_decode(a, (cudaStream_t)stream), "exact decode");
     return SFFT_OK;
 }

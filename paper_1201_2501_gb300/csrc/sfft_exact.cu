@@ -69,8 +69,10 @@ __device__ __forceinline__ double2 mul_conj(double2 a, double2 b) {  // a * conj
 __device__ __forceinline__ void sincospi_r(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void sincospi_r(double x, double* s, double* c) { sincospi(x, s, c); }
 
-__device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldg(p); }
-__device__ __forceinline__ double2 ldg_c(const double2* p) { return __ldg(p); }
+// Sample loads are cached in L2 only: the sigma-strided gather touches one 32-byte sector per sample
+// and an L1 fill would fetch the whole 128-byte line.
+__device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ldg_c(const double2* p) { return __ldcg(p); }
 
 template <typename R>
 __device__ __forceinline__ const R* taps_of(const ExactArgs& a);
@@ -83,39 +85,62 @@ __device__ __forceinline__ const double* taps_of<double>(const ExactArgs& a) {
     return a.taps64;
 }
 
-// w^e = exp(-2 pi i e / n) in FP64 for an exact exponent e in [0, n)
-__device__ __forceinline__ double2 root_pow64(uint32_t e, uint32_t nmask) {
+// Precision of the decode.  Bins, subtraction sums, values and all index arithmetic are FP64.  The
+// transcendental functions (the subtraction twiddles w^{a sigma i}, phases and magnitudes) run in
+// the precision R of the data path: an FP32 bin carries ~1e-6 of accumulated rounding, so an FP32
+// atan2 or sincospi (~1e-7) adds nothing measurable, while GB300's FP64 pipe is ~1/64 of FP32.
+// Every phase the decode compares keeps a tolerance of at least tau_dec (1e-4 rad by default).
+
+// w^e = exp(-2 pi i e / n) for an exact exponent e in [0, n), evaluated in precision R
+template <typename R>
+__device__ __forceinline__ double2 root_pow(uint32_t e, uint32_t nmask) {
     const uint32_t n = nmask + 1u;
     const int64_t es = e > (nmask >> 1) ? (int64_t)e - (int64_t)n : (int64_t)e;
-    double s, c;
-    sincospi(2.0 * (double)es / (double)n, &s, &c);
-    return make_double2(c, -s);
+    R s, c;
+    sincospi_r((R)(2 * es) / (R)n, &s, &c);
+    return make_double2((double)c, -(double)s);
 }
 
-__device__ __forceinline__ double phase01(double2 z) {  // phase(z) / 2 pi in [0, 1)
-    double p = atan2(z.y, z.x) * 0.15915494309189533576888;  // 1 / (2 pi)
+// phase(z) / 2 pi in [0, 1)
+template <typename R>
+__device__ __forceinline__ double phase01(double2 z);
+template <>
+__device__ __forceinline__ double phase01<double>(double2 z) {
+    double p = atan2(z.y, z.x) * 0.15915494309189533576888;
     if (p < 0.0) p += 1.0;
     if (p >= 1.0) p -= 1.0;
     return p;
+}
+template <>
+__device__ __forceinline__ double phase01<float>(double2 z) {
+    double p = (double)atan2f((float)z.y, (float)z.x) * 0.15915494309189533576888;
+    if (p < 0.0) p += 1.0;
+    if (p >= 1.0) p -= 1.0;
+    return p;
+}
+template <typename R>
+__device__ __forceinline__ double cmag(double2 z);
+template <>
+__device__ __forceinline__ double cmag<double>(double2 z) {
+    return hypot(z.x, z.y);
+}
+template <>
+__device__ __forceinline__ double cmag<float>(double2 z) {
+    return (double)hypotf((float)z.x, (float)z.y);
 }
 
 // ------------------------------------------------------------------------------------------------
 // shared-memory layout of the finishing phase
 // ------------------------------------------------------------------------------------------------
 struct FinLayout {
-    size_t U, ent_idx, ent_bin, ent_val, bin_cnt, bin_start, bin_list, cand_idx, cand_val, key, payload, keep, scan;
+    size_t U, ent_idx, ent_bin, ent_val, ent_gain, ent_sub, bin_cnt, bin_start, bin_list, cand_idx, cand_val, srt_idx,
+        srt_val, out_idx, out_val, keep, scan;
     size_t total;
-    uint32_t M;
 };
 __host__ __device__ inline size_t fin_take(size_t* off, size_t bytes) {
     const size_t o = (*off + 15) & ~size_t(15);
     *off = o + bytes;
     return o;
-}
-__host__ __device__ inline uint32_t pow2_ge(uint32_t v) {
-    uint32_t p = 1;
-    while (p < v) p <<= 1;
-    return p;
 }
 __host__ __device__ inline FinLayout fin_layout(uint32_t B, uint32_t H, uint32_t zcap, uint32_t csize) {
     FinLayout L;
@@ -124,15 +149,18 @@ __host__ __device__ inline FinLayout fin_layout(uint32_t B, uint32_t H, uint32_t
     L.ent_idx = fin_take(&off, (size_t)zcap * 4);
     L.ent_bin = fin_take(&off, (size_t)zcap * 4);
     L.ent_val = fin_take(&off, (size_t)zcap * 16);
+    L.ent_gain = fin_take(&off, (size_t)zcap * 8);
+    L.ent_sub = fin_take(&off, (size_t)zcap * H * 16);
     L.bin_cnt = fin_take(&off, (size_t)(B + 1) * 4);
     L.bin_start = fin_take(&off, (size_t)(B + 1) * 4);
     L.bin_list = fin_take(&off, (size_t)zcap * 4);
     L.cand_idx = fin_take(&off, (size_t)B * 4);
     L.cand_val = fin_take(&off, (size_t)B * 16);
-    L.M = pow2_ge(zcap + B);
-    L.key = fin_take(&off, (size_t)L.M * 8);
-    L.payload = fin_take(&off, (size_t)L.M * 4);
-    L.keep = fin_take(&off, (size_t)L.M * 4);
+    L.srt_idx = fin_take(&off, (size_t)B * 4);
+    L.srt_val = fin_take(&off, (size_t)B * 16);
+    L.out_idx = fin_take(&off, (size_t)(zcap + B) * 4);
+    L.out_val = fin_take(&off, (size_t)(zcap + B) * 16);
+    L.keep = fin_take(&off, (size_t)(zcap + B) * 4);
     L.scan = fin_take(&off, (size_t)(kThreads + 8) * 4);
     L.total = off;
     return L;
@@ -153,19 +181,27 @@ __device__ uint32_t block_exclusive_scan(uint32_t* v, uint32_t len, uint32_t* tm
     const uint32_t b0 = min(len, tid * seg), b1 = min(len, b0 + seg);
     uint32_t sum = 0;
     for (uint32_t i = b0; i < b1; ++i) sum += v[i];
-    tmp[tid] = sum;
+    // inclusive scan of the per-thread sums: within each warp by shuffles, then across the 8 warps
+    const uint32_t lane = tid & 31u, warp = tid >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (uint32_t off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) tmp[warp] = incl;
     __syncthreads();
     if (tid == 0) {
         uint32_t run = 0;
-        for (uint32_t i = 0; i < kThreads; ++i) {
-            const uint32_t x = tmp[i];
-            tmp[i] = run;
+        for (uint32_t w = 0; w < (uint32_t)kThreads / 32u; ++w) {
+            const uint32_t x = tmp[w];
+            tmp[w] = run;
             run += x;
         }
         tmp[kThreads] = run;
     }
     __syncthreads();
-    uint32_t run = tmp[tid];
+    uint32_t run = tmp[warp] + incl - sum;
     for (uint32_t i = b0; i < b1; ++i) {
         const uint32_t x = v[i];
         v[i] = run;
@@ -176,40 +212,51 @@ __device__ uint32_t block_exclusive_scan(uint32_t* v, uint32_t len, uint32_t* tm
     return total;
 }
 
-// Ascending bitonic sort of (key, payload), M a power of two.
-__device__ void block_bitonic_sort(uint64_t* key, uint32_t* pay, uint32_t M) {
-    for (uint32_t k = 2; k <= M; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < M; i += kThreads) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const bool up = (i & k) == 0;
-                    const uint64_t a = key[i], b = key[ixj];
-                    if ((a > b) == up) {
-                        key[i] = b;
-                        key[ixj] = a;
-                        const uint32_t t = pay[i];
-                        pay[i] = pay[ixj];
-                        pay[ixj] = t;
-                    }
-                }
-            }
-            __syncthreads();
-        }
+// number of entries of the ascending array a[0..len) that are < key (lower) or <= key (upper)
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t len, uint32_t key) {
+    uint32_t lo = 0, hi = len;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
     }
+    return lo;
+}
+__device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t len, uint32_t key) {
+    uint32_t lo = 0, hi = len;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
 }
 
-// In-place radix-2 decimation-in-time FFT of B = 2^logB points held in bit-reversed order:
-// a_j <- sum_r a_r exp(-2 pi i j r / B) in natural order (Lemma "hashtobins", step 3).
+// Candidates (distinct indices, any order) sorted by index into (srt_idx, srt_val) by rank counting.
+__device__ void rank_sort(const uint32_t* idx, const double2* val, uint32_t m, uint32_t* srt_idx, double2* srt_val) {
+    for (uint32_t c = threadIdx.x; c < m; c += kThreads) {
+        const uint32_t key = idx[c];
+        uint32_t r = 0;
+        for (uint32_t q = 0; q < m; ++q) r += idx[q] < key ? 1u : 0u;
+        srt_idx[r] = key;
+        srt_val[r] = val[c];
+    }
+    __syncthreads();
+}
+
+// In-place radix-2 decimation-in-time FFTs of H rows of B = 2^logB points held in bit-reversed
+// order: a_j <- sum_r a_r exp(-2 pi i j r / B) in natural order (Lemma "hashtobins", step 3).
+// All rows advance together, one barrier per stage.
 template <typename R>
-__device__ void block_fft(typename Cx<R>::T* a, uint32_t logB) {
+__device__ void block_fft_rows(typename Cx<R>::T* a, uint32_t H, uint32_t logB) {
     using C = typename Cx<R>::T;
     const uint32_t B = 1u << logB;
+    const uint32_t halfB = B >> 1;
     for (uint32_t st = 1; st <= logB; ++st) {
         const uint32_t half = 1u << (st - 1);
-        for (uint32_t k = threadIdx.x; k < B / 2; k += kThreads) {
+        for (uint32_t idx = threadIdx.x; idx < H * halfB; idx += kThreads) {
+            const uint32_t h = idx >> (logB - 1);
+            const uint32_t k = idx & (halfB - 1);
             const uint32_t pos = k & (half - 1);
-            const uint32_t i0 = ((k >> (st - 1)) << st) + pos;
+            const uint32_t i0 = h * B + ((k >> (st - 1)) << st) + pos;
             const uint32_t i1 = i0 + half;
             R sn, cs;
             sincospi_r(-(R)pos / (R)half, &sn, &cs);
@@ -224,12 +271,13 @@ __device__ void block_fft(typename Cx<R>::T* a, uint32_t logB) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Location and estimation of one bin (NoiselessSparseFFTInner's loop body), FP64
+// Location and estimation of one bin (NoiselessSparseFFTInner's loop body)
 // ------------------------------------------------------------------------------------------------
 struct DecodeCtx {
     uint32_t n, nmask, B, Np, logNp, H;
     uint32_t sigma, sigma_inv, b, sb;
-    uint64_t shift[kMaxHash];  // shift of hashing h = l + 1 is shift[l]
+    uint32_t shift[kMaxHash];  // ladder shifts beta_l (hashing l + 1)
+    uint32_t logR[kMaxHash];   // log2(beta_l / B)
     const double* wtab;
     double thr, iso_tol, gmin, ref_lo, ref_hi, ref_tol;
 };
@@ -241,68 +289,90 @@ __device__ __forceinline__ int32_t offset_of(uint32_t p, const DecodeCtx& d, uin
     return dd > (d.nmask >> 1) ? (int32_t)((int64_t)dd - (int64_t)d.n) : (int32_t)dd;
 }
 
-// A known entry i of zhat explains the residual of bin j (re-estimation of known values).
-__device__ bool refine_known(const DecodeCtx& d, const double2* u, double mag0, uint32_t i, double2* val) {
-    const uint32_t p = (d.sigma * (i - d.b)) & d.nmask;
-    uint32_t jj;
-    const int32_t o = offset_of(p, d, &jj);
-    const double gain = d.wtab[o < 0 ? -o : o];
-    if (!(gain >= d.gmin)) return false;
-    for (uint32_t l = 0; l + 1 < d.H; ++l) {
-        if (fabs(hypot(u[l + 1].x, u[l + 1].y) - mag0) > 0.25 * mag0) return false;
-        const uint32_t e = ((uint32_t)d.shift[l] * d.sigma * i) & d.nmask;
-        const double pred = (double)e / (double)d.n;
-        double dist = fabs(phase01(mul_conj(u[0], u[l + 1])) - pred);
-        if (dist > 0.5) dist = 1.0 - dist;
-        if (!(dist * 6.283185307179586476925286766559 < d.ref_tol)) return false;
+__device__ __forceinline__ uint32_t ilog2_u32(uint32_t v) { return 31u - __clz(v); }
+
+__device__ void fill_ctx(DecodeCtx& d, uint64_t n, uint32_t nmask, uint32_t B, uint32_t logB, uint32_t H,
+                         const uint64_t* ladder, uint32_t sigma, uint32_t b, const double* wtab, double thr,
+                         double iso_tol, double gmin, double ref_lo, double ref_hi, double ref_tol) {
+    d.n = (uint32_t)n;
+    d.nmask = nmask;
+    d.B = B;
+    d.Np = (uint32_t)(n >> logB);
+    d.logNp = ilog2_u32(d.Np);
+    d.H = H;
+    d.sigma = sigma;
+    d.sigma_inv = inverse_odd(sigma) & nmask;
+    d.b = b;
+    d.sb = (sigma * b) & nmask;
+    for (int l = 0; l < kMaxHash; ++l) {
+        d.shift[l] = (uint32_t)ladder[l];
+        d.logR[l] = ladder[l] >= B ? ilog2_u32((uint32_t)(ladder[l] / B)) : 0u;
     }
-    *val = make_double2(u[0].x / gain, u[0].y / gain);
-    return true;
+    d.wtab = wtab;
+    d.thr = thr;
+    d.iso_tol = iso_tol;
+    d.gmin = gmin;
+    d.ref_lo = ref_lo;
+    d.ref_hi = ref_hi;
+    d.ref_tol = ref_tol;
 }
 
 // Returns 0 (nothing), 1 (a decode of J kept) or 2 (a re-estimate of a known entry).
-// *above is set when |u_0| > thr.  The zhat entries hashed to bin j are ent_idx[list[0..nbin)].
+// *above is set when |u_0| > thr.  The zhat entries hashed to bin j are list[0..nbin) (entry ids),
+// with indices ent_idx[] and window gains ent_gain[].
+template <typename R>
 __device__ int decode_bin(const DecodeCtx& d, uint32_t j, const double2* u, const uint32_t* list, uint32_t nbin,
-                          const uint32_t* ent_idx, uint32_t* oi, double2* ov, bool* above) {
-    const double mag0 = hypot(u[0].x, u[0].y);
+                          const uint32_t* ent_idx, const double* ent_gain, uint32_t* oi, double2* ov, bool* above) {
+    const double mag0 = cmag<R>(u[0]);
+    const uint32_t L = d.H - 1;
     *above = false;
     if (!(mag0 > d.thr)) {
-        if (nbin > 0 && mag0 > d.ref_lo * d.thr && mag0 <= d.ref_hi * d.thr) {
-            uint32_t matches = 0, who = 0;
-            double2 val = make_double2(0.0, 0.0);
-            for (uint32_t e = 0; e < nbin; ++e) {
-                double2 v;
-                const uint32_t i = ent_idx[list[e]];
-                if (refine_known(d, u, mag0, i, &v)) {
-                    ++matches;
-                    who = i;
-                    val = v;
-                }
+        // re-estimation of a known value: exactly one entry of the bin must explain the residual
+        if (nbin == 0 || !(mag0 > d.ref_lo * d.thr && mag0 <= d.ref_hi * d.thr)) return 0;
+        double th[kMaxHash];
+        for (uint32_t l = 0; l < L; ++l) {
+            if (fabs(cmag<R>(u[l + 1]) - mag0) > 0.25 * mag0) return 0;
+            th[l] = phase01<R>(mul_conj(u[0], u[l + 1]));
+        }
+        uint32_t matches = 0, who = 0;
+        double gw = 1.0;
+        for (uint32_t x = 0; x < nbin; ++x) {
+            const uint32_t e = list[x];
+            const uint32_t i = ent_idx[e];
+            const double gain = ent_gain[e];
+            if (!(gain >= d.gmin)) continue;
+            bool ok = true;
+            for (uint32_t l = 0; l < L && ok; ++l) {
+                const uint32_t ph = (d.shift[l] * d.sigma * i) & d.nmask;
+                double dist = fabs(th[l] - (double)ph / (double)d.n);
+                if (dist > 0.5) dist = 1.0 - dist;
+                ok = dist * 6.283185307179586476925286766559 < d.ref_tol;
             }
-            if (matches == 1) {
-                *oi = who;
-                *ov = val;
-                return 2;
+            if (ok) {
+                ++matches;
+                who = i;
+                gw = gain;
             }
         }
-        return 0;
+        if (matches != 1) return 0;
+        *oi = who;
+        *ov = make_double2(u[0].x / gw, u[0].y / gw);
+        return 2;
     }
     *above = true;
-    // location ladder, coarsest shift first: q = sigma i mod n/B
-    const int L = (int)d.H - 1;
-    uint64_t M = (uint64_t)d.Np / (d.shift[L - 1] / d.B);
-    const double th = phase01(mul_conj(u[0], u[L]));
-    uint64_t c = (uint64_t)floor(th * (double)M + 0.5) % M;
-    for (int l = L - 2; l >= 0; --l) {
-        const uint64_t Mp = (uint64_t)d.Np / (d.shift[l] / d.B);
-        const uint64_t ratio = Mp / M;
-        const double thl = phase01(mul_conj(u[0], u[l + 1]));
-        const double y = thl * (double)Mp / (double)M - (double)c / (double)M;
-        int64_t h = (int64_t)floor(y + 0.5);
-        h %= (int64_t)ratio;
-        if (h < 0) h += (int64_t)ratio;
-        c += M * (uint64_t)h;
-        M = Mp;
+    // location ladder, coarsest shift first: q = sigma i mod n/B.  Every modulus is a power of two,
+    // so mod and division are masks and exact scalings.
+    uint32_t logM = d.logNp - d.logR[L - 1];
+    const double th = phase01<R>(mul_conj(u[0], u[L]));
+    uint64_t c = (uint64_t)(int64_t)floor(th * ldexp(1.0, (int)logM) + 0.5) & ((uint64_t(1) << logM) - 1);
+    for (int l = (int)L - 2; l >= 0; --l) {
+        const uint32_t logMp = d.logNp - d.logR[l];
+        const uint32_t logRatio = logMp - logM;
+        const double thl = phase01<R>(mul_conj(u[0], u[l + 1]));
+        const double y = thl * ldexp(1.0, (int)logRatio) - ldexp((double)c, -(int)logM);
+        const int64_t h = (int64_t)floor(y + 0.5) & (int64_t)((uint64_t(1) << logRatio) - 1);
+        c += (uint64_t(1) << logM) * (uint64_t)h;
+        logM = logMp;
     }
     const uint32_t q = (uint32_t)c;
     const uint32_t dd = (q + d.Np - (d.sb & (d.Np - 1)) + (d.Np >> 1)) & (d.Np - 1);
@@ -310,10 +380,10 @@ __device__ int decode_bin(const DecodeCtx& d, uint32_t j, const double2* u, cons
     const uint32_t p = (j * d.Np + (uint32_t)o) & d.nmask;
     const uint32_t si = (p + d.sb) & d.nmask;
     const uint32_t i = (d.sigma_inv * si) & d.nmask;
+    for (uint32_t l = 0; l < L; ++l)
+        if (fabs(cmag<R>(u[l + 1]) - mag0) > d.iso_tol * mag0) return 0;
     const double gain = d.wtab[o < 0 ? -o : o];
     if (!(gain >= d.gmin)) return 0;
-    for (uint32_t l = 0; l + 1 < d.H; ++l)
-        if (fabs(hypot(u[l + 1].x, u[l + 1].y) - mag0) > d.iso_tol * mag0) return 0;
     *oi = i;
     *ov = make_double2(u[0].x / gain, u[0].y / gain);
     return 1;
@@ -369,16 +439,17 @@ __device__ void gather_fold(const ExactArgs& a, uint32_t s, uint32_t c, uint32_t
     const uint32_t ntap = (uint32_t)(t_hi - t_lo);
     const int32_t base = (int32_t)(t_lo - (int64_t)a.a_base - (int64_t)a.maxshift);  // sample held by stage[0]
     const uint32_t cnt = ntap + a.maxshift;
-    // step 1a: gather the sigma-strided samples x_{sigma s}, s in [base, base + cnt) (8 loads in flight)
-    for (uint32_t i0 = tid; i0 < cnt; i0 += kThreads * 8) {
-        C v[8];
+    // step 1a: gather the sigma-strided samples x_{sigma s}, s in [base, base + cnt) (12 loads in flight)
+    constexpr int kInFlight = 12;
+    for (uint32_t i0 = tid; i0 < cnt; i0 += kThreads * kInFlight) {
+        C v[kInFlight];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < kInFlight; ++q) {
             const uint32_t i = i0 + (uint32_t)q * kThreads;
             if (i < cnt) v[q] = ldg_c(x + ((sigma * (uint32_t)(base + (int32_t)i)) & a.nmask));
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < kInFlight; ++q) {
             const uint32_t i = i0 + (uint32_t)q * kThreads;
             if (i < cnt) stage[i] = v[q];
         }
@@ -415,7 +486,7 @@ __device__ void gather_fold(const ExactArgs& a, uint32_t s, uint32_t c, uint32_t
         for (uint32_t h = 0; h < a.H; ++h) red[h * kThreads + tid] = acc[h];
     }
     __syncthreads();
-    C* part = reinterpret_cast<C*>(a.part) + ((size_t)s * a.chunks + c) * a.H * a.B;
+    C* part = reinterpret_cast<C*>(a.part) + (size_t)s * a.part_stride + (size_t)c * a.H * a.B;
     if (!big) {
         // residue of thread tid is (t_lo + tid) mod B; the threads of residue r are owner + m B
         for (uint32_t r = tid; r < a.B; r += kThreads) {
@@ -441,26 +512,52 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     uint32_t* ent_idx = reinterpret_cast<uint32_t*>(smem + Ly.ent_idx);
     uint32_t* ent_bin = reinterpret_cast<uint32_t*>(smem + Ly.ent_bin);
     double2* ent_val = reinterpret_cast<double2*>(smem + Ly.ent_val);
+    double* ent_gain = reinterpret_cast<double*>(smem + Ly.ent_gain);
+    double2* ent_sub = reinterpret_cast<double2*>(smem + Ly.ent_sub);
     uint32_t* bin_cnt = reinterpret_cast<uint32_t*>(smem + Ly.bin_cnt);
     uint32_t* bin_start = reinterpret_cast<uint32_t*>(smem + Ly.bin_start);
     uint32_t* bin_list = reinterpret_cast<uint32_t*>(smem + Ly.bin_list);
     uint32_t* cand_idx = reinterpret_cast<uint32_t*>(smem + Ly.cand_idx);
     double2* cand_val = reinterpret_cast<double2*>(smem + Ly.cand_val);
-    uint64_t* key = reinterpret_cast<uint64_t*>(smem + Ly.key);
-    uint32_t* pay = reinterpret_cast<uint32_t*>(smem + Ly.payload);
+    uint32_t* srt_idx = reinterpret_cast<uint32_t*>(smem + Ly.srt_idx);
+    double2* srt_val = reinterpret_cast<double2*>(smem + Ly.srt_val);
+    uint32_t* out_idx = reinterpret_cast<uint32_t*>(smem + Ly.out_idx);
+    double2* out_val = reinterpret_cast<double2*>(smem + Ly.out_val);
     uint32_t* keep = reinterpret_cast<uint32_t*>(smem + Ly.keep);
     uint32_t* scan = reinterpret_cast<uint32_t*>(smem + Ly.scan);
     __shared__ uint32_t s_nw, s_above, s_kept;
 
+    // zhat of this request and its per-entry subtraction terms (independent of the bins: done first,
+    // in parallel, so that the bin threads below only add)
+    const uint32_t nz = a.bins_only ? a.e_nz : min(a.zcount[s], a.zcap);
+    DecodeCtx d;
+    uint64_t ladder[kMaxHash];
+    for (int l = 0; l < kMaxHash; ++l) ladder[l] = l + 1 < kMaxHash ? a.shift64[l + 1] : 0;
+    fill_ctx(d, a.n, a.nmask, B, a.logB, H, ladder, sigma, b, a.wtab, a.thr, a.iso_tol, a.gmin, a.ref_lo, a.ref_hi,
+             a.ref_tol);
+    for (uint32_t e = tid; e < nz; e += kThreads) {
+        const uint32_t i = a.zidx[(size_t)s * a.zcap + e];
+        ent_idx[e] = i;
+        ent_val[e] = a.zval[(size_t)s * a.zcap + e];
+        uint32_t jb;
+        const int32_t o = offset_of((sigma * (i - b)) & a.nmask, d, &jb);
+        ent_bin[e] = jb;
+        ent_gain[e] = a.wtab[o < 0 ? -o : o];
+    }
     // step 2 (across chunks) and 3: partial folds summed in chunk order, bit-reversed, FFT
-    const C* part = reinterpret_cast<const C*>(a.part) + (size_t)s * a.chunks * H * B;
+    const C* part = reinterpret_cast<const C*>(a.part) + (size_t)s * a.part_stride;
     const uint32_t shift_br = 32u - a.logB;
     for (uint32_t i = tid; i < H * B; i += kThreads) {
         const uint32_t h = i / B, r = i - h * B;
         C sum = mkc((R)0, (R)0);
-        for (uint32_t c = 0; c < a.chunks; ++c) {
-            const C v = __ldcg(part + ((size_t)c * H + h) * B + r);
-            sum = cadd(sum, v);
+        for (uint32_t c0 = 0; c0 < a.chunks; c0 += 16) {  // 16 loads in flight, summed in chunk order
+            C v[16];
+#pragma unroll
+            for (uint32_t q = 0; q < 16; ++q)
+                if (c0 + q < a.chunks) v[q] = __ldcg(part + ((size_t)(c0 + q) * H + h) * B + r);
+#pragma unroll
+            for (uint32_t q = 0; q < 16; ++q)
+                if (c0 + q < a.chunks) sum = cadd(sum, v[q]);
         }
         U[h * B + (__brev(r) >> shift_br)] = sum;
     }
@@ -470,39 +567,15 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         s_kept = 0;
     }
     __syncthreads();
-    for (uint32_t h = 0; h < H; ++h) block_fft<R>(U + h * B, a.logB);
-
-    // zhat of this request
-    const uint32_t nz = a.bins_only ? a.e_nz : min(a.zcount[s], a.zcap);
-    DecodeCtx d;
-    d.n = (uint32_t)a.n;
-    d.nmask = a.nmask;
-    d.B = B;
-    d.Np = (uint32_t)(a.n >> a.logB);
-    d.logNp = 0;
-    while ((1u << d.logNp) < d.Np) ++d.logNp;
-    d.H = H;
-    d.sigma = sigma;
-    d.sigma_inv = inverse_odd(sigma) & a.nmask;
-    d.b = b;
-    d.sb = (sigma * b) & a.nmask;
-    for (int l = 0; l < kMaxHash; ++l) d.shift[l] = l + 1 < kMaxHash ? a.shift64[l + 1] : 0;
-    d.wtab = a.wtab;
-    d.thr = a.thr;
-    d.iso_tol = a.iso_tol;
-    d.gmin = a.gmin;
-    d.ref_lo = a.ref_lo;
-    d.ref_hi = a.ref_hi;
-    d.ref_tol = a.ref_tol;
-    for (uint32_t e = tid; e < nz; e += kThreads) {
-        const uint32_t i = a.zidx[(size_t)s * a.zcap + e];
-        ent_idx[e] = i;
-        ent_val[e] = a.zval[(size_t)s * a.zcap + e];
-        uint32_t jb;
-        offset_of((sigma * (i - b)) & a.nmask, d, &jb);
-        ent_bin[e] = jb;
+    // step 4 terms: W(-o(i)) zhat_i w^{a_h sigma i} for every (entry, hashing)
+    for (uint32_t q = tid; q < nz * H; q += kThreads) {
+        const uint32_t e = q / H, h = q - e * H;
+        const uint32_t i = ent_idx[e];
+        const double2 w = root_pow<R>(((a.a_base + a.a[h]) * sigma * i) & a.nmask, a.nmask);
+        const double2 gz = make_double2(ent_gain[e] * ent_val[e].x, ent_gain[e] * ent_val[e].y);
+        ent_sub[q] = make_double2(gz.x * w.x - gz.y * w.y, gz.x * w.y + gz.y * w.x);
     }
-    __syncthreads();
+    block_fft_rows<R>(U, H, a.logB);  // ends with a barrier
     bucket_entries(ent_bin, nz, B, bin_cnt, bin_start, bin_list, scan);
 
     // step 4 and the decode, one bin per thread
@@ -514,17 +587,9 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         }
         for (uint32_t x = bin_start[j]; x < bin_start[j + 1]; ++x) {
             const uint32_t e = bin_list[x];
-            const uint32_t i = ent_idx[e];
-            const uint32_t p = (sigma * (i - b)) & a.nmask;
-            uint32_t jb;
-            const int32_t o = offset_of(p, d, &jb);
-            const double gain = a.wtab[o < 0 ? -o : o];
-            const double2 gz = make_double2(gain * ent_val[e].x, gain * ent_val[e].y);
             for (uint32_t h = 0; h < H; ++h) {
-                const double2 w = root_pow64(((a.a_base + a.a[h]) * sigma * i) & a.nmask, a.nmask);
-                const double2 sub = make_double2(gz.x * w.x - gz.y * w.y, gz.x * w.y + gz.y * w.x);
-                u[h].x -= sub.x;
-                u[h].y -= sub.y;
+                u[h].x -= ent_sub[e * H + h].x;
+                u[h].y -= ent_sub[e * H + h].y;
             }
         }
         if (a.bins_only) {
@@ -534,8 +599,8 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         uint32_t oi = 0;
         double2 ov;
         bool above;
-        const int kind = decode_bin(d, j, u, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_idx, &oi,
-                                    &ov, &above);
+        const int kind = decode_bin<R>(d, j, u, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_idx,
+                                       ent_gain, &oi, &ov, &above);
         if (above) atomicAdd(&s_above, 1u);
         if (kind == 1) atomicAdd(&s_kept, 1u);
         if (kind != 0) {
@@ -547,71 +612,54 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     __syncthreads();
     if (a.bins_only) return;
 
-    // merge what into zhat: sort (index, source) and add equal indices (zhat first), prune
+    // merge what into zhat (NoiselessSparseFFT: zhat <- zhat + what), zhat first on equal indices,
+    // then drop entries below prune * thr
     const uint32_t nw = s_nw;
     const uint32_t tot = nz + nw;
-    const uint32_t M = pow2_ge(tot < 2 ? 2 : tot);
-    for (uint32_t p = tid; p < M; p += kThreads) {
-        if (p < nz) {
-            key[p] = ((uint64_t)ent_idx[p] << 1);
-            pay[p] = p;
-        } else if (p < tot) {
-            key[p] = ((uint64_t)cand_idx[p - nz] << 1) | 1u;
-            pay[p] = p;
-        } else {
-            key[p] = ~0ull;
-            pay[p] = 0;
-        }
+    rank_sort(cand_idx, cand_val, nw, srt_idx, srt_val);
+    for (uint32_t e = tid; e < nz; e += kThreads) {
+        const uint32_t pos = e + lower_bound_u32(srt_idx, nw, ent_idx[e]);
+        out_idx[pos] = ent_idx[e];
+        out_val[pos] = ent_val[e];
+    }
+    for (uint32_t c = tid; c < nw; c += kThreads) {
+        const uint32_t pos = c + upper_bound_u32(ent_idx, nz, srt_idx[c]);
+        out_idx[pos] = srt_idx[c];
+        out_val[pos] = srt_val[c];
     }
     __syncthreads();
-    block_bitonic_sort(key, pay, M);
     const double drop = a.prune * a.thr;
-    for (uint32_t p = tid; p < M; p += kThreads) {
+    for (uint32_t p = tid; p < tot; p += kThreads) {
         uint32_t kp = 0;
-        if (p < tot) {
-            const uint64_t idx = key[p] >> 1;
-            const bool head = p == 0 || (key[p - 1] >> 1) != idx;
-            if (head) {
-                const uint32_t q0 = pay[p];
-                double2 v = q0 < nz ? ent_val[q0] : cand_val[q0 - nz];
-                if (p + 1 < tot && (key[p + 1] >> 1) == idx) {
-                    const uint32_t q1 = pay[p + 1];
-                    const double2 w = q1 < nz ? ent_val[q1] : cand_val[q1 - nz];
-                    v.x += w.x;
-                    v.y += w.y;
-                }
-                kp = hypot(v.x, v.y) < drop ? 0u : 1u;
+        const uint32_t idx = out_idx[p];
+        if (p == 0 || out_idx[p - 1] != idx) {
+            double2 v = out_val[p];
+            if (p + 1 < tot && out_idx[p + 1] == idx) {
+                v.x += out_val[p + 1].x;
+                v.y += out_val[p + 1].y;
+                out_val[p] = v;  // the duplicate at p + 1 is never a head and is not written
             }
+            kp = cmag<R>(v) < drop ? 0u : 1u;
         }
         keep[p] = kp;
     }
     __syncthreads();
-    const uint32_t newcount = block_exclusive_scan(keep, M, scan);
-    // keep[] now holds output positions; recompute the values of kept heads and store
+    const uint32_t newcount = block_exclusive_scan(keep, tot, scan);
     uint32_t* zi = a.zidx + (size_t)s * a.zcap;
     double2* zv = a.zval + (size_t)s * a.zcap;
     const bool last = a.last_round != 0;
     for (uint32_t p = tid; p < tot; p += kThreads) {
-        const uint64_t idx = key[p] >> 1;
-        const bool head = p == 0 || (key[p - 1] >> 1) != idx;
-        if (!head) continue;
         const uint32_t pos = keep[p];  // exclusive prefix of the keep flags: kept iff the next differs
-        const uint32_t nxt = p + 1 < M ? keep[p + 1] : newcount;
+        const uint32_t nxt = p + 1 < tot ? keep[p + 1] : newcount;
         if (nxt == pos) continue;
-        const uint32_t q0 = pay[p];
-        double2 v = q0 < nz ? ent_val[q0] : cand_val[q0 - nz];
-        if (p + 1 < tot && (key[p + 1] >> 1) == idx) {
-            const uint32_t q1 = pay[p + 1];
-            const double2 w = q1 < nz ? ent_val[q1] : cand_val[q1 - nz];
-            v.x += w.x;
-            v.y += w.y;
-        }
+        const uint32_t idx = out_idx[p];
+        const double2 v = out_val[p];
         if (pos < a.zcap) {
-            zi[pos] = (uint32_t)idx;
+            zi[pos] = idx;
             zv[pos] = v;
         }
         if (last && pos < a.out_cap) {
-            a.out_idx[(size_t)s * a.out_cap + pos] = (uint32_t)idx;
+            a.out_idx[(size_t)s * a.out_cap + pos] = idx;
             a.out_val[(size_t)s * a.out_cap + pos] = v;
         }
     }
@@ -636,7 +684,7 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads, 4) k_exact_round(const ExactArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_last;
-    const uint32_t s = blockIdx.y, c = blockIdx.x;
+    const uint32_t s = a.req_base + blockIdx.y, c = blockIdx.x;
     uint32_t sigma, b;
     if (a.bins_only) {
         sigma = a.e_sigma;
@@ -659,6 +707,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_round(const ExactArgs a) 
 // ------------------------------------------------------------------------------------------------
 // decode on caller bins (single CTA)
 // ------------------------------------------------------------------------------------------------
+template <typename R>
 __global__ void __launch_bounds__(kThreads) k_exact_decode(const DecodeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_nw, s_above, s_kept;
@@ -668,41 +717,26 @@ __global__ void __launch_bounds__(kThreads) k_exact_decode(const DecodeArgs a) {
     double2* U = reinterpret_cast<double2*>(smem + Ly.U);
     uint32_t* ent_idx = reinterpret_cast<uint32_t*>(smem + Ly.ent_idx);
     uint32_t* ent_bin = reinterpret_cast<uint32_t*>(smem + Ly.ent_bin);
+    double* ent_gain = reinterpret_cast<double*>(smem + Ly.ent_gain);
     uint32_t* bin_cnt = reinterpret_cast<uint32_t*>(smem + Ly.bin_cnt);
     uint32_t* bin_start = reinterpret_cast<uint32_t*>(smem + Ly.bin_start);
     uint32_t* bin_list = reinterpret_cast<uint32_t*>(smem + Ly.bin_list);
     uint32_t* cand_idx = reinterpret_cast<uint32_t*>(smem + Ly.cand_idx);
     double2* cand_val = reinterpret_cast<double2*>(smem + Ly.cand_val);
-    uint64_t* key = reinterpret_cast<uint64_t*>(smem + Ly.key);
-    uint32_t* pay = reinterpret_cast<uint32_t*>(smem + Ly.payload);
+    uint32_t* srt_idx = reinterpret_cast<uint32_t*>(smem + Ly.srt_idx);
+    double2* srt_val = reinterpret_cast<double2*>(smem + Ly.srt_val);
     uint32_t* scan = reinterpret_cast<uint32_t*>(smem + Ly.scan);
     DecodeCtx d;
-    d.n = (uint32_t)a.n;
-    d.nmask = a.nmask;
-    d.B = B;
-    d.Np = (uint32_t)(a.n >> a.logB);
-    d.logNp = 0;
-    while ((1u << d.logNp) < d.Np) ++d.logNp;
-    d.H = a.H;
-    d.sigma = a.sigma;
-    d.sigma_inv = inverse_odd(a.sigma) & a.nmask;
-    d.b = a.b;
-    d.sb = (a.sigma * a.b) & a.nmask;
-    for (int l = 0; l < kMaxHash; ++l) d.shift[l] = a.shift64[l];
-    d.wtab = a.wtab;
-    d.thr = a.thr;
-    d.iso_tol = a.iso_tol;
-    d.gmin = a.gmin;
-    d.ref_lo = a.ref_lo;
-    d.ref_hi = a.ref_hi;
-    d.ref_tol = a.ref_tol;
+    fill_ctx(d, a.n, a.nmask, B, a.logB, a.H, a.shift64, a.sigma, a.b, a.wtab, a.thr, a.iso_tol, a.gmin, a.ref_lo,
+             a.ref_hi, a.ref_tol);
     for (uint32_t i = tid; i < a.H * B; i += kThreads) U[i] = a.u[i];
     for (uint32_t e = tid; e < a.nz; e += kThreads) {
         const uint32_t i = a.zidx[e];
         ent_idx[e] = i;
         uint32_t jb;
-        offset_of((a.sigma * (i - a.b)) & a.nmask, d, &jb);
+        const int32_t o = offset_of((a.sigma * (i - a.b)) & a.nmask, d, &jb);
         ent_bin[e] = jb;
+        ent_gain[e] = a.wtab[o < 0 ? -o : o];
     }
     if (tid == 0) {
         s_nw = 0;
@@ -717,8 +751,8 @@ __global__ void __launch_bounds__(kThreads) k_exact_decode(const DecodeArgs a) {
         uint32_t oi = 0;
         double2 ov;
         bool above;
-        const int kind = decode_bin(d, j, u, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_idx, &oi,
-                                    &ov, &above);
+        const int kind = decode_bin<R>(d, j, u, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_idx,
+                                       ent_gain, &oi, &ov, &above);
         if (above) atomicAdd(&s_above, 1u);
         if (kind == 1) atomicAdd(&s_kept, 1u);
         if (kind != 0) {
@@ -729,16 +763,10 @@ __global__ void __launch_bounds__(kThreads) k_exact_decode(const DecodeArgs a) {
     }
     __syncthreads();
     const uint32_t nw = s_nw;
-    const uint32_t M = pow2_ge(nw < 2 ? 2 : nw);
-    for (uint32_t p = tid; p < M; p += kThreads) {
-        key[p] = p < nw ? (uint64_t)cand_idx[p] : ~0ull;
-        pay[p] = p;
-    }
-    __syncthreads();
-    block_bitonic_sort(key, pay, M);
+    rank_sort(cand_idx, cand_val, nw, srt_idx, srt_val);
     for (uint32_t p = tid; p < nw; p += kThreads) {
-        a.widx[p] = (uint32_t)key[p];
-        a.wval[p] = cand_val[pay[p]];
+        a.widx[p] = srt_idx[p];
+        a.wval[p] = srt_val[p];
     }
     if (tid == 0) {
         *a.count = nw;
@@ -784,9 +812,16 @@ cudaError_t launch_exact_round(const ExactArgs& a, uint32_t batch, size_t smem, 
 
 cudaError_t launch_exact_decode(const DecodeArgs& a, cudaStream_t st) {
     const size_t smem = fin_layout(a.B, a.H, a.nz > 0 ? a.nz : 1, 16).total;
-    cudaError_t e = cudaFuncSetAttribute(k_exact_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_exact_decode<<<1, kThreads, smem, st>>>(a);
+    cudaError_t e;
+    if (a.fp64) {
+        e = cudaFuncSetAttribute(k_exact_decode<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_exact_decode<double><<<1, kThreads, smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(k_exact_decode<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_exact_decode<float><<<1, kThreads, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -208,6 +208,7 @@ void sfft_params_default(sfft_params* p, uint64_t n, uint32_t k, uint32_t mode) 
     p->R_est = 5;
     p->s = 0.25;
     p->est_gmin = 0.25;
+    p->streams = 4;
 }
 
 const char* sfft_status_str(sfft_status s) {

@@ -38,6 +38,7 @@ struct ExactArgs {
     uint32_t nmask;            // n - 1
     uint64_t seed;
     uint32_t round;
+    uint32_t req_base;         // request index of blockIdx.y == 0 (a launch may cover part of a batch)
     uint32_t B, logB;
     int64_t T;
     uint32_t H;                // hashings: hashing h uses offset a_base + a[h]
@@ -48,7 +49,9 @@ struct ExactArgs {
     const float* taps32;
     const double* taps64;
     const double* wtab;
-    void* part;                // partial fold sums [batch][chunks][H][B] complex R
+    void* part;                // partial fold sums: request s owns [s part_stride, (s + 1) part_stride),
+                               // laid out [chunks][H][B] complex R (requests may be in different rounds)
+    size_t part_stride;
     uint32_t* counter;         // [batch] arrival counters (zero between launches)
     uint32_t* zidx;            // [batch][zcap]
     double2* zval;             // [batch][zcap]
@@ -85,6 +88,7 @@ struct DecodeArgs {
     uint32_t* count;
     uint32_t* nabove;
     uint32_t* nkept;
+    int fp64;                  // transcendental precision of the decode (that of the plan's data path)
 };
 
 }  // namespace sfft
@@ -102,6 +106,7 @@ struct sfft_plan_s {
     size_t wtab_len = 0;
     void* d_part = nullptr;
     size_t part_bytes = 0;
+    size_t part_stride = 0;  // elements of the partial-fold buffer owned by one request
     uint32_t* d_counter = nullptr;
     uint32_t* d_zidx = nullptr;
     double2* d_zval = nullptr;
@@ -110,6 +115,12 @@ struct sfft_plan_s {
     // single-step helpers
     double2* d_ubins = nullptr;
     uint32_t* d_aux = nullptr;
+    // internal streams: a batch is split into groups whose rounds run on their own streams
+    static constexpr int kMaxStreams = 8;
+    uint32_t nstreams = 1;
+    cudaStream_t aux[kMaxStreams] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kMaxStreams] = {};
     // host-entry staging
     void* d_stage = nullptr;
     size_t stage_bytes = 0;

@@ -58,6 +58,7 @@ class SfftParams(ctypes.Structure):
         ("R_est", ctypes.c_uint32),
         ("s", ctypes.c_double),
         ("est_gmin", ctypes.c_double),
+        ("streams", ctypes.c_uint32),
     ]
 
 

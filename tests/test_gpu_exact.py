@@ -276,6 +276,28 @@ def test_sfft_exact_is_bit_reproducible(sf):
     plan.close()
 
 
+@pytest.mark.parametrize("streams", [2, 3, 8])
+def test_stream_groups_give_identical_results(sf, streams):
+    """Splitting a batch over internal streams (groups in different rounds at the same time) changes
+    nothing: every request's output is bit-identical to the one-stream run."""
+    n, k, batch = 1 << 18, 64, 13
+    f = exact_fields(n, k)
+    xs = [workloads.exact_sparse(n, k, 900 + i).x for i in range(batch)]
+    p1 = gpu_params(sf, f, 0)
+    p1.streams = 1
+    plan1 = sf.Plan(p1, batch)
+    ref = _run_gpu(sf, plan1, xs, 5, f["z_cap"])
+    pm = gpu_params(sf, f, 0)
+    pm.streams = streams
+    planm = sf.Plan(pm, batch)
+    for _ in range(2):
+        got = _run_gpu(sf, planm, xs, 5, f["z_cap"])
+        for ra, rb in zip(ref, got):
+            assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1]) and ra[2] == rb[2]
+    plan1.close()
+    planm.close()
+
+
 def test_edge_cases(sf):
     # zero signal: nothing found, converged
     n, k = 1 << 12, 4
