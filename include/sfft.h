@@ -175,6 +175,48 @@ sfft_status sfft_exact_decode(sfft_plan plan, uint32_t t, uint64_t sigma, uint64
                               uint32_t* d_count, uint32_t* d_nabove, uint32_t* d_nkept, void* stream);
 
 /*
+ * HashToBins for callers that cannot allocate device memory.  The paper has no counterpart: this is
+ * a deployment variant of sfft_hash_to_bins.
+ *
+ * Who needs it: code that runs where cudaMalloc / cudaFree are not allowed or not wanted -- for
+ * example a host that hands out device memory only from its own pool, a latency-critical path where
+ * an allocation's implicit synchronisation is unacceptable, or code that is handed fixed buffers and
+ * must not touch the allocator at all.  Such a caller cannot create an sfft_plan (plan creation
+ * allocates), so this call takes the window itself and keeps its scratch in a fixed array compiled
+ * into the library.
+ *
+ * What it computes: the same bins as sfft_hash_to_bins with explicit (sigma odd, a, b), FP32 data
+ * path:  u_j = FFT_B(fold_B(G_t x_{sigma(t-a)} w^{sigma b t}))_j - sum_{i in zhat} W(-o(i)) zhat_i
+ * w^{a sigma i} [h(i) = j], written to d_u as B (re, im) doubles.
+ *   d_x     n complex64 samples (interleaved float pairs), device
+ *   d_taps  T + 1 float taps g_0..g_T of the flat window (g_{-t} = g_t), device
+ *   d_wtab  n/(2B) + 1 doubles W(o), o = 0..n/(2B), the window's exact gain; read only when nz > 0
+ *           (may be NULL when nz == 0)
+ *   d_zidx, d_zval  nz recovered coefficients (uint32 indices, (re, im) doubles); nz <= 4096
+ * Every pointer is caller-owned device memory; nothing is allocated or freed.
+ *
+ * Scratch: partial fold sums and one arrival counter live in a static device array of
+ * SFFT_STATIC_SCRATCH_BYTES (4 MiB) that every GPU loading the library holds until the process
+ * exits.  A call needs ceil((2T+1) / 2048) * B * 8 + 256 bytes of it; larger requests are rejected
+ * with SFFT_ERR_CAPACITY before anything is launched.  n must be a power of two in [2^6, 2^30],
+ * B a power of two with 2 <= B <= min(n/2, 4096).
+ *
+ * All calls share the one array and it keeps the previous call's contents (the counter is cleared
+ * on the stream before every launch; the partial sums are overwritten before they are read), so two
+ * calls whose work overlaps on the GPU -- on different streams, or from different host threads --
+ * race and return wrong bins.  Serialise them.
+ *
+ * Set-up: the first call on each device (with that device current) looks up the array's device
+ * address with cudaGetSymbolAddress; make that first call before any stream capture begins.
+ * Errors: INVALID_ARG (null pointer, odd/even sigma, out-of-range a/b/B/T, nz > 4096), CAPACITY
+ * (scratch too small), CUDA (set-up or launch failed; see sfft_last_error()).
+ */
+#define SFFT_STATIC_SCRATCH_BYTES (4u * 1024u * 1024u)
+sfft_status sfft_hash_to_bins_static(uint64_t n, uint32_t B, int64_t T, const float* d_taps, const double* d_wtab,
+                                     const void* d_x, uint64_t sigma, uint64_t a, uint64_t b, const uint32_t* d_zidx,
+                                     const double* d_zval, uint32_t nz, double* d_u, void* stream);
+
+/*
  * Philox4x32-10 as the device computes it (Salmon et al., SC 2011): for i < count, the four output
  * words for key (key0, key1) and counter (ctr[0], ctr[1], ctr[2], ctr[3] + i), written to d_out[4 i..].
  */

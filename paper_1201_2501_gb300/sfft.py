@@ -92,7 +92,11 @@ _SIGS = {
     "sfft_hash_to_bins": (ctypes.c_int, [_vp, _u32, _vp, _u64, _u64, _u64, _vp, _vp, _u32, _vp, _vp]),
     "sfft_exact_decode": (ctypes.c_int, [_vp, _u32, _u64, _u64, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sfft_philox": (ctypes.c_int, [_u32, _u32, _u32p, _u32, _vp, _vp]),
+    "sfft_hash_to_bins_static": (ctypes.c_int, [_u64, _u32, ctypes.c_int64, _vp, _vp, _vp, _u64, _u64, _u64, _vp, _vp,
+                                                _u32, _vp, _vp]),
 }
+
+SFFT_STATIC_SCRATCH_BYTES = 4 * 1024 * 1024
 
 EXPORTED = tuple(_SIGS)
 
@@ -269,4 +273,18 @@ def sfft_philox(key0: int, key1: int, ctr, count: int, out, stream=None):
     c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
     _check(lib().sfft_philox(key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF, c, count, _ptr(out), _stream_ptr(stream)),
            "sfft_philox")
+    return out
+
+
+def sfft_hash_to_bins_static(n: int, B: int, T: int, taps, wtab, x, sigma: int, a: int, b: int, zidx=None, zval=None,
+                             out=None, stream=None):
+    """HashToBins that allocates nothing (``sfft_hash_to_bins_static`` in include/sfft.h).
+
+    For callers that must not call the CUDA allocator: every buffer is the caller's device tensor
+    (``taps`` float32 [T+1], ``wtab`` float64 [n/(2B)+1] or None when there is no zhat, ``x``
+    complex64 [n], ``out`` float64 [B, 2]); scratch comes from an array compiled into the library.
+    Calls that overlap on the GPU share that scratch and race: serialise them."""
+    nz = 0 if zidx is None else int(zidx.numel())
+    _check(lib().sfft_hash_to_bins_static(n, B, T, _ptr(taps), _ptr(wtab), _ptr(x), sigma, a, b, _ptr(zidx),
+                                          _ptr(zval), nz, _ptr(out), _stream_ptr(stream)), "sfft_hash_to_bins_static")
     return out
