@@ -175,6 +175,43 @@ sfft_status sfft_exact_decode(sfft_plan plan, uint32_t t, uint64_t sigma, uint64
                               uint32_t* d_count, uint32_t* d_nabove, uint32_t* d_nkept, void* stream);
 
 /*
+ * Description of general-mode round r (Algorithm 2, SparseFFT loop with B_r, k_r): B, the window
+ * half-width T, k' = 3 k_r kept by EstimateValues, LocateSignal's level count D_max (Algorithm 3),
+ * the number t of regions per level, and per level D (0-based) the integer range of beta
+ * ({s n t / 4 w_D, ..., s n t / 2 w_D} rounded inward).  beta_lo/beta_hi hold at least D_max entries.
+ * Host-only.  INVALID_ARG for an exact-mode plan.
+ */
+sfft_status sfft_plan_general_round_info(sfft_plan plan, uint32_t r, uint32_t* B, int64_t* T, uint32_t* kprime,
+                                         uint32_t* dmax, uint32_t* t_regions, uint64_t* beta_lo, uint64_t* beta_hi);
+
+/*
+ * One LocateInner level (Algorithm 3, procedure LocateInner, after its hashing loop) on caller bins,
+ * with general round r's t and the plan's s:  for every bin j with d_valid[j] and each of the nrep
+ * rounds q, c_j = phase(u_j / u'_j) (d_u, d_up: nrep x B (re, im) doubles, the hashings at a_q and
+ * a_q + beta_q), and region q' in 1..t of [l_j, l_j + w) gets a vote when the circular distance of
+ * beta_q theta_{j,q'} and c_j is below s pi.  A bin with no majority region becomes bottom
+ * (d_valid[j] = 0); otherwise l_j moves to the start of the four consecutive regions with the most
+ * votes.  Region starts d_lfp are fixed point with 16 fraction bits, modulo n 2^16; w_fp is the level's
+ * width in the same units.  d_votes receives the B x t vote counts.  B = round r's B.
+ */
+sfft_status sfft_locate_votes(sfft_plan plan, uint32_t r, uint64_t sigma, uint64_t b, uint64_t w_fp, uint32_t nrep,
+                              const uint64_t* d_beta, const double* d_u, const double* d_up, uint64_t* d_lfp,
+                              uint8_t* d_valid, uint32_t* d_votes, void* stream);
+
+/*
+ * EstimateValues (Algorithm 2, after its hashing loop) on caller bins: for each candidate i of the
+ * ascending list d_L (nL <= B), w_i = median_q Re e_q + i median_q Im e_q over the nrep hashings
+ * (sigma_q, a_q, b_q) whose window gain W(-o_q(i)) reaches est_gmin, e_q = u^{(q)}_{h_q(i)}
+ * w^{-a_q sigma_q i} / W(-o_q(i)) (lower median; 0 when no hashing qualifies); then the kprime
+ * largest |w_i| (ties to the smaller index) are written to (d_widx, d_wval) in ascending index order
+ * and their number to *d_count.  d_u: nrep x B (re, im) doubles; window of general round r.
+ */
+sfft_status sfft_estimate_from_bins(sfft_plan plan, uint32_t r, uint32_t nrep, const uint64_t* d_sigma,
+                                    const uint64_t* d_b, const uint64_t* d_a, const double* d_u, const uint32_t* d_L,
+                                    uint32_t nL, uint32_t kprime, uint32_t* d_widx, double* d_wval, uint32_t* d_count,
+                                    void* stream);
+
+/*
  * HashToBins for callers that cannot allocate device memory.  The paper has no counterpart: this is
  * a deployment variant of sfft_hash_to_bins.
  *

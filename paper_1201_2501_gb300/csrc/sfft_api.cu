@@ -59,6 +59,10 @@ void free_plan(sfft_plan_s* pl) {
     cudaFree(pl->d_out_val);
     cudaFree(pl->d_out_count);
     cudaFree(pl->d_out_flag);
+    cudaFree(pl->d_bins);
+    cudaFree(pl->d_phase);
+    cudaFree(pl->d_L);
+    cudaFree(pl->d_nL);
     for (int i = 0; i < sfft_plan_s::kMaxStreams; ++i) {
         if (pl->aux[i]) cudaStreamDestroy(pl->aux[i]);
         if (pl->ev_join[i]) cudaEventDestroy(pl->ev_join[i]);
@@ -119,13 +123,14 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
     sfft_status st = validate(p);
     if (st != SFFT_OK) return st;
     if (max_batch == 0) return SFFT_ERR_INVALID_ARG;
-    if (p->mode != SFFT_EXACT) return SFFT_ERR_INVALID_ARG;  // the general mode has its own plan path
+    const bool general = p->mode == SFFT_GENERAL;
+    if (general && p->precision != SFFT_FP32) return SFFT_ERR_INVALID_ARG;  // general mode: FP32 data path
     sfft_plan_s* pl = new (std::nothrow) sfft_plan_s();
     if (!pl) return SFFT_ERR_OOM;
     pl->p = *p;
     pl->max_batch = max_batch;
     cudaGetDevice(&pl->device);
-    st = build_exact_schedule(pl);
+    st = general ? build_general_schedule(pl) : build_exact_schedule(pl);
     if (st != SFFT_OK) {
         free_plan(pl);
         return st;
@@ -135,14 +140,24 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
     const size_t ntaps = pl->taps_host.size();
     std::vector<float> t32(ntaps);
     for (size_t i = 0; i < ntaps; ++i) t32[i] = (float)pl->taps_host[i];
-    size_t part_elems = 0, max_smem = 0;
-    uint32_t maxB = 0, maxH = 0;
+    size_t part_elems = 0, max_smem = 0, gs_max = 0, fs_max = 0, ls_max = 0, es_max = 0;
+    uint32_t maxB = 0;
     for (const ExactRound& r : pl->rounds) {
         const size_t e = (size_t)r.chunks * (1 + r.nshift) * r.B;
         if (e > part_elems) part_elems = e;
         if (r.smem > max_smem) max_smem = r.smem;
         if (r.B > maxB) maxB = r.B;
-        if (1 + r.nshift > maxH) maxH = 1 + r.nshift;
+    }
+    for (const GeneralRound& r : pl->grounds) {
+        const size_t e = (size_t)r.ngroups * r.ctas * 2 * r.B;
+        if (e > part_elems) part_elems = e;
+        if ((size_t)r.nhash * r.B > pl->bins_stride) pl->bins_stride = (size_t)r.nhash * r.B;
+        if ((size_t)r.npairs * r.B > pl->phase_stride) pl->phase_stride = (size_t)r.npairs * r.B;
+        if (r.B > maxB) maxB = r.B;
+        gs_max = r.smem_gather > gs_max ? r.smem_gather : gs_max;
+        fs_max = r.smem_finish > fs_max ? r.smem_finish : fs_max;
+        ls_max = r.smem_locate > ls_max ? r.smem_locate : ls_max;
+        es_max = r.smem_estimate > es_max ? r.smem_estimate : es_max;
     }
     pl->part_stride = part_elems;
     pl->part_bytes = part_elems * (size_t)max_batch * (fp64 ? 16 : 8);
@@ -167,6 +182,12 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
     SFFT_ALLOC(pl->d_zflag, (size_t)max_batch * sizeof(int32_t));
     SFFT_ALLOC(pl->d_ubins, (size_t)maxB * kMaxHash * sizeof(double2));
     SFFT_ALLOC(pl->d_aux, 64 * sizeof(uint32_t));
+    if (general) {
+        SFFT_ALLOC(pl->d_bins, pl->bins_stride * max_batch * sizeof(double2));
+        SFFT_ALLOC(pl->d_phase, pl->phase_stride * max_batch * sizeof(double));
+        SFFT_ALLOC(pl->d_L, (size_t)maxB * max_batch * sizeof(uint32_t));
+        SFFT_ALLOC(pl->d_nL, (size_t)max_batch * sizeof(uint32_t));
+    }
 #undef SFFT_ALLOC
     auto fail = [&](cudaError_t err, const char* what) {
         set_last_error(std::string(what) + ": " + cudaGetErrorString(err));
@@ -193,7 +214,9 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
         if ((e = cudaEventCreateWithFlags(&pl->ev_join[i], cudaEventDisableTiming)) != cudaSuccess)
             return fail(e, "create event");
     }
-    if ((e = set_exact_smem_limit(max_smem, fp64)) != cudaSuccess) return fail(e, "shared memory limit");
+    if (!general && (e = set_exact_smem_limit(max_smem, fp64)) != cudaSuccess) return fail(e, "shared memory limit");
+    if (general && (e = general_set_smem(gs_max, fs_max, ls_max, es_max)) != cudaSuccess)
+        return fail(e, "shared memory limit");
     // The gather reads one 8- or 16-byte sample per 32-byte sector at random; ask L2 not to widen
     // its DRAM fetches beyond a sector (a per-context performance hint, ignored where unsupported).
     cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32);
@@ -210,7 +233,26 @@ sfft_status sfft_plan_destroy(sfft_plan plan) {
     return SFFT_OK;
 }
 
-uint32_t sfft_plan_rounds(sfft_plan plan) { return plan ? (uint32_t)plan->rounds.size() : 0; }
+uint32_t sfft_plan_rounds(sfft_plan plan) {
+    if (!plan) return 0;
+    return plan->p.mode == SFFT_GENERAL ? (uint32_t)plan->grounds.size() : (uint32_t)plan->rounds.size();
+}
+
+sfft_status sfft_plan_general_round_info(sfft_plan plan, uint32_t r, uint32_t* B, int64_t* T, uint32_t* kprime,
+                                         uint32_t* dmax, uint32_t* t_regions, uint64_t* beta_lo, uint64_t* beta_hi) {
+    if (!plan || plan->p.mode != SFFT_GENERAL || r >= plan->grounds.size()) return SFFT_ERR_INVALID_ARG;
+    const GeneralRound& g = plan->grounds[r];
+    if (B) *B = g.B;
+    if (T) *T = g.T;
+    if (kprime) *kprime = g.kprime;
+    if (dmax) *dmax = g.dmax;
+    if (t_regions) *t_regions = g.t;
+    for (uint32_t D = 0; D < g.dmax; ++D) {
+        if (beta_lo) beta_lo[D] = g.beta_lo[D];
+        if (beta_hi) beta_hi[D] = g.beta_hi[D];
+    }
+    return SFFT_OK;
+}
 
 sfft_status sfft_plan_round_info(sfft_plan plan, uint32_t t, uint64_t seed, uint32_t request, uint32_t* B,
                                  double* alpha, int64_t* T, uint32_t* nshift, uint64_t* shifts, uint64_t* sigma,
@@ -231,10 +273,90 @@ sfft_status sfft_plan_round_info(sfft_plan plan, uint32_t t, uint64_t seed, uint
 }
 
 sfft_status sfft_plan_taps(sfft_plan plan, uint32_t t, double* h_taps, uint64_t cap) {
-    if (!plan || !h_taps || t >= plan->rounds.size()) return SFFT_ERR_INVALID_ARG;
-    const ExactRound& r = plan->rounds[t];
-    if (cap < (uint64_t)r.T + 1) return SFFT_ERR_INVALID_ARG;
-    std::memcpy(h_taps, plan->taps_host.data() + r.taps_off, sizeof(double) * ((size_t)r.T + 1));
+    if (!plan || !h_taps || t >= sfft_plan_rounds(plan)) return SFFT_ERR_INVALID_ARG;
+    const bool general = plan->p.mode == SFFT_GENERAL;
+    const int64_t T = general ? plan->grounds[t].T : plan->rounds[t].T;
+    const size_t off = general ? plan->grounds[t].taps_off : plan->rounds[t].taps_off;
+    if (cap < (uint64_t)T + 1) return SFFT_ERR_INVALID_ARG;
+    std::memcpy(h_taps, plan->taps_host.data() + off, sizeof(double) * ((size_t)T + 1));
+    return SFFT_OK;
+}
+
+static sfft_status execute_general(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, cudaStream_t st,
+                                   uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag) {
+    const sfft_params& p = plan->p;
+    SFFT_CUDA(cudaMemsetAsync(plan->d_zcount, 0, batch * sizeof(uint32_t), st), "clear zhat");
+    SFFT_CUDA(cudaMemsetAsync(plan->d_zflag, 0, batch * sizeof(int32_t), st), "clear flags");
+    const uint32_t R = (uint32_t)plan->grounds.size();
+    uint32_t groups = plan->nstreams;
+    if (groups > batch) groups = batch;
+    if (groups > 1) {
+        SFFT_CUDA(cudaEventRecord(plan->ev_fork, st), "fork");
+        for (uint32_t g = 0; g < groups; ++g) SFFT_CUDA(cudaStreamWaitEvent(plan->aux[g], plan->ev_fork, 0), "fork");
+    }
+    for (uint32_t g = 0; g < groups; ++g) {
+        const uint32_t r0 = (uint32_t)((uint64_t)batch * g / groups);
+        const uint32_t r1 = (uint32_t)((uint64_t)batch * (g + 1) / groups);
+        cudaStream_t gs = groups > 1 ? plan->aux[g] : st;
+        for (uint32_t r = 0; r < R; ++r) {
+            const GeneralRound& gr = plan->grounds[r];
+            GenArgs a;
+            std::memset(&a, 0, sizeof(a));
+            a.x = reinterpret_cast<const float2*>(d_x);
+            a.n = p.n;
+            a.nmask = (uint32_t)(p.n - 1);
+            a.seed = seed;
+            a.round = r;
+            a.req_base = r0;
+            a.B = gr.B;
+            a.logB = gr.logB;
+            a.T = gr.T;
+            a.chunks = gr.chunks;
+            a.cpb = gr.cpb;
+            a.ctas = gr.ctas;
+            a.dmax = gr.dmax;
+            a.t = gr.t;
+            a.logtp = gr.logtp;
+            a.R_loc = p.R_loc;
+            a.R_est = p.R_est;
+            a.npairs = gr.npairs;
+            a.ngroups = gr.ngroups;
+            a.nhash = gr.nhash;
+            a.kprime = gr.kprime;
+            for (uint32_t D = 0; D < gr.dmax; ++D) {
+                a.beta_lo[D] = gr.beta_lo[D];
+                a.beta_hi[D] = gr.beta_hi[D];
+            }
+            a.s = p.s;
+            a.est_gmin = p.est_gmin;
+            a.taps = plan->d_taps32 + gr.taps_off;
+            a.wtab = plan->d_wtab + gr.wtab_off;
+            a.part = reinterpret_cast<float2*>(plan->d_part);
+            a.part_stride = plan->part_stride;
+            a.bins = plan->d_bins;
+            a.phase = plan->d_phase;
+            a.bins_stride = plan->bins_stride;
+            a.phase_stride = plan->phase_stride;
+            a.L = plan->d_L;
+            a.nL = plan->d_nL;
+            a.zidx = plan->d_zidx;
+            a.zval = plan->d_zval;
+            a.zcount = plan->d_zcount;
+            a.zflag = plan->d_zflag;
+            a.zcap = p.z_cap;
+            a.last_round = r + 1 == R;
+            a.out_idx = d_idx;
+            a.out_val = reinterpret_cast<double2*>(d_val);
+            a.out_cap = cap;
+            a.out_count = d_count;
+            a.out_flag = d_flag;
+            SFFT_CUDA(launch_general_round(a, r1 - r0, gr, gs), "general round");
+        }
+        if (groups > 1) {
+            SFFT_CUDA(cudaEventRecord(plan->ev_join[g], gs), "join");
+            SFFT_CUDA(cudaStreamWaitEvent(st, plan->ev_join[g], 0), "join");
+        }
+    }
     return SFFT_OK;
 }
 
@@ -243,6 +365,7 @@ sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64
     if (!plan || !d_x || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
     if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    if (plan->p.mode == SFFT_GENERAL) return execute_general(plan, d_x, batch, seed, st, d_idx, d_val, cap, d_count, d_flag);
     const bool fp64 = plan->p.precision == SFFT_FP64;
     SFFT_CUDA(cudaMemsetAsync(plan->d_zcount, 0, batch * sizeof(uint32_t), st), "clear zhat");
     SFFT_CUDA(cudaMemsetAsync(plan->d_zflag, 0, batch * sizeof(int32_t), st), "clear flags");
@@ -402,6 +525,66 @@ sfft_status sfft_philox(uint32_t key0, uint32_t key1, const uint32_t* h_ctr, uin
     if (!h_ctr || (!d_out && count)) return SFFT_ERR_INVALID_ARG;
     SFFT_CUDA(launch_philox(key0, key1, h_ctr[0], h_ctr[1], h_ctr[2], h_ctr[3], count, d_out, (cudaStream_t)stream),
               "philox");
+    return SFFT_OK;
+}
+
+sfft_status sfft_locate_votes(sfft_plan plan, uint32_t r, uint64_t sigma, uint64_t b, uint64_t w_fp, uint32_t nrep,
+                              const uint64_t* d_beta, const double* d_u, const double* d_up, uint64_t* d_lfp,
+                              uint8_t* d_valid, uint32_t* d_votes, void* stream) {
+    if (!plan || plan->p.mode != SFFT_GENERAL || r >= plan->grounds.size()) return SFFT_ERR_INVALID_ARG;
+    if (!d_beta || !d_u || !d_up || !d_lfp || !d_valid || !d_votes || nrep == 0 || nrep > (uint32_t)kMaxRloc)
+        return SFFT_ERR_INVALID_ARG;
+    if (!(sigma & 1) || sigma >= plan->p.n || b >= plan->p.n) return SFFT_ERR_INVALID_ARG;
+    const GeneralRound& g = plan->grounds[r];
+    VoteArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n = plan->p.n;
+    a.nmask = (uint32_t)(plan->p.n - 1);
+    a.B = g.B;
+    a.t = g.t;
+    a.nrep = nrep;
+    a.sigma = (uint32_t)sigma;
+    a.b = (uint32_t)b;
+    a.w_fp = w_fp;
+    a.s = plan->p.s;
+    a.u = reinterpret_cast<const double2*>(d_u);
+    a.up = reinterpret_cast<const double2*>(d_up);
+    a.beta = d_beta;
+    a.l_fp = d_lfp;
+    a.valid = d_valid;
+    a.votes = d_votes;
+    SFFT_CUDA(launch_locate_votes(a, (cudaStream_t)stream), "locate votes");
+    return SFFT_OK;
+}
+
+sfft_status sfft_estimate_from_bins(sfft_plan plan, uint32_t r, uint32_t nrep, const uint64_t* d_sigma,
+                                    const uint64_t* d_b, const uint64_t* d_a, const double* d_u, const uint32_t* d_L,
+                                    uint32_t nL, uint32_t kprime, uint32_t* d_widx, double* d_wval, uint32_t* d_count,
+                                    void* stream) {
+    if (!plan || plan->p.mode != SFFT_GENERAL || r >= plan->grounds.size()) return SFFT_ERR_INVALID_ARG;
+    if (!d_sigma || !d_b || !d_a || !d_u || (nL > 0 && !d_L) || !d_widx || !d_wval || !d_count) return SFFT_ERR_INVALID_ARG;
+    if (nrep == 0 || nrep > (uint32_t)kMaxRest || nL > plan->grounds[r].B) return SFFT_ERR_INVALID_ARG;
+    const GeneralRound& g = plan->grounds[r];
+    EstArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n = plan->p.n;
+    a.nmask = (uint32_t)(plan->p.n - 1);
+    a.B = g.B;
+    a.logB = g.logB;
+    a.nrep = nrep;
+    a.nL = nL;
+    a.kprime = kprime;
+    a.sig = d_sigma;
+    a.bb = d_b;
+    a.aa = d_a;
+    a.u = reinterpret_cast<const double2*>(d_u);
+    a.L = d_L;
+    a.wtab = plan->d_wtab + g.wtab_off;
+    a.est_gmin = plan->p.est_gmin;
+    a.widx = d_widx;
+    a.wval = reinterpret_cast<double2*>(d_wval);
+    a.count = d_count;
+    SFFT_CUDA(launch_estimate_from_bins(a, (cudaStream_t)stream), "estimate from bins");
     return SFFT_OK;
 }
 

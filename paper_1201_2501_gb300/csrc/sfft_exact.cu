@@ -15,64 +15,10 @@
 #include <stdint.h>
 
 #include "philox.cuh"
+#include "sfft_device.cuh"
 #include "sfft_internal.h"
 
 namespace sfft {
-
-// ------------------------------------------------------------------------------------------------
-// complex helpers
-// ------------------------------------------------------------------------------------------------
-template <typename R>
-struct Cx;
-template <>
-struct Cx<float> {
-    using T = float2;
-};
-template <>
-struct Cx<double> {
-    using T = double2;
-};
-
-__device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
-template <typename C>
-__device__ __forceinline__ C cadd(C a, C b) {
-    a.x += b.x;
-    a.y += b.y;
-    return a;
-}
-template <typename C>
-__device__ __forceinline__ C csub(C a, C b) {
-    a.x -= b.x;
-    a.y -= b.y;
-    return a;
-}
-template <typename C>
-__device__ __forceinline__ C cmul(C a, C b) {
-    C r;
-    r.x = a.x * b.x - a.y * b.y;
-    r.y = a.x * b.y + a.y * b.x;
-    return r;
-}
-// acc + a * b
-template <typename C>
-__device__ __forceinline__ C cfma(C a, C b, C acc) {
-    acc.x = fma(a.x, b.x, acc.x);
-    acc.x = fma(-a.y, b.y, acc.x);
-    acc.y = fma(a.x, b.y, acc.y);
-    acc.y = fma(a.y, b.x, acc.y);
-    return acc;
-}
-__device__ __forceinline__ double2 mul_conj(double2 a, double2 b) {  // a * conj(b)
-    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
-__device__ __forceinline__ void sincospi_r(float x, float* s, float* c) { sincospif(x, s, c); }
-__device__ __forceinline__ void sincospi_r(double x, double* s, double* c) { sincospi(x, s, c); }
-
-// Sample loads are cached in L2 only: the sigma-strided gather touches one 32-byte sector per sample
-// and an L1 fill would fetch the whole 128-byte line.
-__device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldcg(p); }
-__device__ __forceinline__ double2 ldg_c(const double2* p) { return __ldcg(p); }
 
 template <typename R>
 __device__ __forceinline__ const R* taps_of(const ExactArgs& a);
@@ -83,50 +29,6 @@ __device__ __forceinline__ const float* taps_of<float>(const ExactArgs& a) {
 template <>
 __device__ __forceinline__ const double* taps_of<double>(const ExactArgs& a) {
     return a.taps64;
-}
-
-// Precision of the decode.  Bins, subtraction sums, values and all index arithmetic are FP64.  The
-// transcendental functions (the subtraction twiddles w^{a sigma i}, phases and magnitudes) run in
-// the precision R of the data path: an FP32 bin carries ~1e-6 of accumulated rounding, so an FP32
-// atan2 or sincospi (~1e-7) adds nothing measurable, while GB300's FP64 pipe is ~1/64 of FP32.
-// Every phase the decode compares keeps a tolerance of at least tau_dec (1e-4 rad by default).
-
-// w^e = exp(-2 pi i e / n) for an exact exponent e in [0, n), evaluated in precision R
-template <typename R>
-__device__ __forceinline__ double2 root_pow(uint32_t e, uint32_t nmask) {
-    const uint32_t n = nmask + 1u;
-    const int64_t es = e > (nmask >> 1) ? (int64_t)e - (int64_t)n : (int64_t)e;
-    R s, c;
-    sincospi_r((R)(2 * es) / (R)n, &s, &c);
-    return make_double2((double)c, -(double)s);
-}
-
-// phase(z) / 2 pi in [0, 1)
-template <typename R>
-__device__ __forceinline__ double phase01(double2 z);
-template <>
-__device__ __forceinline__ double phase01<double>(double2 z) {
-    double p = atan2(z.y, z.x) * 0.15915494309189533576888;
-    if (p < 0.0) p += 1.0;
-    if (p >= 1.0) p -= 1.0;
-    return p;
-}
-template <>
-__device__ __forceinline__ double phase01<float>(double2 z) {
-    double p = (double)atan2f((float)z.y, (float)z.x) * 0.15915494309189533576888;
-    if (p < 0.0) p += 1.0;
-    if (p >= 1.0) p -= 1.0;
-    return p;
-}
-template <typename R>
-__device__ __forceinline__ double cmag(double2 z);
-template <>
-__device__ __forceinline__ double cmag<double>(double2 z) {
-    return hypot(z.x, z.y);
-}
-template <>
-__device__ __forceinline__ double cmag<float>(double2 z) {
-    return (double)hypotf((float)z.x, (float)z.y);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -172,105 +74,6 @@ size_t exact_finish_smem(uint32_t B, uint32_t H, uint32_t zcap, bool fp64) {
 size_t exact_gather_smem(uint32_t stage, bool fp64) { return (size_t)stage * (fp64 ? 16 : 8); }
 
 // ------------------------------------------------------------------------------------------------
-// block-wide helpers (kThreads threads)
-// ------------------------------------------------------------------------------------------------
-// Exclusive prefix sum of v[0..len) in place; returns the total.  tmp holds kThreads + 1 words.
-__device__ uint32_t block_exclusive_scan(uint32_t* v, uint32_t len, uint32_t* tmp) {
-    const uint32_t tid = threadIdx.x;
-    const uint32_t seg = (len + kThreads - 1) / kThreads;
-    const uint32_t b0 = min(len, tid * seg), b1 = min(len, b0 + seg);
-    uint32_t sum = 0;
-    for (uint32_t i = b0; i < b1; ++i) sum += v[i];
-    // inclusive scan of the per-thread sums: within each warp by shuffles, then across the 8 warps
-    const uint32_t lane = tid & 31u, warp = tid >> 5;
-    uint32_t incl = sum;
-#pragma unroll
-    for (uint32_t off = 1; off < 32; off <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += y;
-    }
-    if (lane == 31) tmp[warp] = incl;
-    __syncthreads();
-    if (tid == 0) {
-        uint32_t run = 0;
-        for (uint32_t w = 0; w < (uint32_t)kThreads / 32u; ++w) {
-            const uint32_t x = tmp[w];
-            tmp[w] = run;
-            run += x;
-        }
-        tmp[kThreads] = run;
-    }
-    __syncthreads();
-    uint32_t run = tmp[warp] + incl - sum;
-    for (uint32_t i = b0; i < b1; ++i) {
-        const uint32_t x = v[i];
-        v[i] = run;
-        run += x;
-    }
-    const uint32_t total = tmp[kThreads];
-    __syncthreads();
-    return total;
-}
-
-// number of entries of the ascending array a[0..len) that are < key (lower) or <= key (upper)
-__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t len, uint32_t key) {
-    uint32_t lo = 0, hi = len;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (a[mid] < key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-__device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t len, uint32_t key) {
-    uint32_t lo = 0, hi = len;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (a[mid] <= key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// Candidates (distinct indices, any order) sorted by index into (srt_idx, srt_val) by rank counting.
-__device__ void rank_sort(const uint32_t* idx, const double2* val, uint32_t m, uint32_t* srt_idx, double2* srt_val) {
-    for (uint32_t c = threadIdx.x; c < m; c += kThreads) {
-        const uint32_t key = idx[c];
-        uint32_t r = 0;
-        for (uint32_t q = 0; q < m; ++q) r += idx[q] < key ? 1u : 0u;
-        srt_idx[r] = key;
-        srt_val[r] = val[c];
-    }
-    __syncthreads();
-}
-
-// In-place radix-2 decimation-in-time FFTs of H rows of B = 2^logB points held in bit-reversed
-// order: a_j <- sum_r a_r exp(-2 pi i j r / B) in natural order (Lemma "hashtobins", step 3).
-// All rows advance together, one barrier per stage.
-template <typename R>
-__device__ void block_fft_rows(typename Cx<R>::T* a, uint32_t H, uint32_t logB) {
-    using C = typename Cx<R>::T;
-    const uint32_t B = 1u << logB;
-    const uint32_t halfB = B >> 1;
-    for (uint32_t st = 1; st <= logB; ++st) {
-        const uint32_t half = 1u << (st - 1);
-        for (uint32_t idx = threadIdx.x; idx < H * halfB; idx += kThreads) {
-            const uint32_t h = idx >> (logB - 1);
-            const uint32_t k = idx & (halfB - 1);
-            const uint32_t pos = k & (half - 1);
-            const uint32_t i0 = h * B + ((k >> (st - 1)) << st) + pos;
-            const uint32_t i1 = i0 + half;
-            R sn, cs;
-            sincospi_r(-(R)pos / (R)half, &sn, &cs);
-            const C w = mkc(cs, sn);
-            const C bv = cmul(a[i1], w);
-            const C av = a[i0];
-            a[i0] = cadd(av, bv);
-            a[i1] = csub(av, bv);
-        }
-        __syncthreads();
-    }
-}
-
-// ------------------------------------------------------------------------------------------------
 // Location and estimation of one bin (NoiselessSparseFFTInner's loop body)
 // ------------------------------------------------------------------------------------------------
 struct DecodeCtx {
@@ -288,8 +91,6 @@ __device__ __forceinline__ int32_t offset_of(uint32_t p, const DecodeCtx& d, uin
     *jbin = jj;
     return dd > (d.nmask >> 1) ? (int32_t)((int64_t)dd - (int64_t)d.n) : (int32_t)dd;
 }
-
-__device__ __forceinline__ uint32_t ilog2_u32(uint32_t v) { return 31u - __clz(v); }
 
 __device__ void fill_ctx(DecodeCtx& d, uint64_t n, uint32_t nmask, uint32_t B, uint32_t logB, uint32_t H,
                          const uint64_t* ladder, uint32_t sigma, uint32_t b, const double* wtab, double thr,
@@ -387,39 +188,6 @@ __device__ int decode_bin(const DecodeCtx& d, uint32_t j, const double2* u, cons
     *oi = i;
     *ov = make_double2(u[0].x / gain, u[0].y / gain);
     return 1;
-}
-
-// Bucket the nz entries of zhat by bin: bin_start[B+1] (exclusive prefix), bin_list (entry ids of
-// each bin, ascending).  ent_bin must be filled.
-__device__ void bucket_entries(const uint32_t* ent_bin, uint32_t nz, uint32_t B, uint32_t* bin_cnt,
-                               uint32_t* bin_start, uint32_t* bin_list, uint32_t* scan_tmp) {
-    for (uint32_t j = threadIdx.x; j <= B; j += kThreads) bin_cnt[j] = 0;
-    __syncthreads();
-    for (uint32_t e = threadIdx.x; e < nz; e += kThreads) atomicAdd(&bin_cnt[ent_bin[e]], 1u);
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j <= B; j += kThreads) bin_start[j] = bin_cnt[j];
-    __syncthreads();
-    block_exclusive_scan(bin_start, B + 1, scan_tmp);
-    for (uint32_t j = threadIdx.x; j <= B; j += kThreads) bin_cnt[j] = bin_start[j];  // fill cursor
-    __syncthreads();
-    for (uint32_t e = threadIdx.x; e < nz; e += kThreads) {
-        const uint32_t slot = atomicAdd(&bin_cnt[ent_bin[e]], 1u);
-        bin_list[slot] = e;
-    }
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < B; j += kThreads) {  // insertion sort of each (short) bin list
-        const uint32_t b0 = bin_start[j], b1 = bin_start[j + 1];
-        for (uint32_t x = b0 + 1; x < b1; ++x) {
-            const uint32_t v = bin_list[x];
-            uint32_t y = x;
-            while (y > b0 && bin_list[y - 1] > v) {
-                bin_list[y] = bin_list[y - 1];
-                --y;
-            }
-            bin_list[y] = v;
-        }
-    }
-    __syncthreads();
 }
 
 // ------------------------------------------------------------------------------------------------

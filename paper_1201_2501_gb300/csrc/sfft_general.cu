@@ -1,0 +1,721 @@
+// sfft_general.cu -- the general-case sparse FFT on sm_103a (Algorithms 2 and 3 of Hassanieh, Indyk,
+// Katabi, Price): SparseFFT's rounds of LocateSignal (LocateInner votes over D_max levels) and
+// EstimateValues (medians over R_est hashings, top-k'), for a batch of requests.
+//
+// The hashings of one round are non-adaptive (the intuition of Sec. 4.1): every LocateInner pair
+// (a, a + beta) of every level and every EstimateValues hashing is known before any vote is counted.
+// So a round is four launches for the whole batch:
+//   1. k_gen_gather   every (chunk range, hashing group, request): permuted gather, window,
+//                     modulation, fold mod B (HashToBins steps 1-2) into partial sums;
+//   2. k_gen_finish   every (hashing group, request): partials summed in order, B-point FFT
+//                     (step 3), recovered coefficients subtracted in FP64 (step 4), bins stored;
+//                     for a LocateInner pair also c_j = phase(u_j / u'_j);
+//   3. k_gen_locate   every request: LocateSignal's levels in order, votes, regions, the list L;
+//   4. k_gen_estimate every request: EstimateValues' medians, the top k', zhat += w_J.
+// Reductions run in a fixed order; results are bit-reproducible.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "philox.cuh"
+#include "sfft_device.cuh"
+#include "sfft_internal.h"
+
+namespace sfft {
+
+// ------------------------------------------------------------------------------------------------
+// hashing parameters
+// ------------------------------------------------------------------------------------------------
+struct HashDesc {
+    uint32_t sigma, b, H;
+    uint32_t a[2];
+    uint64_t beta;
+};
+
+// LocateSignal's sigma, b of round r (Algorithm 3: one draw per call)
+__device__ __forceinline__ void locate_sigma_b(uint64_t seed, uint32_t s, uint32_t r, uint32_t nmask, uint32_t* sigma,
+                                               uint32_t* b) {
+    const Words4 w = draw(seed, s, r, 0, kKindLocate);
+    *sigma = (w.w[0] & nmask) | 1u;
+    *b = w.w[1] & nmask;
+}
+
+// LocateInner round q of level D (g = (D - 1) R_loc + q): a uniform on [n], beta uniform on the level's range
+__device__ __forceinline__ void inner_a_beta(uint64_t seed, uint32_t s, uint32_t r, uint32_t g, uint32_t nmask,
+                                             uint64_t lo, uint64_t hi, uint32_t* a, uint64_t* beta) {
+    const Words4 w = draw(seed, s, r, g, kKindInner);
+    *a = w.w[0] & nmask;
+    *beta = lo + (((uint64_t)w.w[1] * (hi - lo + 1)) >> 32);
+}
+
+// Group g of a round: g < npairs is LocateInner pair g (hashings a and a + beta under the round's
+// sigma, b); g >= npairs is EstimateValues hashing q = g - npairs with fresh (sigma_q, a_q, b_q).
+__device__ __forceinline__ HashDesc group_desc(const GenArgs& a, uint32_t s, uint32_t g) {
+    HashDesc h;
+    if (g < a.npairs) {
+        locate_sigma_b(a.seed, s, a.round, a.nmask, &h.sigma, &h.b);
+        const uint32_t D = g / a.R_loc;
+        inner_a_beta(a.seed, s, a.round, g, a.nmask, a.beta_lo[D], a.beta_hi[D], &h.a[0], &h.beta);
+        h.a[1] = (uint32_t)((h.a[0] + h.beta) & a.nmask);
+        h.H = 2;
+    } else {
+        const Words4 w = draw(a.seed, s, a.round, g - a.npairs, kKindEstimate);
+        h.sigma = (w.w[0] & a.nmask) | 1u;
+        h.b = w.w[1] & a.nmask;
+        h.a[0] = w.w[2] & a.nmask;
+        h.a[1] = 0;
+        h.beta = 0;
+        h.H = 1;
+    }
+    return h;
+}
+
+__device__ __forceinline__ uint32_t hash_index(const GenArgs& a, uint32_t g, uint32_t h) {
+    return g < a.npairs ? 2 * g + h : 2 * a.npairs + (g - a.npairs);
+}
+
+// bin and offset of a permuted position (Sec. 3 definitions)
+__device__ __forceinline__ int32_t gen_offset(uint32_t p, uint32_t n, uint32_t nmask, uint32_t logNp, uint32_t* jbin) {
+    const uint32_t Np = 1u << logNp;
+    const uint32_t jj = ((p + (Np >> 1)) & nmask) >> logNp;
+    const uint32_t dd = (p - jj * Np) & nmask;
+    *jbin = jj;
+    return dd > (nmask >> 1) ? (int32_t)((int64_t)dd - (int64_t)n) : (int32_t)dd;
+}
+
+// ------------------------------------------------------------------------------------------------
+// 1. gather and fold
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_gen_gather(const GenArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t s = a.req_base + blockIdx.z, g = blockIdx.y, c = blockIdx.x, tid = threadIdx.x;
+    const HashDesc h = group_desc(a, s, g);
+    float2* stage = reinterpret_cast<float2*>(smem);   // [2][kChunkTaps]
+    float2* red = stage + 2 * kChunkTaps;               // [H][max(B, kThreads)]
+    const float2* __restrict__ x = a.x + (size_t)s * a.n;
+    const bool big = a.B > (uint32_t)kThreads;
+    if (big)
+        for (uint32_t i = tid; i < h.H * a.B; i += kThreads) red[i] = make_float2(0.f, 0.f);
+    float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const uint32_t sb = h.sigma * h.b;
+    const float inv_half_n = 2.0f / (float)a.n;
+    const uint32_t c0 = c * a.cpb, c1 = min(c0 + a.cpb, a.chunks);
+    int64_t t_first = -a.T + (int64_t)c0 * kChunkTaps;
+    for (uint32_t ch = c0; ch < c1; ++ch) {
+        const int64_t t_lo = -a.T + (int64_t)ch * kChunkTaps;
+        const uint32_t ntap = (uint32_t)(min(t_lo + (int64_t)kChunkTaps, a.T + 1) - t_lo);
+        // step 1a: x_{sigma (t - a_h)} for the chunk's taps, 12 loads in flight per thread
+        for (uint32_t hh = 0; hh < h.H; ++hh) {
+            const int32_t base = (int32_t)(t_lo - (int64_t)h.a[hh]);
+            for (uint32_t i0 = tid; i0 < ntap; i0 += kThreads * 12) {
+                float2 v[12];
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                    const uint32_t i = i0 + (uint32_t)q * kThreads;
+                    if (i < ntap) v[q] = __ldcg(x + ((h.sigma * (uint32_t)(base + (int32_t)i)) & a.nmask));
+                }
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                    const uint32_t i = i0 + (uint32_t)q * kThreads;
+                    if (i < ntap) stage[hh * kChunkTaps + i] = v[q];
+                }
+            }
+        }
+        __syncthreads();
+        // step 1b + 2: window, modulation w^{sigma b t}, fold mod B
+        for (uint32_t k = tid; k < ntap; k += kThreads) {
+            const int32_t t = (int32_t)t_lo + (int32_t)k;
+            const float gv = a.taps[t < 0 ? -t : t];
+            const uint32_t e = (sb * (uint32_t)t) & a.nmask;
+            const int32_t es = e > (a.nmask >> 1) ? (int32_t)((int64_t)e - (int64_t)a.n) : (int32_t)e;
+            float sn, cs;
+            sincospif((float)es * inv_half_n, &sn, &cs);
+            const float2 gt = make_float2(gv * cs, -gv * sn);
+            if (!big) {
+                for (uint32_t hh = 0; hh < h.H; ++hh) acc[hh] = cfma(gt, stage[hh * kChunkTaps + k], acc[hh]);
+            } else {
+                const uint32_t r = (uint32_t)t & (a.B - 1);
+                for (uint32_t hh = 0; hh < h.H; ++hh)
+                    red[hh * a.B + r] = cfma(gt, stage[hh * kChunkTaps + k], red[hh * a.B + r]);
+            }
+        }
+        __syncthreads();
+    }
+    float2* part = a.part + (size_t)s * a.part_stride + ((size_t)g * a.ctas + c) * 2 * a.B;
+    if (!big) {
+        // every chunk starts at a multiple of B away from the first, so thread tid always folds
+        // residue (t_first + tid) mod B; the threads of residue r are owner + m B
+        for (uint32_t hh = 0; hh < h.H; ++hh) red[hh * kThreads + tid] = acc[hh];
+        __syncthreads();
+        for (uint32_t r = tid; r < a.B; r += kThreads) {
+            const uint32_t owner = (r - (uint32_t)t_first) & (a.B - 1);
+            for (uint32_t hh = 0; hh < h.H; ++hh) {
+                float2 sum = make_float2(0.f, 0.f);
+                for (uint32_t m = owner; m < (uint32_t)kThreads; m += a.B) sum = cadd(sum, red[hh * kThreads + m]);
+                part[hh * a.B + r] = sum;
+            }
+        }
+    } else {
+        for (uint32_t i = tid; i < h.H * a.B; i += kThreads) part[i] = red[i];
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// 2. finish the bins of one hashing group
+// ------------------------------------------------------------------------------------------------
+struct GenFinLayout {
+    size_t U, ent_idx, ent_bin, ent_sub, bin_cnt, bin_start, bin_list, scan, total;
+};
+__host__ __device__ inline size_t gtake(size_t* off, size_t bytes) {
+    const size_t o = (*off + 15) & ~size_t(15);
+    *off = o + bytes;
+    return o;
+}
+__host__ __device__ inline GenFinLayout gen_fin_layout(uint32_t B, uint32_t zcap) {
+    GenFinLayout L;
+    size_t off = 0;
+    L.U = gtake(&off, (size_t)2 * B * 8);
+    L.ent_idx = gtake(&off, (size_t)zcap * 4);
+    L.ent_bin = gtake(&off, (size_t)zcap * 4);
+    L.ent_sub = gtake(&off, (size_t)zcap * 2 * 16);
+    L.bin_cnt = gtake(&off, (size_t)(B + 1) * 4);
+    L.bin_start = gtake(&off, (size_t)(B + 1) * 4);
+    L.bin_list = gtake(&off, (size_t)zcap * 4);
+    L.scan = gtake(&off, (size_t)(kThreads + 8) * 4);
+    L.total = off;
+    return L;
+}
+size_t general_finish_smem(uint32_t B, uint32_t zcap) { return gen_fin_layout(B, zcap).total; }
+
+__global__ void __launch_bounds__(kThreads) k_gen_finish(const GenArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t s = a.req_base + blockIdx.y, g = blockIdx.x, tid = threadIdx.x;
+    const HashDesc h = group_desc(a, s, g);
+    const uint32_t B = a.B;
+    const GenFinLayout Ly = gen_fin_layout(B, a.zcap);
+    float2* U = reinterpret_cast<float2*>(smem + Ly.U);
+    uint32_t* ent_idx = reinterpret_cast<uint32_t*>(smem + Ly.ent_idx);
+    uint32_t* ent_bin = reinterpret_cast<uint32_t*>(smem + Ly.ent_bin);
+    double2* ent_sub = reinterpret_cast<double2*>(smem + Ly.ent_sub);
+    uint32_t* bin_cnt = reinterpret_cast<uint32_t*>(smem + Ly.bin_cnt);
+    uint32_t* bin_start = reinterpret_cast<uint32_t*>(smem + Ly.bin_start);
+    uint32_t* bin_list = reinterpret_cast<uint32_t*>(smem + Ly.bin_list);
+    uint32_t* scan = reinterpret_cast<uint32_t*>(smem + Ly.scan);
+    const uint32_t logNp = (uint32_t)(63 - __clzll((long long)a.n)) - a.logB;
+    // steps 2-3: partial folds summed in chunk order, bit-reversed, B-point FFT per hashing
+    const float2* part = a.part + (size_t)s * a.part_stride + (size_t)g * a.ctas * 2 * B;
+    const uint32_t shift_br = 32u - a.logB;
+    for (uint32_t i = tid; i < h.H * B; i += kThreads) {
+        const uint32_t hh = i / B, r = i - hh * B;
+        float2 sum = make_float2(0.f, 0.f);
+        for (uint32_t c = 0; c < a.ctas; ++c) sum = cadd(sum, __ldcg(part + ((size_t)c * 2 + hh) * B + r));
+        U[hh * B + (__brev(r) >> shift_br)] = sum;
+    }
+    // step 4 terms of the recovered coefficients: W(-o(i)) zhat_i w^{a_h sigma i}
+    const uint32_t nz = min(a.zcount[s], a.zcap);
+    for (uint32_t e = tid; e < nz; e += kThreads) {
+        const uint32_t i = a.zidx[(size_t)s * a.zcap + e];
+        ent_idx[e] = i;
+        uint32_t jb;
+        const int32_t o = gen_offset((h.sigma * (i - h.b)) & a.nmask, (uint32_t)a.n, a.nmask, logNp, &jb);
+        ent_bin[e] = jb;
+        const double gain = a.wtab[o < 0 ? -o : o];
+        const double2 z = a.zval[(size_t)s * a.zcap + e];
+        const double2 gz = make_double2(gain * z.x, gain * z.y);
+        for (uint32_t hh = 0; hh < h.H; ++hh) {
+            const double2 w = root_pow<float>((h.a[hh] * h.sigma * i) & a.nmask, a.nmask);
+            ent_sub[2 * e + hh] = make_double2(gz.x * w.x - gz.y * w.y, gz.x * w.y + gz.y * w.x);
+        }
+    }
+    __syncthreads();
+    block_fft_rows<float>(U, h.H, a.logB);
+    bucket_entries(ent_bin, nz, B, bin_cnt, bin_start, bin_list, scan);
+    double2* bins = a.bins + (size_t)s * a.bins_stride;
+    for (uint32_t j = tid; j < B; j += kThreads) {
+        double2 u[2];
+        for (uint32_t hh = 0; hh < h.H; ++hh) {
+            const float2 v = U[hh * B + j];
+            u[hh] = make_double2((double)v.x, (double)v.y);
+        }
+        for (uint32_t xx = bin_start[j]; xx < bin_start[j + 1]; ++xx) {
+            const uint32_t e = bin_list[xx];
+            for (uint32_t hh = 0; hh < h.H; ++hh) {
+                u[hh].x -= ent_sub[2 * e + hh].x;
+                u[hh].y -= ent_sub[2 * e + hh].y;
+            }
+        }
+        for (uint32_t hh = 0; hh < h.H; ++hh) bins[(size_t)hash_index(a, g, hh) * B + j] = u[hh];
+        if (h.H == 2) a.phase[(size_t)s * a.phase_stride + (size_t)g * B + j] = phase01<double>(mul_conj_rn(u[0], u[1]));
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// 3. LocateSignal: votes over the levels
+// ------------------------------------------------------------------------------------------------
+// One LocateInner vote test (Algorithm 3: |beta theta_{j,q} - c_j| circular < s pi).  f = e / M with
+// e the exact fixed-point value of beta (m + sigma b) mod n and M = n 2^F.  The test is taken on
+// integers except for the (rare) e next to a boundary, where the double expression of the test
+// decides, evaluated exactly as written.
+struct VoteBounds {
+    uint64_t ilo, len;    // e is inside iff (e - ilo) mod M <= len
+    uint64_t amb0, amb1;  // integers within 0.25 of a boundary (or ~0 when none)
+    double c;
+};
+__device__ __forceinline__ VoteBounds vote_bounds(double c, double s, uint64_t M) {
+    VoteBounds v;
+    const double Md = (double)M;
+    const double x = c * Md;             // exact: M is a power of two
+    const double hw = 0.5 * s * Md;      // exact for the dyadic s used here; otherwise rounded once
+    const double bl = x - hw, bh = x + hw;
+    const int64_t ilo = (int64_t)floor(bl) + 1;   // smallest integer > bl
+    const int64_t ihi = (int64_t)ceil(bh) - 1;    // largest integer < bh
+    const uint64_t mask = M - 1;
+    v.ilo = (uint64_t)ilo & mask;
+    v.len = (uint64_t)(ihi - ilo) & mask;
+    const double rl = rint(bl), rh = rint(bh);
+    v.amb0 = fabs(bl - rl) < 0.25 ? ((uint64_t)(int64_t)rl & mask) : ~0ull;
+    v.amb1 = fabs(bh - rh) < 0.25 ? ((uint64_t)(int64_t)rh & mask) : ~0ull;
+    v.c = c;
+    return v;
+}
+__device__ __forceinline__ bool vote_hit(const VoteBounds& v, uint64_t e, uint64_t M, double s) {
+    if (e == v.amb0 || e == v.amb1) {
+        const double f = (double)e / (double)M;
+        double dist = fabs(f - v.c);
+        if (dist > 0.5) dist = 1.0 - dist;
+        return dist < s / 2.0;
+    }
+    return ((e - v.ilo) & (M - 1)) <= v.len;
+}
+
+// Votes of bin j at one level, then its region update (the four consecutive subregions with the
+// most votes among those with a majority; bottom when no subregion has one).
+// phase(q) returns c_j of LocateInner round q; beta[q] its beta.
+template <typename PhaseFn>
+__device__ void locate_bin(uint32_t j, uint32_t t, uint32_t nrep, const uint64_t* beta, PhaseFn phase, uint64_t sb_fp,
+                           uint64_t w_fp, uint64_t M, double s, uint64_t* l_fp, uint8_t* valid, uint32_t* votes_out) {
+    uint8_t v[kMaxT];
+    for (uint32_t q = 0; q < t; ++q) v[q] = 0;
+    const uint64_t mask = M - 1;
+    const uint64_t half_step = w_fp / (2 * (uint64_t)t), step = w_fp / t;
+    for (uint32_t r = 0; r < nrep; ++r) {
+        const VoteBounds vb = vote_bounds(phase(r), s, M);
+        // e_q = beta (m_q + sigma b) mod M, m_q = l + (2q - 1) w / 2t, advanced by beta w / t
+        uint64_t e = (beta[r] * ((l_fp[j] + half_step + sb_fp) & mask)) & mask;
+        const uint64_t de = (beta[r] * step) & mask;
+        for (uint32_t q = 0; q < t; ++q) {
+            if (vote_hit(vb, e, M, s)) v[q] += 1;
+            e = (e + de) & mask;
+        }
+    }
+    if (votes_out)
+        for (uint32_t q = 0; q < t; ++q) votes_out[q] = v[q];
+    bool any = false;
+    for (uint32_t q = 0; q < t; ++q) any = any || 2u * v[q] > nrep;
+    if (!any) {
+        valid[j] = 0;
+        return;
+    }
+    uint32_t best = 0, best_sum = 0;
+    for (uint32_t q0 = 0; q0 + 4 <= t; ++q0) {
+        const uint32_t sum = (uint32_t)v[q0] + v[q0 + 1] + v[q0 + 2] + v[q0 + 3];
+        if (q0 == 0 || sum > best_sum) {
+            best = q0;
+            best_sum = sum;
+        }
+    }
+    l_fp[j] = (l_fp[j] + (uint64_t)best * step) & mask;
+}
+
+size_t general_locate_smem(uint32_t B) {
+    size_t off = 0;
+    gtake(&off, (size_t)B * 8);           // regions
+    gtake(&off, (size_t)B);               // valid
+    gtake(&off, (size_t)B * 4);           // candidate keys
+    gtake(&off, (size_t)B * 4);           // sorted keys
+    gtake(&off, (size_t)B * 4);           // keep flags
+    gtake(&off, (size_t)(kThreads + 8) * 4);
+    return off;
+}
+
+// Sorts the m keys of key[] ascending and removes duplicates: the distinct keys end up in
+// key[0..returned count).  tmp and keep hold m words each.
+__device__ uint32_t sort_unique_u32(uint32_t* key, uint32_t m, uint32_t* tmp, uint32_t* keep, uint32_t* scan) {
+    for (uint32_t c = threadIdx.x; c < m; c += kThreads) {  // rank, ties broken by position
+        const uint32_t k = key[c];
+        uint32_t r = 0;
+        for (uint32_t q = 0; q < m; ++q) r += (key[q] < k || (key[q] == k && q < c)) ? 1u : 0u;
+        tmp[r] = k;
+    }
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < m; p += kThreads) keep[p] = (p == 0 || tmp[p - 1] != tmp[p]) ? 1u : 0u;
+    __syncthreads();
+    const uint32_t total = block_exclusive_scan(keep, m, scan);  // keep[p]: output slot of a kept key
+    for (uint32_t p = threadIdx.x; p < m; p += kThreads) {
+        const uint32_t nxt = p + 1 < m ? keep[p + 1] : total;
+        if (nxt != keep[p]) key[keep[p]] = tmp[p];
+    }
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t s_beta[kMaxRloc];
+    const uint32_t s = a.req_base + blockIdx.x, tid = threadIdx.x, B = a.B;
+    size_t off = 0;
+    uint64_t* l_fp = reinterpret_cast<uint64_t*>(smem + gtake(&off, (size_t)B * 8));
+    uint8_t* valid = reinterpret_cast<uint8_t*>(smem + gtake(&off, (size_t)B));
+    uint32_t* cand = reinterpret_cast<uint32_t*>(smem + gtake(&off, (size_t)B * 4));
+    uint32_t* srt = reinterpret_cast<uint32_t*>(smem + gtake(&off, (size_t)B * 4));
+    uint32_t* keep = reinterpret_cast<uint32_t*>(smem + gtake(&off, (size_t)B * 4));
+    uint32_t* scan = reinterpret_cast<uint32_t*>(smem + gtake(&off, (size_t)(kThreads + 8) * 4));
+    __shared__ uint32_t s_nc;
+    uint32_t sigma, b;
+    locate_sigma_b(a.seed, s, a.round, a.nmask, &sigma, &b);
+    const uint64_t n = a.n, Np = n >> a.logB;
+    const uint64_t M = n << kFracBits;
+    const uint64_t sb_fp = ((uint64_t)((sigma * b) & a.nmask)) << kFracBits;
+    for (uint32_t j = tid; j < B; j += kThreads) {  // regions centred on the bins: [j n/B - n/2B, +n/B)
+        l_fp[j] = ((((uint64_t)j * Np) + n - Np / 2) & (n - 1)) << kFracBits;
+        valid[j] = 1;
+    }
+    if (tid == 0) s_nc = 0;
+    const double* phase = a.phase + (size_t)s * a.phase_stride;
+    for (uint32_t D = 0; D < a.dmax; ++D) {
+        if (tid < a.R_loc) {
+            uint32_t aa;
+            uint64_t be;
+            inner_a_beta(a.seed, s, a.round, D * a.R_loc + tid, a.nmask, a.beta_lo[D], a.beta_hi[D], &aa, &be);
+            s_beta[tid] = be;
+        }
+        __syncthreads();
+        const uint64_t w_fp = (Np << kFracBits) >> ((uint64_t)D * a.logtp);
+        const double* ph = phase + (size_t)D * a.R_loc * B;
+        for (uint32_t j = tid; j < B; j += kThreads) {
+            if (!valid[j]) continue;
+            locate_bin(j, a.t, a.R_loc, s_beta, [&](uint32_t r) { return ph[(size_t)r * B + j]; }, sb_fp, w_fp, M, a.s,
+                       l_fp, valid, nullptr);
+        }
+        __syncthreads();
+    }
+    // L = {pi^{-1}(tau_j)}: tau_j the integer nearest the centre of the last region
+    const uint64_t wlast = (Np << kFracBits) >> ((uint64_t)a.dmax * a.logtp);
+    const uint32_t sigma_inv = inverse_odd(sigma) & a.nmask;
+    for (uint32_t j = tid; j < B; j += kThreads) {
+        if (!valid[j]) continue;
+        const uint32_t tau = (uint32_t)(((l_fp[j] + wlast / 2 + (1ull << (kFracBits - 1))) >> kFracBits) & (n - 1));
+        const uint32_t slot = atomicAdd(&s_nc, 1u);
+        cand[slot] = (sigma_inv * tau + b) & a.nmask;
+    }
+    __syncthreads();
+    const uint32_t m = s_nc;
+    const uint32_t nu = sort_unique_u32(cand, m, srt, keep, scan);
+    for (uint32_t p = tid; p < nu; p += kThreads) a.L[(size_t)s * B + p] = cand[p];
+    if (tid == 0) a.nL[s] = nu;
+}
+
+// ------------------------------------------------------------------------------------------------
+// 4. EstimateValues, top k', zhat += w_J
+// ------------------------------------------------------------------------------------------------
+struct EstLayout {
+    size_t w, mag, perm, topi, topv, out_idx, out_val, keep, scan, draws, total;
+    uint32_t P;
+};
+__host__ __device__ inline EstLayout est_layout(uint32_t B, uint32_t kprime, uint32_t zcap) {
+    EstLayout L;
+    size_t off = 0;
+    uint32_t P = 1;
+    while (P < B) P <<= 1;
+    L.P = P;
+    L.w = gtake(&off, (size_t)B * 16);
+    L.mag = gtake(&off, (size_t)B * 8);
+    L.perm = gtake(&off, (size_t)P * 4);
+    L.topi = gtake(&off, (size_t)kprime * 4);
+    L.topv = gtake(&off, (size_t)kprime * 16);
+    L.out_idx = gtake(&off, (size_t)(zcap + kprime) * 4);
+    L.out_val = gtake(&off, (size_t)(zcap + kprime) * 16);
+    L.keep = gtake(&off, (size_t)(zcap + kprime > B ? zcap + kprime : B) * 4);
+    L.scan = gtake(&off, (size_t)(kThreads + 8) * 4);
+    L.draws = gtake(&off, (size_t)kMaxRest * 3 * 8);
+    L.total = off;
+    return L;
+}
+size_t general_estimate_smem(uint32_t B, uint32_t kprime, uint32_t zcap) { return est_layout(B, kprime, zcap).total; }
+
+// w_i = median_q Re e_q + i median_q Im e_q over the hashings q whose window gain at i is >= est_gmin,
+// e_q = u^{(q)}_{h_q(i)} w^{-a_q sigma_q i} / W(-o_q(i)); lower median; 0 when no hashing qualifies.
+template <typename BinFn>
+__device__ double2 estimate_one(uint32_t i, uint32_t nrep, const uint64_t* sig, const uint64_t* bb, const uint64_t* aa,
+                                BinFn bin, uint32_t n, uint32_t nmask, uint32_t logNp, const double* wtab, double gmin) {
+    double re[kMaxRest], im[kMaxRest];
+    uint32_t m = 0;
+    for (uint32_t q = 0; q < nrep; ++q) {
+        const uint32_t sq = (uint32_t)sig[q];
+        const uint32_t p = (sq * (i - (uint32_t)bb[q])) & nmask;
+        uint32_t j;
+        const int32_t o = gen_offset(p, n, nmask, logNp, &j);
+        const double gain = wtab[o < 0 ? -o : o];
+        if (!(gain >= gmin)) continue;
+        const uint32_t e = ((uint32_t)aa[q] * sq * i) & nmask;
+        const double2 w = root_pow<double>(e, nmask);
+        const double2 u = bin(q, j);
+        const double2 v = mul_conj_rn(u, w);
+        const double x = __ddiv_rn(v.x, gain), y = __ddiv_rn(v.y, gain);
+        // insertion into the sorted prefixes
+        uint32_t pr = m, pi = m;
+        while (pr > 0 && re[pr - 1] > x) {
+            re[pr] = re[pr - 1];
+            --pr;
+        }
+        re[pr] = x;
+        while (pi > 0 && im[pi - 1] > y) {
+            im[pi] = im[pi - 1];
+            --pi;
+        }
+        im[pi] = y;
+        ++m;
+    }
+    if (m == 0) return make_double2(0.0, 0.0);
+    return make_double2(re[(m - 1) / 2], im[(m - 1) / 2]);
+}
+
+// (mag2 descending, index ascending) order of candidates via a bitonic sort of a permutation
+__device__ void sort_by_magnitude(const double* mag, const uint32_t* idx, uint32_t m, uint32_t P, uint32_t* perm) {
+    for (uint32_t p = threadIdx.x; p < P; p += kThreads) perm[p] = p;
+    __syncthreads();
+    auto before = [&](uint32_t a, uint32_t b) -> bool {  // a ranks before b
+        if (a >= m) return false;
+        if (b >= m) return true;
+        if (mag[a] != mag[b]) return mag[a] > mag[b];
+        return idx[a] < idx[b];
+    };
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P; i += kThreads) {
+                const uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const uint32_t pa = perm[i], pb = perm[ixj];
+                    const bool swap = up ? before(pb, pa) : before(pa, pb);
+                    if (swap) {
+                        perm[i] = pb;
+                        perm[ixj] = pa;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gen_estimate(const GenArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t s = a.req_base + blockIdx.x, tid = threadIdx.x, B = a.B;
+    const EstLayout Ly = est_layout(B, a.kprime, a.zcap);
+    double2* wv = reinterpret_cast<double2*>(smem + Ly.w);
+    double* mag = reinterpret_cast<double*>(smem + Ly.mag);
+    uint32_t* perm = reinterpret_cast<uint32_t*>(smem + Ly.perm);
+    uint32_t* topi = reinterpret_cast<uint32_t*>(smem + Ly.topi);
+    double2* topv = reinterpret_cast<double2*>(smem + Ly.topv);
+    uint32_t* out_idx = reinterpret_cast<uint32_t*>(smem + Ly.out_idx);
+    double2* out_val = reinterpret_cast<double2*>(smem + Ly.out_val);
+    uint32_t* keep = reinterpret_cast<uint32_t*>(smem + Ly.keep);
+    uint32_t* scan = reinterpret_cast<uint32_t*>(smem + Ly.scan);
+    uint64_t* dr = reinterpret_cast<uint64_t*>(smem + Ly.draws);  // sigma, b, a per hashing
+    if (tid < a.R_est) {
+        const Words4 w = draw(a.seed, s, a.round, tid, kKindEstimate);
+        dr[tid] = (w.w[0] & a.nmask) | 1u;
+        dr[kMaxRest + tid] = w.w[1] & a.nmask;
+        dr[2 * kMaxRest + tid] = w.w[2] & a.nmask;
+    }
+    __syncthreads();
+    const uint32_t nL = a.nL[s];
+    const uint32_t* L = a.L + (size_t)s * B;
+    const double2* bins = a.bins + (size_t)s * a.bins_stride + (size_t)2 * a.npairs * B;
+    const uint32_t logNp = (uint32_t)(63 - __clzll((long long)a.n)) - a.logB;
+    for (uint32_t c = tid; c < nL; c += kThreads) {
+        const double2 w = estimate_one(L[c], a.R_est, dr, dr + kMaxRest, dr + 2 * kMaxRest,
+                                       [&](uint32_t q, uint32_t j) { return bins[(size_t)q * B + j]; }, (uint32_t)a.n,
+                                       a.nmask, logNp, a.wtab, a.est_gmin);
+        wv[c] = w;
+        mag[c] = __dadd_rn(__dmul_rn(w.x, w.x), __dmul_rn(w.y, w.y));
+    }
+    __syncthreads();
+    sort_by_magnitude(mag, L, nL, Ly.P, perm);
+    const uint32_t nJ = nL < a.kprime ? nL : a.kprime;
+    // J sorted by index: the kept candidates are a subset of the ascending L, so keep L's order
+    for (uint32_t c = tid; c < nL; c += kThreads) keep[c] = 0;
+    __syncthreads();
+    for (uint32_t r = tid; r < nJ; r += kThreads) keep[perm[r]] = 1;
+    __syncthreads();
+    const uint32_t total = block_exclusive_scan(keep, nL, scan);
+    for (uint32_t c = tid; c < nL; c += kThreads) {
+        const uint32_t nxt = c + 1 < nL ? keep[c + 1] : total;
+        if (nxt != keep[c]) {
+            topi[keep[c]] = L[c];
+            topv[keep[c]] = wv[c];
+        }
+    }
+    __syncthreads();
+    // zhat <- zhat + w_J (zhat first on equal indices); nothing is dropped in the general case
+    const uint32_t nz = min(a.zcount[s], a.zcap);
+    uint32_t* zi = a.zidx + (size_t)s * a.zcap;
+    double2* zv = a.zval + (size_t)s * a.zcap;
+    for (uint32_t e = tid; e < nz; e += kThreads) {
+        const uint32_t key = zi[e];
+        const uint32_t pos = e + lower_bound_u32(topi, nJ, key);
+        out_idx[pos] = key;
+        out_val[pos] = zv[e];
+    }
+    for (uint32_t c = tid; c < nJ; c += kThreads) {
+        const uint32_t pos = c + upper_bound_u32(zi, nz, topi[c]);
+        out_idx[pos] = topi[c];
+        out_val[pos] = topv[c];
+    }
+    __syncthreads();
+    const uint32_t tot = nz + nJ;
+    for (uint32_t p = tid; p < tot; p += kThreads) {
+        const uint32_t idx = out_idx[p];
+        uint32_t kp = 0;
+        if (p == 0 || out_idx[p - 1] != idx) {
+            if (p + 1 < tot && out_idx[p + 1] == idx) {
+                out_val[p] = make_double2(out_val[p].x + out_val[p + 1].x, out_val[p].y + out_val[p + 1].y);
+            }
+            kp = 1;
+        }
+        keep[p] = kp;
+    }
+    __syncthreads();
+    const uint32_t newcount = block_exclusive_scan(keep, tot, scan);
+    const bool last = a.last_round != 0;
+    for (uint32_t p = tid; p < tot; p += kThreads) {
+        const uint32_t pos = keep[p];
+        const uint32_t nxt = p + 1 < tot ? keep[p + 1] : newcount;
+        if (nxt == pos) continue;
+        if (pos < a.zcap) {
+            zi[pos] = out_idx[p];
+            zv[pos] = out_val[p];
+        }
+        if (last && pos < a.out_cap) {
+            a.out_idx[(size_t)s * a.out_cap + pos] = out_idx[p];
+            a.out_val[(size_t)s * a.out_cap + pos] = out_val[p];
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const bool overflow = newcount > a.zcap;
+        if (overflow) a.zflag[s] = 1;
+        a.zcount[s] = overflow ? a.zcap : newcount;
+        if (last) {
+            const uint32_t kept = overflow ? a.zcap : newcount;
+            a.out_count[s] = kept < a.out_cap ? kept : a.out_cap;
+            a.out_flag[s] = (a.zflag[s] || kept > a.out_cap) ? SFFT_ERR_CAPACITY : SFFT_OK;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// single-step kernels on caller bins
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_locate_votes(const VoteArgs a) {
+    const uint64_t M = a.n << kFracBits;
+    const uint64_t sb_fp = ((uint64_t)((a.sigma * a.b) & a.nmask)) << kFracBits;
+    for (uint32_t j = threadIdx.x; j < a.B; j += kThreads) {
+        for (uint32_t q = 0; q < a.t; ++q) a.votes[(size_t)j * a.t + q] = 0;
+        if (!a.valid[j]) continue;
+        locate_bin(j, a.t, a.nrep, a.beta,
+                   [&](uint32_t r) {
+                       return phase01<double>(mul_conj_rn(a.u[(size_t)r * a.B + j], a.up[(size_t)r * a.B + j]));
+                   },
+                   sb_fp, a.w_fp, M, a.s, a.l_fp, a.valid, a.votes + (size_t)j * a.t);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_estimate_from_bins(const EstArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t tid = threadIdx.x;
+    const EstLayout Ly = est_layout(a.nL > 0 ? a.nL : 1, a.kprime > 0 ? a.kprime : 1, 1);
+    double2* wv = reinterpret_cast<double2*>(smem + Ly.w);
+    double* mag = reinterpret_cast<double*>(smem + Ly.mag);
+    uint32_t* perm = reinterpret_cast<uint32_t*>(smem + Ly.perm);
+    uint32_t* keep = reinterpret_cast<uint32_t*>(smem + Ly.keep);
+    uint32_t* scan = reinterpret_cast<uint32_t*>(smem + Ly.scan);
+    const uint32_t logNp = (uint32_t)(63 - __clzll((long long)a.n)) - a.logB;
+    for (uint32_t c = tid; c < a.nL; c += kThreads) {
+        const double2 w = estimate_one(a.L[c], a.nrep, a.sig, a.bb, a.aa,
+                                       [&](uint32_t q, uint32_t j) { return a.u[(size_t)q * a.B + j]; }, (uint32_t)a.n,
+                                       a.nmask, logNp, a.wtab, a.est_gmin);
+        wv[c] = w;
+        mag[c] = __dadd_rn(__dmul_rn(w.x, w.x), __dmul_rn(w.y, w.y));
+    }
+    __syncthreads();
+    sort_by_magnitude(mag, a.L, a.nL, Ly.P, perm);
+    const uint32_t nJ = a.nL < a.kprime ? a.nL : a.kprime;
+    for (uint32_t c = tid; c < a.nL; c += kThreads) keep[c] = 0;
+    __syncthreads();
+    for (uint32_t r = tid; r < nJ; r += kThreads) keep[perm[r]] = 1;
+    __syncthreads();
+    const uint32_t total = block_exclusive_scan(keep, a.nL, scan);
+    for (uint32_t c = tid; c < a.nL; c += kThreads) {
+        const uint32_t nxt = c + 1 < a.nL ? keep[c + 1] : total;
+        if (nxt != keep[c]) {
+            a.widx[keep[c]] = a.L[c];
+            a.wval[keep[c]] = wv[c];
+        }
+    }
+    if (tid == 0) *a.count = total;
+}
+
+// ------------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------------
+cudaError_t general_set_smem(size_t gather, size_t finish, size_t locate, size_t estimate) {
+    static size_t lim[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    if (gather > lim[0] && (e = cudaFuncSetAttribute(k_gen_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)gather)) == cudaSuccess)
+        lim[0] = gather;
+    if (e != cudaSuccess) return e;
+    if (finish > lim[1] && (e = cudaFuncSetAttribute(k_gen_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)finish)) == cudaSuccess)
+        lim[1] = finish;
+    if (e != cudaSuccess) return e;
+    if (locate > lim[2] && (e = cudaFuncSetAttribute(k_gen_locate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)locate)) == cudaSuccess)
+        lim[2] = locate;
+    if (e != cudaSuccess) return e;
+    if (estimate > lim[3]) {
+        e = cudaFuncSetAttribute(k_gen_estimate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)estimate);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_estimate_from_bins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)estimate);
+        if (e == cudaSuccess) lim[3] = estimate;
+    }
+    return e;
+}
+
+cudaError_t launch_general_round(const GenArgs& a, uint32_t batch, const GeneralRound& r, cudaStream_t st) {
+    k_gen_gather<<<dim3(r.ctas, r.ngroups, batch), kThreads, r.smem_gather, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_gen_finish<<<dim3(r.ngroups, batch), kThreads, r.smem_finish, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_gen_locate<<<batch, kThreads, r.smem_locate, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_gen_estimate<<<batch, kThreads, r.smem_estimate, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_locate_votes(const VoteArgs& a, cudaStream_t st) {
+    k_locate_votes<<<1, kThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_estimate_from_bins(const EstArgs& a, cudaStream_t st) {
+    const size_t smem = est_layout(a.nL > 0 ? a.nL : 1, a.kprime > 0 ? a.kprime : 1, 1).total;
+    cudaError_t e = general_set_smem(0, 0, 0, smem);
+    if (e != cudaSuccess) return e;
+    k_estimate_from_bins<<<1, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sfft

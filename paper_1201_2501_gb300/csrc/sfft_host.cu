@@ -177,6 +177,81 @@ sfft_status build_exact_schedule(sfft_plan_s* pl) {
     return SFFT_OK;
 }
 
+// General schedule (Algorithm 2, SparseFFT): k_0 = k, k_{r+1} = floor(k_r / 4) down to 1;
+// B_r = pow2 >= bins_per_k k_r / eps in [B_min, n/2]; alpha = alpha0 in every round; EstimateValues
+// keeps k' = 3 k_r.  LocateSignal (Algorithm 3): t = largest power of two <= log2 n (or t_regions),
+// t' = t/4, w_0 = n/B, D_max = floor(log_{t'} w_0) + 1, and at level D (width w_D = w_0 / t'^{D-1})
+// beta is uniform on {ceil(s n t / 4 w_D), ..., floor(s n t / 2 w_D)}.
+sfft_status build_general_schedule(sfft_plan_s* pl) {
+    const sfft_params& p = pl->p;
+    pl->grounds.clear();
+    pl->taps_host.clear();
+    pl->wtab_host.clear();
+    const uint32_t logn = ceil_log2(p.n);
+    uint32_t t = p.t_regions;
+    if (t == 0) {
+        t = 1;
+        while (t * 2 <= logn) t *= 2;
+    }
+    if (t < 8 || t > (uint32_t)kMaxT || (t & (t - 1))) return SFFT_ERR_INVALID_ARG;
+    if (p.R_loc == 0 || p.R_loc > (uint32_t)kMaxRloc || p.R_est == 0 || p.R_est > (uint32_t)kMaxRest)
+        return SFFT_ERR_INVALID_ARG;
+    if (p.z_cap > 2048) return SFFT_ERR_INVALID_ARG;
+    const uint32_t tp = t / 4, logtp = ceil_log2(tp);
+    size_t taps_off = 0, wtab_off = 0;
+    for (uint64_t kr = p.k; kr >= 1; kr /= 4) {
+        GeneralRound r;
+        r.kr = (uint32_t)kr;
+        r.kprime = 3 * r.kr;
+        uint64_t B = pow2_at_least(p.bins_per_k * (double)kr / p.eps);
+        if (B < p.B_min) B = p.B_min;
+        if (B > p.n / 2) B = p.n / 2;
+        if (B > kMaxB) return SFFT_ERR_K_RANGE;
+        r.B = (uint32_t)B;
+        r.logB = ceil_log2(B);
+        r.T = window_halfwidth(r.B, p.alpha0, p.delta);
+        r.chunks = (uint32_t)((2 * (uint64_t)r.T + 1 + kChunkTaps - 1) / kChunkTaps);
+        r.cpb = r.chunks < 8 ? r.chunks : 8;
+        r.ctas = (r.chunks + r.cpb - 1) / r.cpb;
+        r.t = t;
+        r.logtp = logtp;
+        const uint32_t lw = ceil_log2(p.n / B);
+        r.dmax = lw / logtp + 1;
+        if (r.dmax > (uint32_t)kMaxLevels) return SFFT_ERR_K_RANGE;
+        for (uint32_t D = 1; D <= r.dmax; ++D) {
+            const uint64_t w = (p.n / B) >> ((uint64_t)(D - 1) * logtp);
+            const double base = p.s * (double)p.n * (double)t / (double)w;
+            uint64_t lo = (uint64_t)std::ceil(base / 4.0), hi = (uint64_t)std::floor(base / 2.0);
+            if (hi < lo) hi = lo;
+            if (hi - lo >= (uint64_t(1) << 32)) return SFFT_ERR_K_RANGE;
+            r.beta_lo[D - 1] = lo;
+            r.beta_hi[D - 1] = hi;
+        }
+        r.npairs = r.dmax * p.R_loc;
+        r.ngroups = r.npairs + p.R_est;
+        r.nhash = 2 * r.npairs + p.R_est;
+        r.taps_off = taps_off;
+        r.wtab_off = wtab_off;
+        r.smem_gather = (size_t)2 * kChunkTaps * 8 + (size_t)2 * (B > (uint64_t)kThreads ? B : kThreads) * 8;
+        r.smem_finish = general_finish_smem(r.B, p.z_cap);
+        r.smem_locate = general_locate_smem(r.B);
+        r.smem_estimate = general_estimate_smem(r.B, r.kprime, p.z_cap);
+        const size_t lim = 200 * 1024;
+        if (r.smem_finish > lim || r.smem_locate > lim || r.smem_estimate > lim) return SFFT_ERR_K_RANGE;
+        const uint64_t Np = p.n / B;
+        pl->taps_host.resize(taps_off + (size_t)r.T + 1);
+        window_taps_host(p.n, r.B, p.alpha0, p.delta, r.T, pl->taps_host.data() + taps_off);
+        pl->wtab_host.resize(wtab_off + Np / 2 + 1);
+        window_table_host(p.n, pl->taps_host.data() + taps_off, r.T, Np / 2 + 1, pl->wtab_host.data() + wtab_off);
+        taps_off += (size_t)r.T + 1;
+        wtab_off += Np / 2 + 1;
+        pl->grounds.push_back(r);
+        if (kr < 4) break;
+    }
+    pl->wtab_len = wtab_off;
+    return SFFT_OK;
+}
+
 }  // namespace sfft
 
 extern "C" {

@@ -91,6 +91,94 @@ struct DecodeArgs {
     int fp64;                  // transcendental precision of the decode (that of the plan's data path)
 };
 
+// ---- general mode (Algorithms 2 and 3) ----
+constexpr int kMaxLevels = 16;   // LocateSignal levels D_max
+constexpr int kMaxRloc = 15;     // LocateInner rounds per level
+constexpr int kMaxRest = 15;     // EstimateValues hashings
+constexpr int kMaxT = 32;        // regions per level t
+constexpr int kFracBits = 16;    // fixed-point fraction bits of region positions
+
+struct GeneralRound {
+    uint32_t kr = 0, kprime = 0;   // k_r and k' = 3 k_r
+    uint32_t B = 0, logB = 0;
+    int64_t T = 0;
+    uint32_t chunks = 0;           // 2048-tap chunks of the window
+    uint32_t cpb = 0;              // chunks per CTA of the gather launch
+    uint32_t ctas = 0;             // CTAs per hashing group and request
+    uint32_t dmax = 0, t = 0, logtp = 0;
+    uint64_t beta_lo[kMaxLevels] = {}, beta_hi[kMaxLevels] = {};
+    uint32_t npairs = 0, ngroups = 0, nhash = 0;
+    size_t taps_off = 0, wtab_off = 0;
+    size_t smem_gather = 0, smem_finish = 0, smem_locate = 0, smem_estimate = 0;
+};
+
+// Kernel argument block of the general-mode kernels of one round (passed by value).
+struct GenArgs {
+    const float2* x;
+    uint64_t n;
+    uint32_t nmask, logn;
+    uint64_t seed;
+    uint32_t round;
+    uint32_t req_base;     // request index of the launch's first request
+    uint32_t B, logB;
+    int64_t T;
+    uint32_t chunks, cpb, ctas;
+    uint32_t dmax, t, logtp, R_loc, R_est, npairs, ngroups, nhash, kprime;
+    uint64_t beta_lo[kMaxLevels], beta_hi[kMaxLevels];
+    double s, est_gmin;
+    const float* taps;
+    const double* wtab;
+    float2* part;          // [batch][ngroups][ctas][2][B]
+    size_t part_stride;    // elements per request
+    double2* bins;         // [batch][nhash][B]  (hashing 2g, 2g+1: pair g; 2 npairs + q: estimate q)
+    double* phase;         // [batch][npairs][B] phase(u_a conj(u_{a+beta})) / 2 pi
+    size_t bins_stride, phase_stride;  // elements per request
+    uint32_t* L;           // [batch][B] candidate frequencies
+    uint32_t* nL;          // [batch]
+    uint32_t* zidx;        // [batch][zcap]
+    double2* zval;
+    uint32_t* zcount;
+    int32_t* zflag;
+    uint32_t zcap;
+    uint32_t last_round;
+    uint32_t* out_idx;
+    double2* out_val;
+    uint32_t out_cap;
+    uint32_t* out_count;
+    int32_t* out_flag;
+};
+
+// One LocateInner level on caller bins (sfft_locate_votes).
+struct VoteArgs {
+    uint64_t n;
+    uint32_t nmask, B, t, nrep;
+    uint32_t sigma, b;
+    uint64_t w_fp;
+    double s;
+    const double2* u;      // nrep x B
+    const double2* up;     // nrep x B
+    const uint64_t* beta;  // nrep
+    uint64_t* l_fp;        // B (in/out)
+    uint8_t* valid;        // B (in/out)
+    uint32_t* votes;       // B x t (out)
+};
+
+// EstimateValues on caller bins (sfft_estimate_from_bins).
+struct EstArgs {
+    uint64_t n;
+    uint32_t nmask, B, logB, nrep, nL, kprime;
+    const uint64_t* sig;
+    const uint64_t* bb;
+    const uint64_t* aa;
+    const double2* u;      // nrep x B
+    const uint32_t* L;     // nL, ascending
+    const double* wtab;
+    double est_gmin;
+    uint32_t* widx;
+    double2* wval;
+    uint32_t* count;
+};
+
 }  // namespace sfft
 
 struct sfft_plan_s {
@@ -98,6 +186,12 @@ struct sfft_plan_s {
     uint32_t max_batch = 0;
     int device = 0;
     std::vector<sfft::ExactRound> rounds;
+    std::vector<sfft::GeneralRound> grounds;  // general mode
+    double2* d_bins = nullptr;
+    double* d_phase = nullptr;
+    uint32_t* d_L = nullptr;
+    uint32_t* d_nL = nullptr;
+    size_t bins_stride = 0, phase_stride = 0;
     std::vector<double> taps_host;  // every round's taps, FP64
     std::vector<double> wtab_host;  // every round's W(o), o = 0..n/2B
     float* d_taps32 = nullptr;
@@ -145,6 +239,15 @@ cudaError_t launch_exact_round(const ExactArgs& a, uint32_t batch, size_t smem, 
 cudaError_t launch_exact_decode(const DecodeArgs& a, cudaStream_t st);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                           uint32_t count, uint32_t* out, cudaStream_t st);
+// general mode (sfft_general.cu, sfft_host.cu)
+sfft_status build_general_schedule(sfft_plan_s* pl);
+size_t general_finish_smem(uint32_t B, uint32_t zcap);
+size_t general_locate_smem(uint32_t B);
+size_t general_estimate_smem(uint32_t B, uint32_t kprime, uint32_t zcap);
+cudaError_t general_set_smem(size_t gather, size_t finish, size_t locate, size_t estimate);
+cudaError_t launch_general_round(const GenArgs& a, uint32_t batch, const GeneralRound& r, cudaStream_t st);
+cudaError_t launch_locate_votes(const VoteArgs& a, cudaStream_t st);
+cudaError_t launch_estimate_from_bins(const EstArgs& a, cudaStream_t st);
 size_t exact_finish_smem(uint32_t B, uint32_t H, uint32_t zcap, bool fp64);
 size_t exact_gather_smem(uint32_t stage, bool fp64);
 cudaError_t set_exact_smem_limit(size_t bytes, bool fp64);

@@ -94,6 +94,10 @@ _SIGS = {
     "sfft_philox": (ctypes.c_int, [_u32, _u32, _u32p, _u32, _vp, _vp]),
     "sfft_hash_to_bins_static": (ctypes.c_int, [_u64, _u32, ctypes.c_int64, _vp, _vp, _vp, _u64, _u64, _u64, _vp, _vp,
                                                 _u32, _vp, _vp]),
+    "sfft_plan_general_round_info": (ctypes.c_int, [_vp, _u32, _u32p, _i64p, _u32p, _u32p, _u32p, _u64p, _u64p]),
+    "sfft_locate_votes": (ctypes.c_int, [_vp, _u32, _u64, _u64, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "sfft_estimate_from_bins": (ctypes.c_int, [_vp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _u32, _u32, _vp, _vp, _vp,
+                                               _vp]),
 }
 
 SFFT_STATIC_SCRATCH_BYTES = 4 * 1024 * 1024
@@ -197,7 +201,7 @@ class Plan:
     def taps(self, t: int):
         import numpy as np
 
-        T = self.round_info(t)["T"]
+        T = general_round_info(self, t)["T"] if self.params.mode == SFFT_GENERAL else self.round_info(t)["T"]
         out = np.zeros(T + 1, dtype=np.float64)
         _check(lib().sfft_plan_taps(self.handle, t, out.ctypes.data_as(_dblp), T + 1), "sfft_plan_taps")
         return out
@@ -288,3 +292,28 @@ def sfft_hash_to_bins_static(n: int, B: int, T: int, taps, wtab, x, sigma: int, 
     _check(lib().sfft_hash_to_bins_static(n, B, T, _ptr(taps), _ptr(wtab), _ptr(x), sigma, a, b, _ptr(zidx),
                                           _ptr(zval), nz, _ptr(out), _stream_ptr(stream)), "sfft_hash_to_bins_static")
     return out
+
+
+def general_round_info(plan: Plan, r: int) -> dict:
+    B, kp, dmax, t = (ctypes.c_uint32() for _ in range(4))
+    T = ctypes.c_int64()
+    lo = (ctypes.c_uint64 * 16)()
+    hi = (ctypes.c_uint64 * 16)()
+    _check(lib().sfft_plan_general_round_info(plan.handle, r, ctypes.byref(B), ctypes.byref(T), ctypes.byref(kp),
+                                              ctypes.byref(dmax), ctypes.byref(t), lo, hi), "sfft_plan_general_round_info")
+    return dict(B=B.value, T=T.value, kprime=kp.value, dmax=dmax.value, t=t.value,
+                beta_lo=[int(lo[i]) for i in range(dmax.value)], beta_hi=[int(hi[i]) for i in range(dmax.value)])
+
+
+def sfft_locate_votes(plan: Plan, r: int, sigma: int, b: int, w_fp: int, beta, u, up, l_fp, valid, votes, stream=None):
+    """One LocateInner level on device bins; l_fp / valid are updated in place, votes [B, t] filled."""
+    _check(lib().sfft_locate_votes(plan.handle, r, sigma, b, w_fp, int(beta.numel()), _ptr(beta), _ptr(u), _ptr(up),
+                                   _ptr(l_fp), _ptr(valid), _ptr(votes), _stream_ptr(stream)), "sfft_locate_votes")
+
+
+def sfft_estimate_from_bins(plan: Plan, r: int, sig, bb, aa, u, L, kprime: int, widx, wval, count, stream=None):
+    """EstimateValues on device bins; returns nothing (outputs in widx, wval, count)."""
+    nL = 0 if L is None else int(L.numel())
+    _check(lib().sfft_estimate_from_bins(plan.handle, r, int(sig.numel()), _ptr(sig), _ptr(bb), _ptr(aa), _ptr(u),
+                                         _ptr(L), nL, kprime, _ptr(widx), _ptr(wval), _ptr(count),
+                                         _stream_ptr(stream)), "sfft_estimate_from_bins")

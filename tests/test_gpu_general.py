@@ -1,0 +1,229 @@
+"""Parity of the CUDA general-case path (Algorithms 2 and 3) with the FP64 oracle, through the C ABI.
+
+* schedule, window widths, beta ranges and draws: bit-exact;
+* one LocateInner level and EstimateValues on the same synthetic FP64 bins: votes, regions, bottoms
+  and the kept indices bit-exact, estimates within 1e-12;
+* whole transforms on noisy signals (FP32 data path against the FP64 oracle): the l2/l2 ratio
+  ||X - zhat|| / Err(X, k) within 1.05x of the oracle's, and the guarantee of the Theorem of Sec. 4.
+  Individual votes near a boundary may differ (FP32 bins), so supports are compared through this
+  ratio, not element by element.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1201_2501_gb300 import workloads
+from tests.common import general_fields, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1201_2501_gb300 import build, sfft
+
+    build.build()
+    sfft.lib()
+    return sfft
+
+
+def gpu_params(sf, fields):
+    p = sf.sfft_params_default(fields["n"], fields["k"], fields["mode"])
+    for name, _ in sf.SfftParams._fields_:
+        if name in fields:
+            setattr(p, name, fields[name])
+    return p
+
+
+@pytest.mark.parametrize("n,k", [(1 << 14, 8), (1 << 18, 64), (1 << 22, 256)])
+def test_general_schedule_matches_oracle(sf, n, k):
+    f = general_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f), 1)
+    ks, Bs = oracle.general_rounds(P)
+    assert plan.rounds == len(Bs)
+    for r, (kr, B) in enumerate(zip(ks, Bs)):
+        g = sf.general_round_info(plan, r)
+        t, tp, dmax = oracle.locate_geometry(P, B)
+        assert (g["B"], g["kprime"], g["dmax"], g["t"]) == (B, 3 * kr, dmax, t)
+        assert g["T"] == oracle.window_T(n, B, P.alpha0, P.delta)
+        for D in range(dmax):
+            w = (n // B) >> (D * int(np.log2(tp)))
+            assert (g["beta_lo"][D], g["beta_hi"][D]) == oracle.beta_range(P, t, w)
+            d = oracle.locate_draws(P, 77, 3, r, B, D + 1, 0)
+            assert g["beta_lo"][D] <= d["beta"] <= g["beta_hi"][D]
+    plan.close()
+
+
+def _noisy_pair_bins(rng, n, B, sigma, b, a, beta, tones, noise):
+    """Bins of the hashings at a and a + beta for planted tones (i, X), with additive noise."""
+    u = np.zeros(B, dtype=np.complex128)
+    up = np.zeros(B, dtype=np.complex128)
+    for i, X in tones:
+        p = (sigma * (i - b)) % n
+        j, _ = oracle.bin_offset(p, n, B)
+        u[j] += X * np.exp(-2j * np.pi * ((a * sigma * i) % n) / n)
+        up[j] += X * np.exp(-2j * np.pi * (((a + beta) * sigma * i) % n) / n)
+    u += noise * (rng.standard_normal(B) + 1j * rng.standard_normal(B))
+    up += noise * (rng.standard_normal(B) + 1j * rng.standard_normal(B))
+    return u, up
+
+
+@pytest.mark.parametrize("n,k,level", [(1 << 16, 32, 0), (1 << 16, 32, 2), (1 << 22, 256, 0), (1 << 22, 256, 4)])
+def test_locate_votes_bit_exact(sf, n, k, level):
+    f = general_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f), 1)
+    g = sf.general_round_info(plan, 0)
+    B, t = g["B"], g["t"]
+    _, tp, _ = oracle.locate_geometry(P, B)
+    F = oracle.FRAC_BITS
+    rng = np.random.default_rng(n + level)
+    sigma, b = int(rng.integers(0, n)) | 1, int(rng.integers(0, n))
+    tones = [(int(i), np.exp(2j * np.pi * rng.uniform()) * (1 + 9 * rng.uniform())) for i in
+             rng.choice(n, size=k, replace=False)]
+    w = (n // B) >> (level * int(np.log2(tp)))
+    us, ups, betas = [], [], []
+    for q in range(P.R_loc):
+        a = int(rng.integers(0, n))
+        beta = int(rng.integers(g["beta_lo"][level], g["beta_hi"][level] + 1))
+        u, up = _noisy_pair_bins(rng, n, B, sigma, b, a, beta, tones, 0.3)
+        us.append(u)
+        ups.append(up)
+        betas.append(beta)
+    Np = n // B
+    l0 = np.array([((j * Np - Np // 2) % n) << F for j in range(B)], dtype=np.uint64)
+    # move the regions of later levels to a random sub-window so that every path is exercised
+    if level:
+        l0 = (l0 + (rng.integers(0, Np - w + 1, size=B).astype(np.uint64) << np.uint64(F))) % np.uint64(n << F)
+    v0 = (rng.uniform(size=B) < 0.9).astype(np.uint8)
+    ol, ov, ovotes = oracle.locate_inner_votes(P, B, sigma, b, t, w << F, betas, np.stack(us), np.stack(ups), l0, v0)
+    cplx = lambda a: torch.as_tensor(np.stack([a.real, a.imag], -1)).cuda()
+    d_l = torch.as_tensor(l0.view(np.int64)).cuda()
+    d_v = torch.as_tensor(v0).cuda()
+    d_votes = torch.zeros((B, t), dtype=torch.int32, device="cuda")
+    sf.sfft_locate_votes(plan, 0, sigma, b, w << F, torch.as_tensor(np.array(betas, dtype=np.int64)).cuda(),
+                         cplx(np.stack(us)), cplx(np.stack(ups)), d_l, d_v, d_votes)
+    torch.cuda.synchronize()
+    gl = d_l.cpu().numpy().view(np.uint64)
+    gv = d_v.cpu().numpy()
+    gvotes = d_votes.cpu().numpy().astype(np.uint32)
+    assert np.array_equal(gv, ov)
+    assert np.array_equal(gvotes[v0 == 1], ovotes[v0 == 1])
+    assert np.array_equal(gl[ov == 1], ol[ov == 1])
+    assert ov.sum() > 0 and (1 - ov[v0 == 1]).sum() > 0  # both outcomes occur
+    plan.close()
+
+
+@pytest.mark.parametrize("n,k", [(1 << 16, 32), (1 << 22, 256)])
+def test_estimate_from_bins_bit_exact(sf, n, k):
+    f = general_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f), 1)
+    g = sf.general_round_info(plan, 0)
+    B = g["B"]
+    rng = np.random.default_rng(n + 5)
+    R = P.R_est
+    sig = (rng.integers(0, n, size=R) | 1).astype(np.uint64)
+    bb = rng.integers(0, n, size=R).astype(np.uint64)
+    aa = rng.integers(0, n, size=R).astype(np.uint64)
+    u = (rng.standard_normal((R, B)) + 1j * rng.standard_normal((R, B))) * 3
+    L = np.sort(rng.choice(n, size=min(B, 3 * k), replace=False)).astype(np.uint64)
+    kprime = g["kprime"] // 2
+    oi, ov = oracle.estimate_from_bins(P, B, P.alpha0, sig, bb, aa, u, L, kprime)
+    cplx = lambda a: torch.as_tensor(np.stack([a.real, a.imag], -1)).cuda()
+    widx = torch.zeros(len(L), dtype=torch.int32, device="cuda")
+    wval = torch.zeros((len(L), 2), dtype=torch.float64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    t64 = lambda a: torch.as_tensor(a.view(np.int64)).cuda()
+    sf.sfft_estimate_from_bins(plan, 0, t64(sig), t64(bb), t64(aa), cplx(u), torch.as_tensor(L.astype(np.int32)).cuda(),
+                               kprime, widx, wval, cnt)
+    torch.cuda.synchronize()
+    c = int(cnt.item())
+    gi = widx.cpu().numpy()[:c].astype(np.uint32)
+    gv = wval.cpu().numpy()[:c]
+    assert c == len(oi)
+    assert np.array_equal(gi.astype(np.uint64), oi)
+    assert np.max(np.abs((gv[:, 0] + 1j * gv[:, 1]) - ov)) <= 1e-12 * max(1.0, np.max(np.abs(ov)))
+    plan.close()
+
+
+def _l2l2(X, zi, zv, k):
+    n = len(X)
+    Z = np.zeros(n, dtype=np.complex128)
+    Z[zi.astype(np.int64)] = zv
+    err = np.sqrt(np.sum(np.sort(np.abs(X) ** 2)[: n - k]))
+    return np.linalg.norm(X - Z) / err
+
+
+def _run_gpu(sf, plan, xs, seed, cap):
+    x = torch.as_tensor(np.stack(xs)).cuda()
+    idx, val, cnt, flag = sf.sfft_execute(plan, x, seed, cap)
+    torch.cuda.synchronize()
+    idx = idx.cpu().numpy().view(np.uint32)
+    val = val.cpu().numpy()
+    cnt = cnt.cpu().numpy()
+    return [(idx[r, :cnt[r]].astype(np.int64), val[r, :cnt[r], 0] + 1j * val[r, :cnt[r], 1], int(flag.cpu()[r]))
+            for r in range(len(xs))]
+
+
+@pytest.mark.parametrize("m,k,batch", [(14, 8, 6), (16, 32, 4), (18, 64, 2)])
+def test_sfft_general_l2l2_matches_oracle(sf, m, k, batch):
+    n = 1 << m
+    f = general_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f), batch)
+    sigs = [workloads.general_noisy(n, k, workloads.seed_for(3, 40 + i)) for i in range(batch)]
+    seed = 555
+    got = _run_gpu(sf, plan, [s.x for s in sigs], seed, f["z_cap"])
+    ratios_g, ratios_o = [], []
+    for r, s in enumerate(sigs):
+        x128 = s.x.astype(np.complex128)
+        X = np.fft.fft(x128)
+        oi, ov, of = oracle.sfft_general(P, x128, seed, r)
+        rg = _l2l2(X, got[r][0], got[r][1], k)
+        ro = _l2l2(X, oi, ov, k)
+        ratios_g.append(rg)
+        ratios_o.append(ro)
+        assert got[r][2] == 0
+        # the bins differ only by FP32 rounding, so most decisions coincide
+        common = len(set(got[r][0].tolist()) & set(oi.astype(np.int64).tolist()))
+        assert common >= 0.9 * min(len(oi), len(got[r][0]))
+    rg, ro = np.mean(ratios_g), np.mean(ratios_o)
+    assert abs(rg / ro - 1.0) <= 0.05, (ratios_g, ratios_o)
+    assert max(ratios_g) <= 1 + P.eps + 0.5  # Theorem of Sec. 4 with eps = 1 (plus delta ||X|| slack)
+    plan.close()
+
+
+def test_sfft_general_is_bit_reproducible(sf):
+    n, k, batch = 1 << 16, 32, 5
+    f = general_fields(n, k)
+    plan = sf.Plan(gpu_params(sf, f), batch)
+    xs = [workloads.general_noisy(n, k, 70 + i).x for i in range(batch)]
+    a = _run_gpu(sf, plan, xs, 9, f["z_cap"])
+    b = _run_gpu(sf, plan, xs, 9, f["z_cap"])
+    for ra, rb in zip(a, b):
+        assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1]) and ra[2] == rb[2]
+    plan.close()
+
+
+def test_sfft_general_full_size_sampled(sf):
+    """n = 2^22, k = 256, SNR 20 dB (the general-case workload), two requests; request 0 against the oracle."""
+    n, k, batch = 1 << 22, 256, 2
+    f = general_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f), batch)
+    sigs = [workloads.general_noisy(n, k, workloads.seed_for(3, i)) for i in range(batch)]
+    got = _run_gpu(sf, plan, [s.x for s in sigs], 321, f["z_cap"])
+    x128 = sigs[0].x.astype(np.complex128)
+    X = np.fft.fft(x128)
+    oi, ov, of = oracle.sfft_general(P, x128, 321, 0)
+    rg, ro = _l2l2(X, got[0][0], got[0][1], k), _l2l2(X, oi, ov, k)
+    assert abs(rg / ro - 1.0) <= 0.05, (rg, ro)
+    X1 = np.fft.fft(sigs[1].x.astype(np.complex128))
+    assert _l2l2(X1, got[1][0], got[1][1], k) <= 1 + P.eps
+    plan.close()
