@@ -260,22 +260,31 @@ struct VoteBounds {
     uint64_t amb0, amb1;  // integers within 0.25 of a boundary (or ~0 when none)
     double c;
 };
-__device__ __forceinline__ VoteBounds vote_bounds(double c, double s, uint64_t M) {
+constexpr int kVoteGuard = 16;  // extra fraction bits of the fixed-point boundaries
+// Boundaries of the vote arc (c - s/2, c + s/2) in units of 1/M, as 64-bit fixed point with
+// kVoteGuard fraction bits: c M 2^G is one exact scaling of c (truncated to an integer, an error
+// below 2^-G units), so only one double operation is spent per (bin, round).
+__device__ __forceinline__ VoteBounds vote_bounds(double c, int64_t hw_fix, uint32_t logM) {
     VoteBounds v;
-    const double Md = (double)M;
-    const double x = c * Md;             // exact: M is a power of two
-    const double hw = 0.5 * s * Md;      // exact for the dyadic s used here; otherwise rounded once
-    const double bl = x - hw, bh = x + hw;
-    const int64_t ilo = (int64_t)floor(bl) + 1;   // smallest integer > bl
-    const int64_t ihi = (int64_t)ceil(bh) - 1;    // largest integer < bh
-    const uint64_t mask = M - 1;
+    const int64_t one = int64_t(1) << kVoteGuard, frac_mask = one - 1;
+    const int64_t xfix = (int64_t)(c * ldexp(1.0, (int)logM + kVoteGuard));
+    const int64_t blf = xfix - hw_fix, bhf = xfix + hw_fix;
+    const uint64_t mask = (uint64_t(1) << logM) - 1;
+    const int64_t ilo = (blf >> kVoteGuard) + 1;                  // smallest integer > bl
+    const int64_t ihi = ((bhf + frac_mask) >> kVoteGuard) - 1;    // largest integer < bh
     v.ilo = (uint64_t)ilo & mask;
     v.len = (uint64_t)(ihi - ilo) & mask;
-    const double rl = rint(bl), rh = rint(bh);
-    v.amb0 = fabs(bl - rl) < 0.25 ? ((uint64_t)(int64_t)rl & mask) : ~0ull;
-    v.amb1 = fabs(bh - rh) < 0.25 ? ((uint64_t)(int64_t)rh & mask) : ~0ull;
+    const int64_t fl = blf & frac_mask, fh = bhf & frac_mask;
+    v.amb0 = fl < one / 4 ? ((uint64_t)(blf >> kVoteGuard) & mask)
+                          : (fl > 3 * (one / 4) ? ((uint64_t)((blf >> kVoteGuard) + 1) & mask) : ~0ull);
+    v.amb1 = fh < one / 4 ? ((uint64_t)(bhf >> kVoteGuard) & mask)
+                          : (fh > 3 * (one / 4) ? ((uint64_t)((bhf >> kVoteGuard) + 1) & mask) : ~0ull);
     v.c = c;
     return v;
+}
+// half width s M / 2 of the vote arc in the same fixed point
+__device__ __forceinline__ int64_t vote_halfwidth(double s, uint32_t logM) {
+    return (int64_t)llrint(0.5 * s * ldexp(1.0, (int)logM + kVoteGuard));
 }
 __device__ __forceinline__ bool vote_hit(const VoteBounds& v, uint64_t e, uint64_t M, double s) {
     if (e == v.amb0 || e == v.amb1) {
@@ -291,16 +300,18 @@ __device__ __forceinline__ bool vote_hit(const VoteBounds& v, uint64_t e, uint64
 // most votes among those with a majority; bottom when no subregion has one).
 // phase(q) returns c_j of LocateInner round q; beta[q] its beta.
 template <typename PhaseFn>
-__device__ void locate_bin(uint32_t j, uint32_t t, uint32_t nrep, const uint64_t* beta, PhaseFn phase, uint64_t sb_fp,
-                           uint64_t w_fp, uint64_t M, double s, uint64_t* l_fp, uint8_t* valid, uint32_t* votes_out) {
+__device__ void locate_bin(uint32_t t, uint32_t nrep, const uint64_t* beta, PhaseFn phase, uint64_t sb_fp,
+                           uint64_t w_fp, uint32_t logM, double s, int64_t hw_fix, uint64_t& l_fp, uint8_t& valid,
+                           uint32_t* votes_out) {
     uint8_t v[kMaxT];
     for (uint32_t q = 0; q < t; ++q) v[q] = 0;
+    const uint64_t M = uint64_t(1) << logM;
     const uint64_t mask = M - 1;
     const uint64_t half_step = w_fp / (2 * (uint64_t)t), step = w_fp / t;
     for (uint32_t r = 0; r < nrep; ++r) {
-        const VoteBounds vb = vote_bounds(phase(r), s, M);
+        const VoteBounds vb = vote_bounds(phase(r), hw_fix, logM);
         // e_q = beta (m_q + sigma b) mod M, m_q = l + (2q - 1) w / 2t, advanced by beta w / t
-        uint64_t e = (beta[r] * ((l_fp[j] + half_step + sb_fp) & mask)) & mask;
+        uint64_t e = (beta[r] * ((l_fp + half_step + sb_fp) & mask)) & mask;
         const uint64_t de = (beta[r] * step) & mask;
         for (uint32_t q = 0; q < t; ++q) {
             if (vote_hit(vb, e, M, s)) v[q] += 1;
@@ -312,7 +323,7 @@ __device__ void locate_bin(uint32_t j, uint32_t t, uint32_t nrep, const uint64_t
     bool any = false;
     for (uint32_t q = 0; q < t; ++q) any = any || 2u * v[q] > nrep;
     if (!any) {
-        valid[j] = 0;
+        valid = 0;
         return;
     }
     uint32_t best = 0, best_sum = 0;
@@ -323,18 +334,12 @@ __device__ void locate_bin(uint32_t j, uint32_t t, uint32_t nrep, const uint64_t
             best_sum = sum;
         }
     }
-    l_fp[j] = (l_fp[j] + (uint64_t)best * step) & mask;
+    l_fp = (l_fp + (uint64_t)best * step) & mask;
 }
 
 size_t general_locate_smem(uint32_t B) {
-    size_t off = 0;
-    gtake(&off, (size_t)B * 8);           // regions
-    gtake(&off, (size_t)B);               // valid
-    gtake(&off, (size_t)B * 4);           // candidate keys
-    gtake(&off, (size_t)B * 4);           // sorted keys
-    gtake(&off, (size_t)B * 4);           // keep flags
-    gtake(&off, (size_t)(kThreads + 8) * 4);
-    return off;
+    (void)B;
+    return 0;
 }
 
 // Sorts the m keys of key[] ascending and removes duplicates: the distinct keys end up in
@@ -358,30 +363,27 @@ __device__ uint32_t sort_unique_u32(uint32_t* key, uint32_t m, uint32_t* tmp, ui
     return total;
 }
 
+// LocateSignal for one bin per thread: the bins of a request are independent until L is formed, so
+// a request spreads over ceil(B / kThreads) CTAs.  The candidate of bin j (pi^{-1} of the integer
+// nearest the centre of its last region, or ~0 for bottom) goes to L[s B + j]; EstimateValues sorts
+// and de-duplicates them.
 __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t s_beta[kMaxRloc];
-    const uint32_t s = a.req_base + blockIdx.x, tid = threadIdx.x, B = a.B;
-    size_t off = 0;
-    uint64_t* l_fp = reinterpret_cast<uint64_t*>(smem + gtake(&off, (size_t)B * 8));
-    uint8_t* valid = reinterpret_cast<uint8_t*>(smem + gtake(&off, (size_t)B));
-    uint32_t* cand = reinterpret_cast<uint32_t*>(smem + gtake(&off, (size_t)B * 4));
-    uint32_t* srt = reinterpret_cast<uint32_t*>(smem + gtake(&off, (size_t)B * 4));
-    uint32_t* keep = reinterpret_cast<uint32_t*>(smem + gtake(&off, (size_t)B * 4));
-    uint32_t* scan = reinterpret_cast<uint32_t*>(smem + gtake(&off, (size_t)(kThreads + 8) * 4));
-    __shared__ uint32_t s_nc;
+    const uint32_t s = a.req_base + blockIdx.y, tid = threadIdx.x;
+    const uint32_t j = blockIdx.x * kThreads + tid;
+    const uint32_t B = a.B;
     uint32_t sigma, b;
     locate_sigma_b(a.seed, s, a.round, a.nmask, &sigma, &b);
     const uint64_t n = a.n, Np = n >> a.logB;
-    const uint64_t M = n << kFracBits;
+    const uint32_t logM = (uint32_t)(63 - __clzll((long long)n)) + kFracBits;
+    const int64_t hw_fix = vote_halfwidth(a.s, logM);
     const uint64_t sb_fp = ((uint64_t)((sigma * b) & a.nmask)) << kFracBits;
-    for (uint32_t j = tid; j < B; j += kThreads) {  // regions centred on the bins: [j n/B - n/2B, +n/B)
-        l_fp[j] = ((((uint64_t)j * Np) + n - Np / 2) & (n - 1)) << kFracBits;
-        valid[j] = 1;
-    }
-    if (tid == 0) s_nc = 0;
+    // the region of bin j starts centred on the bin: [j n/B - n/2B, + n/B)
+    uint64_t l_fp = ((((uint64_t)j * Np) + n - Np / 2) & (n - 1)) << kFracBits;
+    uint8_t valid = j < B ? 1 : 0;
     const double* phase = a.phase + (size_t)s * a.phase_stride;
     for (uint32_t D = 0; D < a.dmax; ++D) {
+        __syncthreads();
         if (tid < a.R_loc) {
             uint32_t aa;
             uint64_t be;
@@ -389,36 +391,27 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
             s_beta[tid] = be;
         }
         __syncthreads();
+        if (!valid) continue;
         const uint64_t w_fp = (Np << kFracBits) >> ((uint64_t)D * a.logtp);
         const double* ph = phase + (size_t)D * a.R_loc * B;
-        for (uint32_t j = tid; j < B; j += kThreads) {
-            if (!valid[j]) continue;
-            locate_bin(j, a.t, a.R_loc, s_beta, [&](uint32_t r) { return ph[(size_t)r * B + j]; }, sb_fp, w_fp, M, a.s,
-                       l_fp, valid, nullptr);
-        }
-        __syncthreads();
+        locate_bin(a.t, a.R_loc, s_beta, [&](uint32_t r) { return ph[(size_t)r * B + j]; }, sb_fp, w_fp, logM, a.s,
+                   hw_fix, l_fp, valid, nullptr);
     }
-    // L = {pi^{-1}(tau_j)}: tau_j the integer nearest the centre of the last region
-    const uint64_t wlast = (Np << kFracBits) >> ((uint64_t)a.dmax * a.logtp);
-    const uint32_t sigma_inv = inverse_odd(sigma) & a.nmask;
-    for (uint32_t j = tid; j < B; j += kThreads) {
-        if (!valid[j]) continue;
-        const uint32_t tau = (uint32_t)(((l_fp[j] + wlast / 2 + (1ull << (kFracBits - 1))) >> kFracBits) & (n - 1));
-        const uint32_t slot = atomicAdd(&s_nc, 1u);
-        cand[slot] = (sigma_inv * tau + b) & a.nmask;
+    if (j >= B) return;
+    uint32_t cand = 0xFFFFFFFFu;
+    if (valid) {
+        const uint64_t wlast = (Np << kFracBits) >> ((uint64_t)a.dmax * a.logtp);
+        const uint32_t tau = (uint32_t)(((l_fp + wlast / 2 + (1ull << (kFracBits - 1))) >> kFracBits) & (n - 1));
+        cand = ((inverse_odd(sigma) & a.nmask) * tau + b) & a.nmask;
     }
-    __syncthreads();
-    const uint32_t m = s_nc;
-    const uint32_t nu = sort_unique_u32(cand, m, srt, keep, scan);
-    for (uint32_t p = tid; p < nu; p += kThreads) a.L[(size_t)s * B + p] = cand[p];
-    if (tid == 0) a.nL[s] = nu;
+    a.L[(size_t)s * B + j] = cand;
 }
 
 // ------------------------------------------------------------------------------------------------
 // 4. EstimateValues, top k', zhat += w_J
 // ------------------------------------------------------------------------------------------------
 struct EstLayout {
-    size_t w, mag, perm, topi, topv, out_idx, out_val, keep, scan, draws, total;
+    size_t w, mag, perm, topi, topv, out_idx, out_val, keep, scan, draws, Lk, Lt, total;
     uint32_t P;
 };
 __host__ __device__ inline EstLayout est_layout(uint32_t B, uint32_t kprime, uint32_t zcap) {
@@ -437,6 +430,8 @@ __host__ __device__ inline EstLayout est_layout(uint32_t B, uint32_t kprime, uin
     L.keep = gtake(&off, (size_t)(zcap + kprime > B ? zcap + kprime : B) * 4);
     L.scan = gtake(&off, (size_t)(kThreads + 8) * 4);
     L.draws = gtake(&off, (size_t)kMaxRest * 3 * 8);
+    L.Lk = gtake(&off, (size_t)B * 4);
+    L.Lt = gtake(&off, (size_t)B * 4);
     L.total = off;
     return L;
 }
@@ -529,8 +524,20 @@ __global__ void __launch_bounds__(kThreads) k_gen_estimate(const GenArgs a) {
         dr[2 * kMaxRest + tid] = w.w[2] & a.nmask;
     }
     __syncthreads();
-    const uint32_t nL = a.nL[s];
-    const uint32_t* L = a.L + (size_t)s * B;
+    // L: the candidates of the bins that LocateSignal did not reject, sorted and de-duplicated
+    uint32_t* Lk = reinterpret_cast<uint32_t*>(smem + Ly.Lk);
+    uint32_t* Lt = reinterpret_cast<uint32_t*>(smem + Ly.Lt);
+    __shared__ uint32_t s_m;
+    if (tid == 0) s_m = 0;
+    __syncthreads();
+    for (uint32_t j = tid; j < B; j += kThreads) {
+        const uint32_t c = a.L[(size_t)s * B + j];
+        if (c != 0xFFFFFFFFu) Lk[atomicAdd(&s_m, 1u)] = c;
+    }
+    __syncthreads();
+    const uint32_t nL = sort_unique_u32(Lk, s_m, Lt, keep, scan);
+    const uint32_t* L = Lk;
+    if (tid == 0) a.nL[s] = nL;
     const double2* bins = a.bins + (size_t)s * a.bins_stride + (size_t)2 * a.npairs * B;
     const uint32_t logNp = (uint32_t)(63 - __clzll((long long)a.n)) - a.logB;
     for (uint32_t c = tid; c < nL; c += kThreads) {
@@ -618,16 +625,21 @@ __global__ void __launch_bounds__(kThreads) k_gen_estimate(const GenArgs a) {
 // single-step kernels on caller bins
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_locate_votes(const VoteArgs a) {
-    const uint64_t M = a.n << kFracBits;
+    const uint32_t logM = (uint32_t)(63 - __clzll((long long)a.n)) + kFracBits;
+    const int64_t hw_fix = vote_halfwidth(a.s, logM);
     const uint64_t sb_fp = ((uint64_t)((a.sigma * a.b) & a.nmask)) << kFracBits;
     for (uint32_t j = threadIdx.x; j < a.B; j += kThreads) {
         for (uint32_t q = 0; q < a.t; ++q) a.votes[(size_t)j * a.t + q] = 0;
         if (!a.valid[j]) continue;
-        locate_bin(j, a.t, a.nrep, a.beta,
+        uint64_t l = a.l_fp[j];
+        uint8_t v = 1;
+        locate_bin(a.t, a.nrep, a.beta,
                    [&](uint32_t r) {
                        return phase01<double>(mul_conj_rn(a.u[(size_t)r * a.B + j], a.up[(size_t)r * a.B + j]));
                    },
-                   sb_fp, a.w_fp, M, a.s, a.l_fp, a.valid, a.votes + (size_t)j * a.t);
+                   sb_fp, a.w_fp, logM, a.s, hw_fix, l, v, a.votes + (size_t)j * a.t);
+        a.l_fp[j] = l;
+        a.valid[j] = v;
     }
 }
 
@@ -699,7 +711,7 @@ cudaError_t launch_general_round(const GenArgs& a, uint32_t batch, const General
     if (e != cudaSuccess) return e;
     k_gen_finish<<<dim3(r.ngroups, batch), kThreads, r.smem_finish, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_gen_locate<<<batch, kThreads, r.smem_locate, st>>>(a);
+    k_gen_locate<<<dim3((r.B + kThreads - 1) / kThreads, batch), kThreads, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_gen_estimate<<<batch, kThreads, r.smem_estimate, st>>>(a);
     return cudaGetLastError();
