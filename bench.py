@@ -128,6 +128,38 @@ def max_over_ranks(v, world):
     return float(t.item())
 
 
+KERNEL_SOURCES = ("sfft_exact.cu", "sfft_device.cuh", "sfft_internal.h", "philox.cuh")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_exact_round_n22_k64_b256_launches.md")
+
+
+def kernel_fingerprint():
+    """First 16 hex digits of sha256 over the sha256 hex digests of the exact round kernel's sources."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1201_2501_gb300", "csrc", f), "rb") as fh:
+            h.update(hashlib.sha256(fh.read()).hexdigest().encode())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) of one step of the round kernel, from the committed ncu launch list
+    of the same workload; None when the kernel sources changed since that capture."""
+    import re
+
+    try:
+        with open(TRAFFIC_PROFILE) as f:
+            text = f.read()
+    except OSError:
+        return None
+    fp = re.search(r"sources_sha256_16 = ([0-9a-f]{16})", text)
+    tr = re.search(r"traffic_per_step_bytes = (\d+)", text)
+    if not fp or not tr or fp.group(1) != kernel_fingerprint():
+        return None
+    return int(tr.group(1))
+
+
 def launch_groups(batch, streams):
     """Stream groups sfft_execute splits an exact-mode batch into (one round kernel each per round)."""
     g = streams if streams else 4
@@ -327,7 +359,7 @@ def run_ours(args):
                        "l2": "inputs (8 GiB per GPU) exceed L2; no flush", "parallelism": f"replicas x{world}",
                        "support_exact_fraction": exact / batch},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak, "traffic": profiled_traffic() if batch == 256 else None,
                          "kernel": "k_exact_round (all rounds of a step)",
                          "bytes_per_transform": bytes_tr, "samples_per_transform": samples_tr,
                          "peak_kind": peak_kind},
@@ -468,7 +500,7 @@ def general_measurement(sfft, stream, args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=256)
