@@ -149,6 +149,118 @@ sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64
 sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, uint64_t seed, void* stream,
                               uint32_t* h_idx, double* h_val, uint32_t cap, uint32_t* h_count, int32_t* h_flag);
 
+/*
+ * One request of sfft_execute_requests: its own signal, seed and request index.  The result depends
+ * on (signal, params, seed, id) only, not on the batch or slot the request runs in: request r of
+ * sfft_execute with seed s equals a request {row r, s, r}.
+ */
+typedef struct sfft_request {
+    const void* d_x;    /* device signal: n complex values of the plan's precision, 8-byte (FP32) or
+                           16-byte (FP64) aligned; caller-owned, valid until the work completes */
+    uint64_t seed;      /* Philox key of the request's draws */
+    uint32_t id;        /* request index of the Philox counter */
+    uint32_t reserved;  /* 0 */
+} sfft_request;
+
+/*
+ * sfft_execute over `batch` independent requests (batch <= max_batch) whose signals lie anywhere in
+ * device memory.  The table h_reqs (host memory) is copied into the plan before the call returns, so
+ * it may be reused at once; the outputs are laid out as for sfft_execute (slot r = h_reqs[r]).
+ * A plan serves one stream at a time: the table copy and the kernels go to `stream`.
+ * Errors: INVALID_ARG (null pointer, batch out of range, cap == 0, a null or misaligned d_x), CUDA.
+ */
+sfft_status sfft_execute_requests(sfft_plan plan, const sfft_request* h_reqs, uint32_t batch, void* stream,
+                                  uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Serving: continuous batching of independent transforms                                         */
+/* ---------------------------------------------------------------------------------------------- */
+/*
+ * The paper has no serving layer; this one runs its transforms as a service.  A server owns a
+ * dispatcher thread on the device current at creation.  Jobs of any (n, k, mode, ...) are submitted
+ * from any thread.  The dispatcher:
+ *   - keeps one resident plan set per distinct sfft_params (window taps, W tables and workspace stay
+ *     on the device between jobs; the least recently used idle sets beyond max_plans are released);
+ *   - admits jobs in submission order: a job whose signal is in host memory is admitted once its
+ *     device copy fits in mem_budget (resident plans count against it too), and its copy starts on a
+ *     copy stream at once; a job whose signal is already on the device is admitted immediately;
+ *   - launches, for each parameter set with admitted jobs and an idle plan instance, one batch of up
+ *     to max_batch of them (sfft_execute_requests), so jobs that arrive while earlier batches run on
+ *     the GPU are batched into the next launch as instances free up, and batches of different
+ *     parameter sets and instances overlap on the device;
+ *   - when a batch completes, copies each job's results to its host arrays, frees its staging memory
+ *     and marks it done.
+ * A job's result equals that of the same request run alone (same params, signal, seed and id),
+ * bit for bit.
+ */
+typedef struct sfft_server_s* sfft_server;
+
+typedef struct sfft_server_config {
+    uint64_t mem_budget;  /* device bytes for resident plans and staged signals; 0 -> half of the
+                             free device memory at creation */
+    uint32_t max_batch;   /* jobs per launch; 0 -> 64 */
+    uint32_t instances;   /* plan instances per parameter set (batches of one set in flight at once);
+                             0 -> 2 */
+    uint32_t max_plans;   /* resident parameter sets; 0 -> 16 */
+    uint32_t reserved;    /* 0 */
+} sfft_server_config;
+
+typedef struct sfft_job {
+    const void* x;        /* the signal: n complex values of the params' precision */
+    uint32_t x_on_device; /* 1: device memory, read in place (valid until the job completes);
+                             0: host memory, copied on admission (page-locked copies fastest; the
+                             array may be reused once the job completes) */
+    uint32_t id;          /* request index of the job's draws */
+    uint64_t seed;        /* Philox key of the job's draws */
+    uint32_t* h_idx;      /* host output: up to cap recovered frequencies, ascending */
+    double* h_val;        /* host output: their values as (re, im) doubles */
+    uint32_t cap;         /* capacity of h_idx / h_val (entries) */
+    uint32_t reserved;    /* 0 */
+} sfft_job;
+
+typedef struct sfft_job_result {
+    uint32_t count;       /* entries written (<= cap) */
+    int32_t flag;         /* the transform's status: OK, NOT_CONVERGED or CAPACITY */
+    double queued_us;     /* submission to launch */
+    double latency_us;    /* submission to completion (host clock) */
+} sfft_job_result;
+
+typedef struct sfft_server_stats {
+    uint64_t submitted, completed, failed;
+    uint64_t launches;    /* batches launched */
+    uint64_t plans;       /* resident plan instances */
+    uint64_t bytes_in_use, bytes_peak;  /* device bytes held (plans + staged signals) */
+    double mean_batch;    /* jobs per launch */
+    double p50_us, p99_us;  /* latency of the jobs completed so far */
+} sfft_server_stats;
+
+/* Start a server (NULL cfg -> all defaults).  Errors: INVALID_ARG, CUDA (no device), OOM. */
+sfft_status sfft_server_create(const sfft_server_config* cfg, sfft_server* out);
+
+/* Finish every submitted job, stop the dispatcher and release all memory.  NULL is accepted. */
+sfft_status sfft_server_destroy(sfft_server s);
+
+/*
+ * Queue one job; *ticket names it.  The params and the job description are copied.
+ * Errors: INVALID_ARG (null, bad params, null outputs, cap == 0), N_NOT_POW2, K_RANGE, OOM (the job's
+ * signal and plan can never fit in mem_budget), BUSY (the server is being destroyed).
+ */
+sfft_status sfft_submit(sfft_server s, const sfft_params* p, const sfft_job* job, uint64_t* ticket);
+
+/* OK: done (results written); BUSY: not done yet; INVALID_ARG: unknown ticket; another status: the
+ * job failed (e.g. CUDA, OOM at plan creation). */
+sfft_status sfft_poll(sfft_server s, uint64_t ticket);
+
+/*
+ * Wait up to timeout_us for a job.  On OK the job is done, *res (if not NULL) describes it and the
+ * ticket is released; on TIMEOUT it is still pending; on another error status it failed (and is
+ * released).  INVALID_ARG: unknown ticket.
+ */
+sfft_status sfft_wait(sfft_server s, uint64_t ticket, uint64_t timeout_us, sfft_job_result* res);
+
+/* Counters and latency percentiles since creation. */
+sfft_status sfft_server_stats_get(sfft_server s, sfft_server_stats* st);
+
 /* ---------------------------------------------------------------------------------------------- */
 /* Single steps (for parity tests and for callers that drive the rounds themselves)               */
 /* ---------------------------------------------------------------------------------------------- */

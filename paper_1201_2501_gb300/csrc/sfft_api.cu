@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -54,6 +55,7 @@ void free_plan(sfft_plan_s* pl) {
     cudaFree(pl->d_zflag);
     cudaFree(pl->d_ubins);
     cudaFree(pl->d_aux);
+    cudaFree(pl->d_reqs);
     cudaFree(pl->d_stage);
     cudaFree(pl->d_out_idx);
     cudaFree(pl->d_out_val);
@@ -115,6 +117,19 @@ ExactArgs base_args(const sfft_plan_s* pl, const ExactRound& r, uint32_t t) {
 
 }  // namespace
 
+// sfft_execute_requests copies the caller's table byte for byte into the device table
+static_assert(sizeof(ReqDesc) == sizeof(sfft_request), "request table layout");
+static_assert(offsetof(ReqDesc, x) == offsetof(sfft_request, d_x) && offsetof(ReqDesc, seed) == offsetof(sfft_request, seed) &&
+                  offsetof(ReqDesc, id) == offsetof(sfft_request, id),
+              "request table layout");
+
+sfft_status sfft::validate_params(const sfft_params* p) {
+    const sfft_status st = validate(p);
+    if (st != SFFT_OK) return st;
+    if (p->mode == SFFT_GENERAL && p->precision != SFFT_FP32) return SFFT_ERR_INVALID_ARG;
+    return SFFT_OK;
+}
+
 extern "C" {
 
 sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan* out) {
@@ -165,6 +180,7 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
 #define SFFT_ALLOC(ptr, bytes)                                        \
     do {                                                              \
         e = cudaMalloc((void**)&(ptr), (bytes));                      \
+        pl->dev_bytes += (bytes);                                     \
         if (e != cudaSuccess) {                                       \
             set_last_error(std::string("cudaMalloc: ") + cudaGetErrorString(e)); \
             free_plan(pl);                                            \
@@ -182,6 +198,7 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
     SFFT_ALLOC(pl->d_zflag, (size_t)max_batch * sizeof(int32_t));
     SFFT_ALLOC(pl->d_ubins, (size_t)maxB * kMaxHash * sizeof(double2));
     SFFT_ALLOC(pl->d_aux, 64 * sizeof(uint32_t));
+    SFFT_ALLOC(pl->d_reqs, (size_t)max_batch * sizeof(ReqDesc));
     if (general) {
         SFFT_ALLOC(pl->d_bins, pl->bins_stride * max_batch * sizeof(double2));
         SFFT_ALLOC(pl->d_phase, pl->phase_stride * max_batch * sizeof(double));
@@ -282,7 +299,8 @@ sfft_status sfft_plan_taps(sfft_plan plan, uint32_t t, double* h_taps, uint64_t 
     return SFFT_OK;
 }
 
-static sfft_status execute_general(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, cudaStream_t st,
+static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDesc* d_reqs, uint32_t batch,
+                                   uint64_t seed, cudaStream_t st,
                                    uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag) {
     const sfft_params& p = plan->p;
     SFFT_CUDA(cudaMemsetAsync(plan->d_zcount, 0, batch * sizeof(uint32_t), st), "clear zhat");
@@ -303,6 +321,7 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, uint32_t bat
             GenArgs a;
             std::memset(&a, 0, sizeof(a));
             a.x = reinterpret_cast<const float2*>(d_x);
+            a.reqs = d_reqs;
             a.n = p.n;
             a.nmask = (uint32_t)(p.n - 1);
             a.seed = seed;
@@ -360,12 +379,15 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, uint32_t bat
     return SFFT_OK;
 }
 
-sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, void* stream,
-                         uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag) {
-    if (!plan || !d_x || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
-    if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (plan->p.mode == SFFT_GENERAL) return execute_general(plan, d_x, batch, seed, st, d_idx, d_val, cap, d_count, d_flag);
+}  // extern "C"
+
+// One batch through every round: rows of d_x (d_reqs == nullptr) or the requests of the device table
+// d_reqs.  Arguments are checked by the callers.
+sfft_status sfft::execute_batch(sfft_plan plan, const void* d_x, const ReqDesc* d_reqs, uint32_t batch,
+                                uint64_t seed, cudaStream_t st, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
+                          int32_t* d_flag) {
+    if (plan->p.mode == SFFT_GENERAL)
+        return execute_general(plan, d_x, d_reqs, batch, seed, st, d_idx, d_val, cap, d_count, d_flag);
     const bool fp64 = plan->p.precision == SFFT_FP64;
     SFFT_CUDA(cudaMemsetAsync(plan->d_zcount, 0, batch * sizeof(uint32_t), st), "clear zhat");
     SFFT_CUDA(cudaMemsetAsync(plan->d_zflag, 0, batch * sizeof(int32_t), st), "clear flags");
@@ -388,6 +410,7 @@ sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64
             const ExactRound& r = plan->rounds[t];
             ExactArgs a = base_args(plan, r, t);
             a.x = d_x;
+            a.reqs = d_reqs;
             a.seed = seed;
             a.req_base = r0;
             a.first_round = t == 0;
@@ -405,6 +428,29 @@ sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64
         }
     }
     return SFFT_OK;
+}
+
+extern "C" {
+
+sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, void* stream,
+                         uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag) {
+    if (!plan || !d_x || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
+    if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
+    return execute_batch(plan, d_x, nullptr, batch, seed, (cudaStream_t)stream, d_idx, d_val, cap, d_count, d_flag);
+}
+
+sfft_status sfft_execute_requests(sfft_plan plan, const sfft_request* h_reqs, uint32_t batch, void* stream,
+                                  uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag) {
+    if (!plan || !h_reqs || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
+    if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
+    const size_t align = plan->p.precision == SFFT_FP64 ? 16 : 8;
+    for (uint32_t r = 0; r < batch; ++r)
+        if (!h_reqs[r].d_x || ((uintptr_t)h_reqs[r].d_x % align) != 0) return SFFT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // a pageable source is staged by the driver before the call returns, so h_reqs may be reused at once
+    SFFT_CUDA(cudaMemcpyAsync(plan->d_reqs, h_reqs, (size_t)batch * sizeof(ReqDesc), cudaMemcpyHostToDevice, st),
+              "copy request table");
+    return execute_batch(plan, nullptr, plan->d_reqs, batch, 0, st, d_idx, d_val, cap, d_count, d_flag);
 }
 
 sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, uint64_t seed, void* stream,

@@ -61,6 +61,18 @@ __device__ __forceinline__ void sincospi_r(double x, double* s, double* c) { sin
 
 // Sample loads are cached in L2 only: the sigma-strided gather touches one 32-byte sector per sample
 // and an L1 fill would fetch the whole 128-byte line.
+// Request s of a launch: its signal row, its seed and the request index its random draws use.
+struct ReqView {
+    const void* x;
+    uint64_t seed;
+    uint32_t id;
+};
+__device__ __forceinline__ ReqView req_view(const ReqDesc* reqs, const void* x, uint64_t row_bytes, uint64_t seed,
+                                            uint32_t s) {
+    if (reqs) return ReqView{reqs[s].x, reqs[s].seed, reqs[s].id};
+    return ReqView{static_cast<const unsigned char*>(x) + (size_t)s * row_bytes, seed, s};
+}
+
 __device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldcg(p); }
 __device__ __forceinline__ double2 ldg_c(const double2* p) { return __ldcg(p); }
 

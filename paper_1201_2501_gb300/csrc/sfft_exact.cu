@@ -194,13 +194,13 @@ __device__ int decode_bin(const DecodeCtx& d, uint32_t j, const double2* u, cons
 // The round kernel
 // ------------------------------------------------------------------------------------------------
 template <typename R>
-__device__ void gather_fold(const ExactArgs& a, uint32_t s, uint32_t c, uint32_t sigma, uint32_t b,
-                            unsigned char* smem) {
+__device__ void gather_fold(const ExactArgs& a, const void* xrow, uint32_t s, uint32_t c, uint32_t sigma,
+                            uint32_t b, unsigned char* smem) {
     using C = typename Cx<R>::T;
     C* stage = reinterpret_cast<C*>(smem);
     C* red = stage + a.stage;
     const uint32_t tid = threadIdx.x;
-    const C* __restrict__ x = reinterpret_cast<const C*>(a.x) + (size_t)s * a.n;
+    const C* __restrict__ x = reinterpret_cast<const C*>(xrow);
     const R* __restrict__ taps = taps_of<R>(a);
     const int64_t t_lo = -a.T + (int64_t)c * kChunkTaps;
     const int64_t t_hi = min(t_lo + (int64_t)kChunkTaps, a.T + 1);
@@ -453,14 +453,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_round(const ExactArgs a) 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_last;
     const uint32_t s = a.req_base + blockIdx.y, c = blockIdx.x;
+    const ReqView rq = req_view(a.reqs, a.x, a.n * sizeof(typename Cx<R>::T), a.seed, s);
     uint32_t sigma, b;
     if (a.bins_only) {
         sigma = a.e_sigma;
         b = a.e_b;
     } else {
-        exact_hash(a.seed, s, a.round, a.nmask, &sigma, &b);
+        exact_hash(rq.seed, rq.id, a.round, a.nmask, &sigma, &b);
     }
-    gather_fold<R>(a, s, c, sigma, b, smem);
+    gather_fold<R>(a, rq.x, s, c, sigma, b, smem);
     // arrival: the last CTA of request s finishes the round (nobody waits)
     __threadfence();
     __syncthreads();

@@ -10,7 +10,8 @@
 //   2. k_gen_finish   every (hashing group, request): partials summed in order, B-point FFT
 //                     (step 3), recovered coefficients subtracted in FP64 (step 4), bins stored;
 //                     for a LocateInner pair also c_j = phase(u_j / u'_j);
-//   3. k_gen_locate   every request: LocateSignal's levels in order, votes, regions, the list L;
+//   3. k_gen_locate   every (bin, request), one thread per bin: LocateSignal's levels in order,
+//                     votes, regions, the bin's candidate for the list L;
 //   4. k_gen_estimate every request: EstimateValues' medians, the top k', zhat += w_J.
 // Reductions run in a fixed order; results are bit-reproducible.
 #include <cuda_runtime.h>
@@ -49,16 +50,16 @@ __device__ __forceinline__ void inner_a_beta(uint64_t seed, uint32_t s, uint32_t
 
 // Group g of a round: g < npairs is LocateInner pair g (hashings a and a + beta under the round's
 // sigma, b); g >= npairs is EstimateValues hashing q = g - npairs with fresh (sigma_q, a_q, b_q).
-__device__ __forceinline__ HashDesc group_desc(const GenArgs& a, uint32_t s, uint32_t g) {
+__device__ __forceinline__ HashDesc group_desc(const GenArgs& a, uint64_t seed, uint32_t id, uint32_t g) {
     HashDesc h;
     if (g < a.npairs) {
-        locate_sigma_b(a.seed, s, a.round, a.nmask, &h.sigma, &h.b);
+        locate_sigma_b(seed, id, a.round, a.nmask, &h.sigma, &h.b);
         const uint32_t D = g / a.R_loc;
-        inner_a_beta(a.seed, s, a.round, g, a.nmask, a.beta_lo[D], a.beta_hi[D], &h.a[0], &h.beta);
+        inner_a_beta(seed, id, a.round, g, a.nmask, a.beta_lo[D], a.beta_hi[D], &h.a[0], &h.beta);
         h.a[1] = (uint32_t)((h.a[0] + h.beta) & a.nmask);
         h.H = 2;
     } else {
-        const Words4 w = draw(a.seed, s, a.round, g - a.npairs, kKindEstimate);
+        const Words4 w = draw(seed, id, a.round, g - a.npairs, kKindEstimate);
         h.sigma = (w.w[0] & a.nmask) | 1u;
         h.b = w.w[1] & a.nmask;
         h.a[0] = w.w[2] & a.nmask;
@@ -67,6 +68,11 @@ __device__ __forceinline__ HashDesc group_desc(const GenArgs& a, uint32_t s, uin
         h.H = 1;
     }
     return h;
+}
+
+// request s of a general-mode launch (signal row, seed, draw index)
+__device__ __forceinline__ ReqView gen_req(const GenArgs& a, uint32_t s) {
+    return req_view(a.reqs, a.x, a.n * sizeof(float2), a.seed, s);
 }
 
 __device__ __forceinline__ uint32_t hash_index(const GenArgs& a, uint32_t g, uint32_t h) {
@@ -88,10 +94,11 @@ __device__ __forceinline__ int32_t gen_offset(uint32_t p, uint32_t n, uint32_t n
 __global__ void __launch_bounds__(kThreads) k_gen_gather(const GenArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t s = a.req_base + blockIdx.z, g = blockIdx.y, c = blockIdx.x, tid = threadIdx.x;
-    const HashDesc h = group_desc(a, s, g);
+    const ReqView rq = gen_req(a, s);
+    const HashDesc h = group_desc(a, rq.seed, rq.id, g);
     float2* stage = reinterpret_cast<float2*>(smem);   // [2][kChunkTaps]
     float2* red = stage + 2 * kChunkTaps;               // [H][max(B, kThreads)]
-    const float2* __restrict__ x = a.x + (size_t)s * a.n;
+    const float2* __restrict__ x = static_cast<const float2*>(rq.x);
     const bool big = a.B > (uint32_t)kThreads;
     if (big)
         for (uint32_t i = tid; i < h.H * a.B; i += kThreads) red[i] = make_float2(0.f, 0.f);
@@ -189,7 +196,8 @@ size_t general_finish_smem(uint32_t B, uint32_t zcap) { return gen_fin_layout(B,
 __global__ void __launch_bounds__(kThreads) k_gen_finish(const GenArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t s = a.req_base + blockIdx.y, g = blockIdx.x, tid = threadIdx.x;
-    const HashDesc h = group_desc(a, s, g);
+    const ReqView rq = gen_req(a, s);
+    const HashDesc h = group_desc(a, rq.seed, rq.id, g);
     const uint32_t B = a.B;
     const GenFinLayout Ly = gen_fin_layout(B, a.zcap);
     float2* U = reinterpret_cast<float2*>(smem + Ly.U);
@@ -372,8 +380,9 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
     const uint32_t s = a.req_base + blockIdx.y, tid = threadIdx.x;
     const uint32_t j = blockIdx.x * kThreads + tid;
     const uint32_t B = a.B;
+    const ReqView rq = gen_req(a, s);
     uint32_t sigma, b;
-    locate_sigma_b(a.seed, s, a.round, a.nmask, &sigma, &b);
+    locate_sigma_b(rq.seed, rq.id, a.round, a.nmask, &sigma, &b);
     const uint64_t n = a.n, Np = n >> a.logB;
     const uint32_t logM = (uint32_t)(63 - __clzll((long long)n)) + kFracBits;
     const int64_t hw_fix = vote_halfwidth(a.s, logM);
@@ -387,7 +396,7 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
         if (tid < a.R_loc) {
             uint32_t aa;
             uint64_t be;
-            inner_a_beta(a.seed, s, a.round, D * a.R_loc + tid, a.nmask, a.beta_lo[D], a.beta_hi[D], &aa, &be);
+            inner_a_beta(rq.seed, rq.id, a.round, D * a.R_loc + tid, a.nmask, a.beta_lo[D], a.beta_hi[D], &aa, &be);
             s_beta[tid] = be;
         }
         __syncthreads();
@@ -517,8 +526,9 @@ __global__ void __launch_bounds__(kThreads) k_gen_estimate(const GenArgs a) {
     uint32_t* keep = reinterpret_cast<uint32_t*>(smem + Ly.keep);
     uint32_t* scan = reinterpret_cast<uint32_t*>(smem + Ly.scan);
     uint64_t* dr = reinterpret_cast<uint64_t*>(smem + Ly.draws);  // sigma, b, a per hashing
+    const ReqView rq = gen_req(a, s);
     if (tid < a.R_est) {
-        const Words4 w = draw(a.seed, s, a.round, tid, kKindEstimate);
+        const Words4 w = draw(rq.seed, rq.id, a.round, tid, kKindEstimate);
         dr[tid] = (w.w[0] & a.nmask) | 1u;
         dr[kMaxRest + tid] = w.w[1] & a.nmask;
         dr[2 * kMaxRest + tid] = w.w[2] & a.nmask;

@@ -17,6 +17,17 @@ constexpr int kMaxHash = 4;       // hashings per exact round: a = 0 plus up to 
 constexpr uint32_t kMaxB = 4096;  // largest B of the fused exact round
 constexpr uint32_t kNoIndex = 0xFFFFFFFFu;
 
+// Per-request descriptor of a launch (device table, optional).  Without a table, request s of a
+// launch reads row s of the batch and draws its hashings with the launch's seed and request index s;
+// with one, request s reads x, draws with (seed, id), so its result does not depend on which slot of
+// which launch it ran in.
+struct ReqDesc {
+    const void* x;
+    uint64_t seed;
+    uint32_t id;
+    uint32_t reserved;
+};
+
 // One round of the exact schedule (Algorithm 1's loop t = 0..log k, with this library's readings).
 struct ExactRound {
     uint32_t B = 0, logB = 0;
@@ -39,6 +50,7 @@ struct ExactArgs {
     uint64_t seed;
     uint32_t round;
     uint32_t req_base;         // request index of blockIdx.y == 0 (a launch may cover part of a batch)
+    const ReqDesc* reqs;       // optional per-request table (see ReqDesc)
     uint32_t B, logB;
     int64_t T;
     uint32_t H;                // hashings: hashing h uses offset a_base + a[h]
@@ -120,6 +132,7 @@ struct GenArgs {
     uint64_t seed;
     uint32_t round;
     uint32_t req_base;     // request index of the launch's first request
+    const ReqDesc* reqs;   // optional per-request table (see ReqDesc)
     uint32_t B, logB;
     int64_t T;
     uint32_t chunks, cpb, ctas;
@@ -209,6 +222,8 @@ struct sfft_plan_s {
     // single-step helpers
     double2* d_ubins = nullptr;
     uint32_t* d_aux = nullptr;
+    sfft::ReqDesc* d_reqs = nullptr;  // [max_batch] request table of sfft_execute_requests
+    size_t dev_bytes = 0;          // device memory allocated at plan creation
     // internal streams: a batch is split into groups whose rounds run on their own streams
     static constexpr int kMaxStreams = 8;
     uint32_t nstreams = 1;
@@ -226,8 +241,15 @@ struct sfft_plan_s {
 };
 
 namespace sfft {
-// host-side plan construction (sfft_host.cpp)
+// the checks sfft_plan_create applies to a parameter set (without allocating anything)
+sfft_status validate_params(const sfft_params* p);
+// host-side plan construction (sfft_host.cu)
 sfft_status build_exact_schedule(sfft_plan_s* pl);
+// One batch through every round of the plan's mode: rows of d_x, or the device request table d_reqs
+// when it is not null (then d_x and seed are unused).  Arguments are checked by the callers.
+sfft_status execute_batch(sfft_plan_s* plan, const void* d_x, const ReqDesc* d_reqs, uint32_t batch, uint64_t seed,
+                          cudaStream_t st, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
+                          int32_t* d_flag);
 void window_taps_host(uint64_t n, uint32_t B, double alpha, double delta, int64_t T, double* g);
 void window_table_host(uint64_t n, const double* g, int64_t T, uint64_t len, double* W);
 int64_t window_halfwidth(uint32_t B, double alpha, double delta);

@@ -62,6 +62,44 @@ class SfftParams(ctypes.Structure):
     ]
 
 
+class SfftRequest(ctypes.Structure):
+    """Mirror of ``sfft_request``."""
+
+    _fields_ = [("d_x", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("id", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class SfftServerConfig(ctypes.Structure):
+    """Mirror of ``sfft_server_config``."""
+
+    _fields_ = [("mem_budget", ctypes.c_uint64), ("max_batch", ctypes.c_uint32), ("instances", ctypes.c_uint32),
+                ("max_plans", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class SfftJob(ctypes.Structure):
+    """Mirror of ``sfft_job``."""
+
+    _fields_ = [("x", ctypes.c_void_p), ("x_on_device", ctypes.c_uint32), ("id", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("h_idx", ctypes.c_void_p), ("h_val", ctypes.c_void_p),
+                ("cap", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class SfftJobResult(ctypes.Structure):
+    """Mirror of ``sfft_job_result``."""
+
+    _fields_ = [("count", ctypes.c_uint32), ("flag", ctypes.c_int32), ("queued_us", ctypes.c_double),
+                ("latency_us", ctypes.c_double)]
+
+
+class SfftServerStats(ctypes.Structure):
+    """Mirror of ``sfft_server_stats``."""
+
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("plans", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64),
+                ("bytes_peak", ctypes.c_uint64), ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double)]
+
+
 class SfftError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -98,6 +136,13 @@ _SIGS = {
     "sfft_locate_votes": (ctypes.c_int, [_vp, _u32, _u64, _u64, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sfft_estimate_from_bins": (ctypes.c_int, [_vp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _u32, _u32, _vp, _vp, _vp,
                                                _vp]),
+    "sfft_execute_requests": (ctypes.c_int, [_vp, ctypes.POINTER(SfftRequest), _u32, _vp, _vp, _vp, _u32, _vp, _vp]),
+    "sfft_server_create": (ctypes.c_int, [ctypes.POINTER(SfftServerConfig), ctypes.POINTER(_vp)]),
+    "sfft_server_destroy": (ctypes.c_int, [_vp]),
+    "sfft_submit": (ctypes.c_int, [_vp, _P, ctypes.POINTER(SfftJob), _u64p]),
+    "sfft_poll": (ctypes.c_int, [_vp, _u64]),
+    "sfft_wait": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(SfftJobResult)]),
+    "sfft_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(SfftServerStats)]),
 }
 
 SFFT_STATIC_SCRATCH_BYTES = 4 * 1024 * 1024
@@ -241,6 +286,100 @@ def sfft_execute_host(plan: Plan, x, seed: int, cap: int, outputs=None, stream=N
     _check(lib().sfft_execute_host(plan.handle, _ptr(x), batch, seed, _stream_ptr(stream), _ptr(idx), _ptr(val), cap,
                                    _ptr(count), _ptr(flag)), "sfft_execute_host")
     return outputs
+
+
+def sfft_execute_requests(plan: Plan, xs, seeds, ids, cap: int, outputs=None, stream=None):
+    """Run independent requests: ``xs`` a list of device tensors (n values each, anywhere in memory),
+    request r drawing with (seeds[r], ids[r]).  Outputs as for sfft_execute, slot r = request r."""
+    import torch
+
+    batch = len(xs)
+    if outputs is None:
+        dev = xs[0].device
+        outputs = (torch.empty((batch, cap), dtype=torch.int32, device=dev),
+                   torch.empty((batch, cap, 2), dtype=torch.float64, device=dev),
+                   torch.empty((batch,), dtype=torch.int32, device=dev),
+                   torch.empty((batch,), dtype=torch.int32, device=dev))
+    table = (SfftRequest * batch)()
+    for r, (x, sd, i) in enumerate(zip(xs, seeds, ids)):
+        table[r].d_x = _ptr(x)
+        table[r].seed = int(sd)
+        table[r].id = int(i)
+        table[r].reserved = 0
+    idx, val, count, flag = outputs
+    _check(lib().sfft_execute_requests(plan.handle, table, batch, _stream_ptr(stream), _ptr(idx), _ptr(val), cap,
+                                       _ptr(count), _ptr(flag)), "sfft_execute_requests")
+    return outputs
+
+
+class Server:
+    """Continuous-batching server (``sfft_server_*``, ``sfft_submit``, ``sfft_poll``, ``sfft_wait``).
+
+    ``submit`` takes a signal tensor (host or device; it must stay alive and unchanged until the job
+    completes, which this object ensures by holding a reference) and returns a ticket; ``wait``
+    returns (indices int64, values complex128, result dict) with the host arrays the server wrote."""
+
+    def __init__(self, mem_budget: int = 0, max_batch: int = 0, instances: int = 0, max_plans: int = 0):
+        import numpy as np  # noqa: F401  (output arrays)
+
+        cfg = SfftServerConfig(mem_budget, max_batch, instances, max_plans, 0)
+        h = ctypes.c_void_p()
+        _check(lib().sfft_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sfft_server_create")
+        self.handle = h
+        self._live = {}
+        self._mu = threading.Lock()
+
+    def submit(self, params: SfftParams, x, seed: int, id: int = 0, cap: int = 0) -> int:
+        import numpy as np
+
+        cap = cap or params.z_cap
+        on_dev = bool(getattr(x, "is_cuda", False))
+        if not on_dev and hasattr(x, "is_contiguous") and not x.is_contiguous():
+            x = x.contiguous()
+        idx = np.empty(cap, dtype=np.uint32)
+        val = np.empty((cap, 2), dtype=np.float64)
+        job = SfftJob(_ptr(x) if hasattr(x, "data_ptr") else x.ctypes.data, 1 if on_dev else 0, id, seed,
+                      idx.ctypes.data, val.ctypes.data, cap, 0)
+        t = ctypes.c_uint64()
+        _check(lib().sfft_submit(self.handle, ctypes.byref(params), ctypes.byref(job), ctypes.byref(t)),
+               "sfft_submit")
+        with self._mu:
+            self._live[t.value] = (x, idx, val)
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        return lib().sfft_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        import numpy as np
+
+        res = SfftJobResult()
+        st = lib().sfft_wait(self.handle, ticket, int(timeout_s * 1e6), ctypes.byref(res))
+        if st == SFFT_ERR_TIMEOUT:
+            raise TimeoutError(f"sfft_wait: job {ticket} still pending after {timeout_s} s")
+        with self._mu:
+            x, idx, val = self._live.pop(ticket, (None, None, None))
+        _check(st, "sfft_wait")
+        c = res.count
+        out = {"count": c, "flag": res.flag, "queued_us": res.queued_us, "latency_us": res.latency_us}
+        return idx[:c].astype(np.int64), val[:c, 0] + 1j * val[:c, 1], out
+
+    def stats(self) -> dict:
+        st = SfftServerStats()
+        _check(lib().sfft_server_stats_get(self.handle, ctypes.byref(st)), "sfft_server_stats_get")
+        return {f: getattr(st, f) for f, _ in SfftServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().sfft_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sfft_hash_to_bins(plan: Plan, t: int, x, sigma: int, a: int, b: int, zidx=None, zval=None, out=None,

@@ -61,3 +61,48 @@ def test_params_default_and_struct_layout(built_lib):
     for f in FIELDS_DEFAULT:
         assert hasattr(p, f)
 
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """sizeof and every field offset of the ctypes mirrors equal the C compiler's for include/sfft.h."""
+    import ctypes
+
+    from paper_1201_2501_gb300 import sfft
+
+    mirrors = {"sfft_params": sfft.SfftParams, "sfft_request": sfft.SfftRequest,
+               "sfft_server_config": sfft.SfftServerConfig, "sfft_job": sfft.SfftJob,
+               "sfft_job_result": sfft.SfftJobResult, "sfft_server_stats": sfft.SfftServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sfft.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, f, v = line.split()
+        got[(cname, f)] = int(v)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_server_create_without_a_device_fails_cleanly(built_lib):
+    """With no CUDA device the server reports SFFT_ERR_CUDA and hands out no handle."""
+    import ctypes
+
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_1201_2501_gb300 import sfft
+
+    h = ctypes.c_void_p(123)
+    st = sfft.lib().sfft_server_create(None, ctypes.byref(h))
+    assert st == sfft.SFFT_ERR_CUDA
+    assert not h.value
+    assert sfft.lib().sfft_server_destroy(None) == sfft.SFFT_OK
