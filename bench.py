@@ -118,14 +118,23 @@ def barrier(world):
 
 
 def max_over_ranks(v, world):
+    """The largest v over the ranks (a CUDA tensor under NCCL, a CPU tensor under gloo)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(units_per_rank, world, steps, ms_local):
+    """Whole-job throughput of N independent replicas: all ranks' units over the slowest rank's time.
+    Returns (units/s, slowest rank's ms)."""
+    ms_max = max_over_ranks(ms_local, world)
+    return units_per_rank * world * steps / (ms_max / 1000.0), ms_max
 
 
 KERNEL_SOURCES = ("sfft_exact.cu", "sfft_device.cuh", "sfft_internal.h", "philox.cuh")
@@ -325,8 +334,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     barrier(world)
     ms = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(ms, world)
-    value = batch * world * args.steps / (ms_max / 1000.0)
+    value, ms_max = replica_value(batch, world, args.steps, ms)
     ms_step = ms_max / args.steps
     bytes_tr, samples_tr = algorithmic_bytes_per_transform(plan)
     hbm_peak, peak_kind = _peaks()
