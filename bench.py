@@ -485,7 +485,137 @@ def context_measurements(sfft, plan, x, cap, stream, args):
     del idx, dst
     if not args.no_general:
         out["general_case"] = general_measurement(sfft, stream, args)
+    if not args.no_serving:
+        out["serving"] = serving_measurement(sfft, args)
     return out
+
+
+SERVE_EXPS = (16, 18, 20, 22)
+SERVE_K_EXACT = (8, 32, 128, 512)
+SERVE_K_GENERAL = (8, 32, 128)
+
+
+def _serve_stream(srv, sigs, params, seq, rate, seed):
+    """Submits `seq` (type, instance) as a Poisson process of `rate` requests/s (None: all at once)
+    while a second thread waits for completions.  Returns (requests/s from the first submission to
+    the last completion, latencies in us, mean batch of the launches this stream caused)."""
+    import queue
+    import threading
+
+    q = queue.Queue()
+    lat = []
+
+    def waiter():
+        for _ in range(len(seq)):
+            t = q.get()
+            _, _, info = srv.wait(t, timeout_s=300)
+            lat.append(info["latency_us"])
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    st0 = srv.stats()
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=len(seq)) if rate else np.zeros(len(seq))
+    t0 = time.perf_counter()
+    due = t0
+    for r, (ti, i) in enumerate(seq):
+        due += gaps[r]
+        while True:
+            d = due - time.perf_counter()
+            if d <= 0:
+                break
+            if d > 2e-4:
+                time.sleep(d - 1e-4)
+        q.put(srv.submit(params[ti], sigs[(ti, i)], SEED, id=r))
+    th.join()
+    el = time.perf_counter() - t0
+    st1 = srv.stats()
+    launches = st1["launches"] - st0["launches"]
+    return len(seq) / el, lat, len(seq) / max(1, launches)
+
+
+def _pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(q * len(v)))]
+
+
+def serving_measurement(sfft, args):
+    """Serving: requests of uneven n and k arrive as a Poisson process and go through the continuous-
+    batching server (sfft_submit / sfft_wait) with every signal resident on the device.  Throughput and
+    p50/p99 latency at swept arrival rates (fractions of the rate the server sustains when everything
+    arrives at once), beside the same requests as serial single-request GPU sFFT calls and as serial
+    cuFFT dense FFTs."""
+    import torch
+
+    from paper_1201_2501_gb300 import workloads
+
+    types = [(e, k, sfft.SFFT_EXACT) for e in SERVE_EXPS for k in SERVE_K_EXACT]
+    types += [(e, k, sfft.SFFT_GENERAL) for e in SERVE_EXPS for k in SERVE_K_GENERAL]
+    per_type = 2
+    sigs = {}
+    for ti, (e, k, mode) in enumerate(types):
+        for i in range(per_type):
+            sigs[(ti, i)] = workloads.sparse_signal_device(1 << e, k, workloads.seed_for(5, 100 * ti + i), "cuda",
+                                                           snr_db=None if mode == sfft.SFFT_EXACT else 20.0)[0]
+    params = [sfft.sfft_params_default(1 << e, k, mode, delta=DELTA) for (e, k, mode) in types]
+    rng = np.random.default_rng(0x5EED5000)
+    seq = [(int(rng.integers(len(types))), int(rng.integers(per_type))) for _ in range(args.serve_requests)]
+    srv = sfft.Server(max_batch=64, instances=2, max_plans=len(types) + 4)
+    _serve_stream(srv, sigs, params, [(ti, 0) for ti in range(len(types))] * 2, None, 1)  # plans built
+    thr_all, lat_all, mb_all = _serve_stream(srv, sigs, params, seq, None, 2)
+    rates = []
+    for frac in (0.25, 0.5, 0.8):
+        lam = frac * thr_all
+        thr, lat, mb = _serve_stream(srv, sigs, params, seq, lam, int(frac * 100))
+        rates.append({"offered_per_s": lam, "throughput_per_s": thr, "p50_us": _pct(lat, 0.5),
+                      "p99_us": _pct(lat, 0.99), "mean_batch": mb})
+    srv.close()
+    # the same requests one at a time: plain GPU sFFT calls, then cuFFT, each synchronised
+    sub = seq[: min(len(seq), args.serve_serial)]
+    plans = {}
+    outs = {}
+    for ti, _ in sub:
+        if ti not in plans:
+            plans[ti] = sfft.Plan(params[ti], 1)
+            outs[ti] = sfft.sfft_execute(plans[ti], sigs[(ti, 0)][None], SEED, params[ti].z_cap)
+    torch.cuda.synchronize()
+    plain = []
+    t0 = time.perf_counter()
+    for r, (ti, i) in enumerate(sub):
+        a = time.perf_counter()
+        sfft.sfft_execute_requests(plans[ti], [sigs[(ti, i)]], [SEED], [r], params[ti].z_cap, outs[ti])
+        torch.cuda.synchronize()
+        plain.append((time.perf_counter() - a) * 1e6)
+    plain_el = time.perf_counter() - t0
+    for pl in plans.values():
+        pl.close()
+    for ti, i in sub[:20]:
+        torch.fft.fft(sigs[(ti, i)])
+    torch.cuda.synchronize()
+    dense = []
+    t0 = time.perf_counter()
+    for ti, i in sub:
+        a = time.perf_counter()
+        torch.fft.fft(sigs[(ti, i)])
+        torch.cuda.synchronize()
+        dense.append((time.perf_counter() - a) * 1e6)
+    dense_el = time.perf_counter() - t0
+    del sigs
+    torch.cuda.empty_cache()
+    return {
+        "workload": "n = 2^e, e uniform on {16,18,20,22}; half exactly k-sparse (k uniform on {8,32,128,512}), "
+                    "half k heavy + complex Gaussian time noise at SNR 20 dB (k uniform on {8,32,128}); "
+                    f"{len(types)} parameter sets x {per_type} resident signals; Poisson arrivals; "
+                    "latency = submission to completion on the host clock",
+        "requests": len(seq),
+        "all_at_once": {"throughput_per_s": thr_all, "p50_us": _pct(lat_all, 0.5), "p99_us": _pct(lat_all, 0.99),
+                        "mean_batch": mb_all},
+        "poisson": rates,
+        "serial_plain_gpu_sfft": {"throughput_per_s": len(sub) / plain_el, "p50_us": _pct(plain, 0.5),
+                                  "p99_us": _pct(plain, 0.99), "requests": len(sub)},
+        "serial_cufft": {"throughput_per_s": len(sub) / dense_el, "p50_us": _pct(dense, 0.5),
+                         "p99_us": _pct(dense, 0.99), "requests": len(sub),
+                         "what": "torch.fft.fft (cuFFT C2C) of each request's signal, one at a time"},
+    }
 
 
 def general_measurement(sfft, stream, args):
@@ -542,6 +672,9 @@ def main():
     ap.add_argument("--no-context", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-general", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-serial", type=int, default=400)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -2,6 +2,7 @@
 // single steps.  Everything here is host code that validates arguments and enqueues kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -56,6 +57,9 @@ void free_plan(sfft_plan_s* pl) {
     cudaFree(pl->d_ubins);
     cudaFree(pl->d_aux);
     cudaFree(pl->d_reqs);
+    cudaFree(pl->d_fin);
+    cudaFree(pl->d_gfin);
+    cudaFree(pl->d_gest);
     cudaFree(pl->d_stage);
     cudaFree(pl->d_out_idx);
     cudaFree(pl->d_out_val);
@@ -99,6 +103,8 @@ ExactArgs base_args(const sfft_plan_s* pl, const ExactRound& r, uint32_t t) {
     a.wtab = pl->d_wtab + r.wtab_off;
     a.part = pl->d_part;
     a.part_stride = pl->part_stride;
+    a.fin_scratch = r.fin_global ? pl->d_fin : nullptr;
+    a.fin_stride = pl->fin_stride;
     a.counter = pl->d_counter;
     a.zidx = pl->d_zidx;
     a.zval = pl->d_zval;
@@ -130,9 +136,9 @@ sfft_status sfft::validate_params(const sfft_params* p) {
     return SFFT_OK;
 }
 
-extern "C" {
-
-sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan* out) {
+// Plan creation; with `tables` (a plan of the same parameters) its schedule and host window tables
+// are copied instead of computed again.
+sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sfft_plan_s* tables, sfft_plan* out) {
     if (!out) return SFFT_ERR_INVALID_ARG;
     *out = nullptr;
     sfft_status st = validate(p);
@@ -145,7 +151,15 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
     pl->p = *p;
     pl->max_batch = max_batch;
     cudaGetDevice(&pl->device);
-    st = general ? build_general_schedule(pl) : build_exact_schedule(pl);
+    if (tables) {
+        pl->rounds = tables->rounds;
+        pl->grounds = tables->grounds;
+        pl->taps_host = tables->taps_host;
+        pl->wtab_host = tables->wtab_host;
+        pl->wtab_len = tables->wtab_len;
+    } else {
+        st = general ? build_general_schedule(pl) : build_exact_schedule(pl);
+    }
     if (st != SFFT_OK) {
         free_plan(pl);
         return st;
@@ -162,6 +176,7 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
         if (e > part_elems) part_elems = e;
         if (r.smem > max_smem) max_smem = r.smem;
         if (r.B > maxB) maxB = r.B;
+        if (r.fin_global && r.fin_bytes > pl->fin_stride) pl->fin_stride = (r.fin_bytes + 255) & ~size_t(255);
     }
     for (const GeneralRound& r : pl->grounds) {
         const size_t e = (size_t)r.ngroups * r.ctas * 2 * r.B;
@@ -170,9 +185,15 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
         if ((size_t)r.npairs * r.B > pl->phase_stride) pl->phase_stride = (size_t)r.npairs * r.B;
         if (r.B > maxB) maxB = r.B;
         gs_max = r.smem_gather > gs_max ? r.smem_gather : gs_max;
-        fs_max = r.smem_finish > fs_max ? r.smem_finish : fs_max;
+        if (r.fin_global) {
+            pl->gfin_stride = std::max(pl->gfin_stride, (r.smem_finish + 255) & ~size_t(255));
+            pl->gfin_groups = std::max(pl->gfin_groups, (size_t)r.ngroups);
+        } else {
+            fs_max = r.smem_finish > fs_max ? r.smem_finish : fs_max;
+        }
+        if (r.est_global) pl->gest_stride = std::max(pl->gest_stride, (r.smem_estimate + 255) & ~size_t(255));
         ls_max = r.smem_locate > ls_max ? r.smem_locate : ls_max;
-        es_max = r.smem_estimate > es_max ? r.smem_estimate : es_max;
+        if (!r.est_global) es_max = r.smem_estimate > es_max ? r.smem_estimate : es_max;
     }
     pl->part_stride = part_elems;
     pl->part_bytes = part_elems * (size_t)max_batch * (fp64 ? 16 : 8);
@@ -199,6 +220,9 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
     SFFT_ALLOC(pl->d_ubins, (size_t)maxB * kMaxHash * sizeof(double2));
     SFFT_ALLOC(pl->d_aux, 64 * sizeof(uint32_t));
     SFFT_ALLOC(pl->d_reqs, (size_t)max_batch * sizeof(ReqDesc));
+    if (pl->fin_stride) SFFT_ALLOC(pl->d_fin, pl->fin_stride * max_batch);
+    if (pl->gfin_stride) SFFT_ALLOC(pl->d_gfin, pl->gfin_stride * pl->gfin_groups * max_batch);
+    if (pl->gest_stride) SFFT_ALLOC(pl->d_gest, pl->gest_stride * max_batch);
     if (general) {
         SFFT_ALLOC(pl->d_bins, pl->bins_stride * max_batch * sizeof(double2));
         SFFT_ALLOC(pl->d_phase, pl->phase_stride * max_batch * sizeof(double));
@@ -241,6 +265,12 @@ sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "plan synchronise");
     *out = pl;
     return SFFT_OK;
+}
+
+extern "C" {
+
+sfft_status sfft_plan_create(const sfft_params* p, uint32_t max_batch, sfft_plan* out) {
+    return plan_create(p, max_batch, nullptr, out);
 }
 
 sfft_status sfft_plan_destroy(sfft_plan plan) {
@@ -352,6 +382,10 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
             a.wtab = plan->d_wtab + gr.wtab_off;
             a.part = reinterpret_cast<float2*>(plan->d_part);
             a.part_stride = plan->part_stride;
+            a.fin_scratch = gr.fin_global ? plan->d_gfin : nullptr;
+            a.fin_stride = plan->gfin_stride;
+            a.est_scratch = gr.est_global ? plan->d_gest : nullptr;
+            a.est_stride = plan->gest_stride;
             a.bins = plan->d_bins;
             a.phase = plan->d_phase;
             a.bins_stride = plan->bins_stride;

@@ -12,6 +12,8 @@
 // Every reduction has a fixed order and no floating-point atomics exist, so results are
 // bit-reproducible.
 #include <cuda_runtime.h>
+
+#include <mutex>
 #include <stdint.h>
 
 #include "philox.cuh"
@@ -469,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_round(const ExactArgs a) 
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    finish_round<R>(a, s, sigma, b, smem);
+    finish_round<R>(a, s, sigma, b, a.fin_scratch ? a.fin_scratch + (size_t)s * a.fin_stride : smem);
     if (threadIdx.x == 0) a.counter[s] = 0;
 }
 
@@ -558,6 +560,8 @@ __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uin
 // The dynamic shared-memory ceiling of a kernel is process-wide: it is only ever raised, so a plan
 // created later with smaller rounds cannot lower it under another plan's feet.
 cudaError_t set_exact_smem_limit(size_t bytes, bool fp64) {
+    static std::mutex mu;  // plans may be created from several threads
+    std::lock_guard<std::mutex> lk(mu);
     static size_t limit[2] = {0, 0};
     size_t& cur = limit[fp64 ? 1 : 0];
     if (bytes <= cur) return cudaSuccess;

@@ -15,6 +15,8 @@
 //   4. k_gen_estimate every request: EstimateValues' medians, the top k', zhat += w_J.
 // Reductions run in a fixed order; results are bit-reproducible.
 #include <cuda_runtime.h>
+
+#include <mutex>
 #include <stdint.h>
 
 #include "philox.cuh"
@@ -200,14 +202,16 @@ __global__ void __launch_bounds__(kThreads) k_gen_finish(const GenArgs a) {
     const HashDesc h = group_desc(a, rq.seed, rq.id, g);
     const uint32_t B = a.B;
     const GenFinLayout Ly = gen_fin_layout(B, a.zcap);
-    float2* U = reinterpret_cast<float2*>(smem + Ly.U);
-    uint32_t* ent_idx = reinterpret_cast<uint32_t*>(smem + Ly.ent_idx);
-    uint32_t* ent_bin = reinterpret_cast<uint32_t*>(smem + Ly.ent_bin);
-    double2* ent_sub = reinterpret_cast<double2*>(smem + Ly.ent_sub);
-    uint32_t* bin_cnt = reinterpret_cast<uint32_t*>(smem + Ly.bin_cnt);
-    uint32_t* bin_start = reinterpret_cast<uint32_t*>(smem + Ly.bin_start);
-    uint32_t* bin_list = reinterpret_cast<uint32_t*>(smem + Ly.bin_list);
-    uint32_t* scan = reinterpret_cast<uint32_t*>(smem + Ly.scan);
+    // the arrays live in shared memory, or in this (request, group)'s slice of fin_scratch when large
+    unsigned char* fb = a.fin_scratch ? a.fin_scratch + ((size_t)s * a.ngroups + g) * a.fin_stride : smem;
+    float2* U = reinterpret_cast<float2*>(fb + Ly.U);
+    uint32_t* ent_idx = reinterpret_cast<uint32_t*>(fb + Ly.ent_idx);
+    uint32_t* ent_bin = reinterpret_cast<uint32_t*>(fb + Ly.ent_bin);
+    double2* ent_sub = reinterpret_cast<double2*>(fb + Ly.ent_sub);
+    uint32_t* bin_cnt = reinterpret_cast<uint32_t*>(fb + Ly.bin_cnt);
+    uint32_t* bin_start = reinterpret_cast<uint32_t*>(fb + Ly.bin_start);
+    uint32_t* bin_list = reinterpret_cast<uint32_t*>(fb + Ly.bin_list);
+    uint32_t* scan = reinterpret_cast<uint32_t*>(fb + Ly.scan);
     const uint32_t logNp = (uint32_t)(63 - __clzll((long long)a.n)) - a.logB;
     // steps 2-3: partial folds summed in chunk order, bit-reversed, B-point FFT per hashing
     const float2* part = a.part + (size_t)s * a.part_stride + (size_t)g * a.ctas * 2 * B;
@@ -516,16 +520,18 @@ __global__ void __launch_bounds__(kThreads) k_gen_estimate(const GenArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t s = a.req_base + blockIdx.x, tid = threadIdx.x, B = a.B;
     const EstLayout Ly = est_layout(B, a.kprime, a.zcap);
-    double2* wv = reinterpret_cast<double2*>(smem + Ly.w);
-    double* mag = reinterpret_cast<double*>(smem + Ly.mag);
-    uint32_t* perm = reinterpret_cast<uint32_t*>(smem + Ly.perm);
-    uint32_t* topi = reinterpret_cast<uint32_t*>(smem + Ly.topi);
-    double2* topv = reinterpret_cast<double2*>(smem + Ly.topv);
-    uint32_t* out_idx = reinterpret_cast<uint32_t*>(smem + Ly.out_idx);
-    double2* out_val = reinterpret_cast<double2*>(smem + Ly.out_val);
-    uint32_t* keep = reinterpret_cast<uint32_t*>(smem + Ly.keep);
-    uint32_t* scan = reinterpret_cast<uint32_t*>(smem + Ly.scan);
-    uint64_t* dr = reinterpret_cast<uint64_t*>(smem + Ly.draws);  // sigma, b, a per hashing
+    // the arrays live in shared memory, or in this request's slice of est_scratch when large
+    unsigned char* eb = a.est_scratch ? a.est_scratch + (size_t)s * a.est_stride : smem;
+    double2* wv = reinterpret_cast<double2*>(eb + Ly.w);
+    double* mag = reinterpret_cast<double*>(eb + Ly.mag);
+    uint32_t* perm = reinterpret_cast<uint32_t*>(eb + Ly.perm);
+    uint32_t* topi = reinterpret_cast<uint32_t*>(eb + Ly.topi);
+    double2* topv = reinterpret_cast<double2*>(eb + Ly.topv);
+    uint32_t* out_idx = reinterpret_cast<uint32_t*>(eb + Ly.out_idx);
+    double2* out_val = reinterpret_cast<double2*>(eb + Ly.out_val);
+    uint32_t* keep = reinterpret_cast<uint32_t*>(eb + Ly.keep);
+    uint32_t* scan = reinterpret_cast<uint32_t*>(eb + Ly.scan);
+    uint64_t* dr = reinterpret_cast<uint64_t*>(eb + Ly.draws);  // sigma, b, a per hashing
     const ReqView rq = gen_req(a, s);
     if (tid < a.R_est) {
         const Words4 w = draw(rq.seed, rq.id, a.round, tid, kKindEstimate);
@@ -535,8 +541,8 @@ __global__ void __launch_bounds__(kThreads) k_gen_estimate(const GenArgs a) {
     }
     __syncthreads();
     // L: the candidates of the bins that LocateSignal did not reject, sorted and de-duplicated
-    uint32_t* Lk = reinterpret_cast<uint32_t*>(smem + Ly.Lk);
-    uint32_t* Lt = reinterpret_cast<uint32_t*>(smem + Ly.Lt);
+    uint32_t* Lk = reinterpret_cast<uint32_t*>(eb + Ly.Lk);
+    uint32_t* Lt = reinterpret_cast<uint32_t*>(eb + Ly.Lt);
     __shared__ uint32_t s_m;
     if (tid == 0) s_m = 0;
     __syncthreads();
@@ -692,6 +698,8 @@ __global__ void __launch_bounds__(kThreads) k_estimate_from_bins(const EstArgs a
 // launchers
 // ------------------------------------------------------------------------------------------------
 cudaError_t general_set_smem(size_t gather, size_t finish, size_t locate, size_t estimate) {
+    static std::mutex mu;  // plans may be created from several threads
+    std::lock_guard<std::mutex> lk(mu);
     static size_t lim[4] = {0, 0, 0, 0};
     cudaError_t e = cudaSuccess;
     if (gather > lim[0] && (e = cudaFuncSetAttribute(k_gen_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -719,11 +727,11 @@ cudaError_t launch_general_round(const GenArgs& a, uint32_t batch, const General
     k_gen_gather<<<dim3(r.ctas, r.ngroups, batch), kThreads, r.smem_gather, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_gen_finish<<<dim3(r.ngroups, batch), kThreads, r.smem_finish, st>>>(a);
+    k_gen_finish<<<dim3(r.ngroups, batch), kThreads, r.fin_global ? 0 : r.smem_finish, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_gen_locate<<<dim3((r.B + kThreads - 1) / kThreads, batch), kThreads, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_gen_estimate<<<batch, kThreads, r.smem_estimate, st>>>(a);
+    k_gen_estimate<<<batch, kThreads, r.est_global ? 0 : r.smem_estimate, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -163,7 +163,10 @@ sfft_status build_exact_schedule(sfft_plan_s* pl) {
         const size_t gs = exact_gather_smem(r.stage, fp64) + (size_t)(1 + r.nshift) * (B > (uint64_t)kThreads ? B : kThreads) *
                                                               (fp64 ? 16 : 8);
         const size_t fs = exact_finish_smem(r.B, 1 + r.nshift, p.z_cap, fp64);
-        r.smem = gs > fs ? gs : fs;
+        // a finisher that does not fit next to the gather's staging keeps its arrays in device memory
+        r.fin_bytes = fs;
+        r.fin_global = fs > kFinSmemMax;
+        r.smem = r.fin_global ? gs : (gs > fs ? gs : fs);
         if (r.smem > 200 * 1024) return SFFT_ERR_K_RANGE;
         pl->taps_host.resize(taps_off + (size_t)r.T + 1);
         window_taps_host(p.n, r.B, r.alpha, p.delta, r.T, pl->taps_host.data() + taps_off);
@@ -196,7 +199,7 @@ sfft_status build_general_schedule(sfft_plan_s* pl) {
     if (t < 8 || t > (uint32_t)kMaxT || (t & (t - 1))) return SFFT_ERR_INVALID_ARG;
     if (p.R_loc == 0 || p.R_loc > (uint32_t)kMaxRloc || p.R_est == 0 || p.R_est > (uint32_t)kMaxRest)
         return SFFT_ERR_INVALID_ARG;
-    if (p.z_cap > 2048) return SFFT_ERR_INVALID_ARG;
+    if (p.z_cap > 4096) return SFFT_ERR_INVALID_ARG;
     const uint32_t tp = t / 4, logtp = ceil_log2(tp);
     size_t taps_off = 0, wtab_off = 0;
     for (uint64_t kr = p.k; kr >= 1; kr /= 4) {
@@ -236,8 +239,10 @@ sfft_status build_general_schedule(sfft_plan_s* pl) {
         r.smem_finish = general_finish_smem(r.B, p.z_cap);
         r.smem_locate = general_locate_smem(r.B);
         r.smem_estimate = general_estimate_smem(r.B, r.kprime, p.z_cap);
-        const size_t lim = 200 * 1024;
-        if (r.smem_finish > lim || r.smem_locate > lim || r.smem_estimate > lim) return SFFT_ERR_K_RANGE;
+        // arrays beyond kFinSmemMax go to device memory (one CTA per request and group uses them)
+        r.fin_global = r.smem_finish > kFinSmemMax;
+        r.est_global = r.smem_estimate > kFinSmemMax;
+        if (r.smem_gather > 200 * 1024 || r.smem_locate > 200 * 1024) return SFFT_ERR_K_RANGE;
         const uint64_t Np = p.n / B;
         pl->taps_host.resize(taps_off + (size_t)r.T + 1);
         window_taps_host(p.n, r.B, p.alpha0, p.delta, r.T, pl->taps_host.data() + taps_off);

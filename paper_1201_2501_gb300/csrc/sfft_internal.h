@@ -16,6 +16,7 @@ constexpr int kChunkTaps = 2048;  // taps per CTA in the gather phase (8 per thr
 constexpr int kMaxHash = 4;       // hashings per exact round: a = 0 plus up to 3 ladder shifts
 constexpr uint32_t kMaxB = 4096;  // largest B of the fused exact round
 constexpr uint32_t kNoIndex = 0xFFFFFFFFu;
+constexpr size_t kFinSmemMax = 160 * 1024;  // largest on-chip finisher of the exact round
 
 // Per-request descriptor of a launch (device table, optional).  Without a table, request s of a
 // launch reads row s of the batch and draws its hashings with the launch's seed and request index s;
@@ -40,6 +41,8 @@ struct ExactRound {
     size_t taps_off = 0;      // offset of this round's taps in the tap arrays
     size_t wtab_off = 0;      // offset of this round's W(o), o = 0..n/2B, in the W table
     size_t smem = 0;          // dynamic shared memory of the round kernel
+    bool fin_global = false;  // the finisher's arrays do not fit on chip: they live in d_fin
+    size_t fin_bytes = 0;     // size of the finisher's arrays of one request
 };
 
 // Kernel argument block of the exact round (passed by value).
@@ -78,6 +81,10 @@ struct ExactArgs {
     uint32_t out_cap;
     uint32_t* out_count;
     int32_t* out_flag;
+    // the finisher's arrays: in shared memory (fin_scratch null) or, for large B and zcap, in the
+    // global region [s fin_stride, (s + 1) fin_stride) of fin_scratch (only one CTA per request uses it)
+    unsigned char* fin_scratch;
+    size_t fin_stride;
     // single-hashing mode (sfft_hash_to_bins): explicit (sigma, b), bins written to ubins, no decode
     int bins_only;
     uint32_t e_sigma, e_b, e_nz;
@@ -122,6 +129,7 @@ struct GeneralRound {
     uint32_t npairs = 0, ngroups = 0, nhash = 0;
     size_t taps_off = 0, wtab_off = 0;
     size_t smem_gather = 0, smem_finish = 0, smem_locate = 0, smem_estimate = 0;
+    bool fin_global = false, est_global = false;  // arrays too large for shared memory: in d_gfin / d_gest
 };
 
 // Kernel argument block of the general-mode kernels of one round (passed by value).
@@ -143,6 +151,10 @@ struct GenArgs {
     const double* wtab;
     float2* part;          // [batch][ngroups][ctas][2][B]
     size_t part_stride;    // elements per request
+    unsigned char* fin_scratch;  // k_gen_finish arrays in device memory: [batch][ngroups][fin_stride], or null
+    size_t fin_stride;
+    unsigned char* est_scratch;  // k_gen_estimate arrays in device memory: [batch][est_stride], or null
+    size_t est_stride;
     double2* bins;         // [batch][nhash][B]  (hashing 2g, 2g+1: pair g; 2 npairs + q: estimate q)
     double* phase;         // [batch][npairs][B] phase(u_a conj(u_{a+beta})) / 2 pi
     size_t bins_stride, phase_stride;  // elements per request
@@ -223,6 +235,12 @@ struct sfft_plan_s {
     double2* d_ubins = nullptr;
     uint32_t* d_aux = nullptr;
     sfft::ReqDesc* d_reqs = nullptr;  // [max_batch] request table of sfft_execute_requests
+    unsigned char* d_fin = nullptr;   // [max_batch][fin_stride] finisher arrays of rounds with fin_global
+    size_t fin_stride = 0;
+    unsigned char* d_gfin = nullptr;  // general mode: [max_batch][ngroups][gfin_stride]
+    size_t gfin_stride = 0, gfin_groups = 0;
+    unsigned char* d_gest = nullptr;  // general mode: [max_batch][gest_stride]
+    size_t gest_stride = 0;
     size_t dev_bytes = 0;          // device memory allocated at plan creation
     // internal streams: a batch is split into groups whose rounds run on their own streams
     static constexpr int kMaxStreams = 8;
@@ -241,6 +259,9 @@ struct sfft_plan_s {
 };
 
 namespace sfft {
+// sfft_plan_create; with `tables` (a plan of the same parameters) the host schedule and window
+// tables are copied from it instead of computed
+sfft_status plan_create(const sfft_params* p, uint32_t max_batch, const sfft_plan_s* tables, sfft_plan_s** out);
 // the checks sfft_plan_create applies to a parameter set (without allocating anything)
 sfft_status validate_params(const sfft_params* p);
 // host-side plan construction (sfft_host.cu)

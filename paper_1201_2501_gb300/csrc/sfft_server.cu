@@ -114,6 +114,22 @@ struct ParamSet {
     std::vector<std::unique_ptr<Instance>> inst;
     std::deque<Job*> ready;
     uint64_t last_use = 0;
+    uint32_t pending = 0;          // instances being built by the builder thread
+    sfft_status build_error = SFFT_OK;  // why the set's first instance could not be built
+};
+
+// A plan instance the builder thread is asked for, and what it hands back.
+struct BuildOrder {
+    ParamKey key;
+    sfft_params p;
+    const sfft_plan_s* tables;     // an instance of the same set to copy the host tables from, or null
+    size_t reserved;               // device bytes already counted for it (a copy's size is known)
+};
+struct BuildResult {
+    ParamKey key;
+    std::unique_ptr<Instance> inst;
+    sfft_status status;
+    size_t reserved;
 };
 
 void destroy_instance(Instance* in) {
@@ -151,6 +167,11 @@ struct sfft_server_s {
     uint64_t submitted = 0, completed = 0, failed = 0, launches = 0, launched_jobs = 0, n_inst = 0;
     size_t bytes_in_use = 0, bytes_peak = 0;
     std::vector<double> latencies;
+    std::thread builder;
+    std::condition_variable cv_build;  // wakes the builder
+    std::deque<BuildOrder> orders;
+    std::vector<BuildResult> built;
+    bool builder_stop = false;
 
     // dispatcher-only state
     std::deque<Job*> admit_q;
@@ -192,7 +213,7 @@ cudaEvent_t take_event(sfft_server_s* S) {
 }
 
 bool set_idle(const ParamSet& ps) {
-    if (!ps.ready.empty()) return false;
+    if (!ps.ready.empty() || ps.pending) return false;
     for (const auto& in : ps.inst)
         if (in->busy) return false;
     return true;
@@ -288,10 +309,12 @@ void fail_job(sfft_server_s* S, Job* j, sfft_status st) {
     finish_jobs(S, {j});
 }
 
-Instance* new_instance(sfft_server_s* S, ParamSet& ps, sfft_status* err) {
+// Builds a plan instance (builder thread; touches no server state).
+std::unique_ptr<Instance> build_instance(const sfft_params& p, uint32_t mb, const sfft_plan_s* tables,
+                                         sfft_status* err) {
     auto in = std::make_unique<Instance>();
-    const uint32_t mb = S->cfg.max_batch, zc = ps.p.z_cap;
-    sfft_status st = sfft_plan_create(&ps.p, mb, &in->plan);
+    const uint32_t zc = p.z_cap;
+    sfft_status st = plan_create(&p, mb, tables, &in->plan);
     if (st != SFFT_OK) {
         *err = st;
         return nullptr;
@@ -314,13 +337,83 @@ Instance* new_instance(sfft_server_s* S, ParamSet& ps, sfft_status* err) {
         return nullptr;
     }
     in->bytes = in->plan->dev_bytes + (size_t)mb * zc * 20 + (size_t)mb * 8;
-    account(S, (long long)in->bytes);
+    *err = SFFT_OK;
+    return in;
+}
+
+// The builder thread: plans are built here so that the dispatcher keeps serving other parameter sets
+// (building computes window tables on the host and synchronises the device).
+void builder(sfft_server_s* S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        BuildOrder o;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_build.wait(lk, [&] { return S->builder_stop || !S->orders.empty(); });
+            if (S->orders.empty()) return;
+            o = S->orders.front();
+            S->orders.pop_front();
+        }
+        sfft_status err = SFFT_OK;
+        std::unique_ptr<Instance> in = build_instance(o.p, S->cfg.max_batch, o.tables, &err);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->built.push_back(BuildResult{o.key, std::move(in), err, o.reserved});
+        }
+        S->cv_work.notify_one();
+    }
+}
+
+// Dispatcher: attach finished builds to their sets; a set whose first build failed fails its jobs.
+void collect_builds(sfft_server_s* S) {
+    std::vector<BuildResult> got;
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        ++S->n_inst;
+        got.swap(S->built);
     }
-    ps.inst.push_back(std::move(in));
-    return ps.inst.back().get();
+    for (BuildResult& b : got) {
+        auto it = S->sets.find(b.key);
+        if (it == S->sets.end()) {  // cannot happen: a set with a pending build is never dropped
+            if (b.inst) destroy_instance(b.inst.get());
+            account(S, -(long long)b.reserved);
+            continue;
+        }
+        ParamSet& ps = *it->second;
+        --ps.pending;
+        account(S, (b.inst ? (long long)b.inst->bytes : 0) - (long long)b.reserved);
+        if (b.inst) {
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                ++S->n_inst;
+            }
+            ps.inst.push_back(std::move(b.inst));
+        } else if (ps.inst.empty() && ps.pending == 0) {
+            ps.build_error = b.status;
+            while (!ps.ready.empty()) {
+                Job* j = ps.ready.front();
+                ps.ready.pop_front();
+                fail_job(S, j, b.status);
+            }
+        }
+    }
+}
+
+// Orders one more instance of a set.  The first instance of a set is always built (the set cannot run
+// without it; its size is counted once known); a further one only if a copy of the first fits in the
+// budget, and its size is reserved at once.
+void order_build(sfft_server_s* S, const ParamKey& key, ParamSet& ps) {
+    size_t reserve = 0;
+    if (!ps.inst.empty()) {
+        reserve = ps.inst.front()->bytes;
+        if (!make_room(S, reserve, &key)) return;
+        account(S, (long long)reserve);
+    }
+    ++ps.pending;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->orders.push_back(BuildOrder{key, ps.p, ps.inst.empty() ? nullptr : ps.inst.front()->plan, reserve});
+    }
+    S->cv_build.notify_one();
 }
 
 // 1. completed batches: results to the jobs' host arrays, staging memory back to the cache
@@ -382,6 +475,17 @@ void admit(sfft_server_s* S) {
                 --resident;
             }
         }
+        ParamSet& ps = *it->second;
+        if (ps.inst.empty()) {
+            if (ps.pending == 0 && ps.build_error != SFFT_OK) {  // the set cannot be built
+                S->admit_q.pop_front();
+                fail_job(S, j, ps.build_error);
+                continue;
+            }
+            if (ps.pending == 0) order_build(S, it->first, ps);
+            // a host signal is staged only once its set's plan exists and is counted in the budget
+            if (!j->desc.x_on_device) break;
+        }
         if (!j->desc.x_on_device) {
             void* buf = take_buffer(S, j->x_bytes, j->key);
             if (!buf) {
@@ -423,20 +527,11 @@ void launch(sfft_server_s* S) {
                     in = c.get();
                     break;
                 }
-            if (!in && ps.inst.size() < S->cfg.instances) {
-                sfft_status err = SFFT_OK;
-                in = new_instance(S, ps, &err);
-                if (!in) {
-                    if (!ps.inst.empty()) break;  // wait for the existing instance
-                    while (!ps.ready.empty()) {   // no plan can be built for this set
-                        Job* j = ps.ready.front();
-                        ps.ready.pop_front();
-                        fail_job(S, j, err);
-                    }
-                    break;
-                }
+            if (!in) {
+                // all instances busy (or none yet): ask for one more, and serve the other sets meanwhile
+                if (ps.inst.size() + ps.pending < S->cfg.instances) order_build(S, kv.first, ps);
+                break;
             }
-            if (!in) break;
             const uint32_t batch = (uint32_t)std::min<size_t>(ps.ready.size(), S->cfg.max_batch);
             in->jobs.assign(ps.ready.begin(), ps.ready.begin() + batch);
             ps.ready.erase(ps.ready.begin(), ps.ready.begin() + batch);
@@ -513,15 +608,23 @@ bool any_ready(const sfft_server_s* S) {
     return false;
 }
 
+bool any_pending(const sfft_server_s* S) {
+    for (const auto& kv : S->sets)
+        if (kv.second->pending) return true;
+    return false;
+}
+
 void dispatcher(sfft_server_s* S) {
     cudaSetDevice(S->device);
+    bool stop = false;
     for (;;) {
         std::vector<Job*> fresh;
-        bool stop = false;
         const bool busy = any_busy(S) || any_ready(S) || !S->admit_q.empty();
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            auto wake = [&] { return !S->inbox.empty() || S->stopping || S->gpu_event; };
+            auto wake = [&] {
+                return !S->inbox.empty() || (S->stopping && !stop) || S->gpu_event || !S->built.empty();
+            };
             if (!wake()) {
                 if (busy)
                     S->cv_work.wait_for(lk, std::chrono::microseconds(200), wake);
@@ -534,10 +637,11 @@ void dispatcher(sfft_server_s* S) {
             stop = S->stopping;
         }
         for (Job* j : fresh) S->admit_q.push_back(j);
+        collect_builds(S);
         reap(S);
         admit(S);
         launch(S);
-        if (stop && S->admit_q.empty() && !any_busy(S) && !any_ready(S)) {
+        if (stop && S->admit_q.empty() && !any_busy(S) && !any_ready(S) && !any_pending(S)) {
             std::lock_guard<std::mutex> lk(S->mu);
             if (S->inbox.empty()) break;
         }
@@ -584,8 +688,15 @@ sfft_status sfft_server_create(const sfft_server_config* cfg, sfft_server* out) 
         return SFFT_ERR_CUDA;
     }
     try {
+        S->builder = std::thread(builder, S);
         S->thread = std::thread(dispatcher, S);
     } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->builder_stop = true;
+        }
+        S->cv_build.notify_one();
+        if (S->builder.joinable()) S->builder.join();
         cudaStreamDestroy(S->copy_stream);
         delete S;
         return SFFT_ERR_OOM;
@@ -602,7 +713,15 @@ sfft_status sfft_server_destroy(sfft_server S) {
     }
     S->cv_work.notify_one();
     if (S->thread.joinable()) S->thread.join();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->builder_stop = true;
+    }
+    S->cv_build.notify_one();
+    if (S->builder.joinable()) S->builder.join();
     cudaSetDevice(S->device);
+    for (BuildResult& b : S->built)
+        if (b.inst) destroy_instance(b.inst.get());
     while (!S->sets.empty()) drop_set(S, S->sets.begin());
     for (auto& kv : S->free_bufs) cudaFree(kv.second);
     for (cudaEvent_t ev : S->event_pool) cudaEventDestroy(ev);

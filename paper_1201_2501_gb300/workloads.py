@@ -126,3 +126,28 @@ def exact_sparse_batch_device(n: int, k: int, seeds, device, chunk: int = 16):
         out[c0:c1] = torch.fft.ifft(X, dim=-1).to(torch.complex64)
         del X
     return out, sup, val
+
+
+def sparse_signal_device(n: int, k: int, seed: int, device, snr_db=None):
+    """One signal built on a torch device (complex64 [n]): the spectrum of ``exact_sparse`` (snr_db
+    None) or of ``general_noisy`` (heavy coefficients; complex Gaussian time noise at snr_db, drawn on
+    the device from a torch generator seeded with `seed`, so the noise differs from the numpy
+    generator's).  Returns (x, support, values)."""
+    import torch
+
+    rng = _rng(seed)
+    support = draw_support(rng, n, k)
+    mag = np.ones(k) if snr_db is None else 10.0 ** rng.uniform(0.0, 1.0, size=k)
+    values = mag * np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, size=k))
+    X = torch.zeros(n, dtype=torch.complex128, device=device)
+    X[torch.as_tensor(support, device=device)] = torch.as_tensor(values, device=device)
+    x = torch.fft.ifft(X)
+    del X
+    if snr_db is not None:
+        power = float(np.sum(np.abs(values) ** 2)) / float(n) ** 2
+        sd = float(np.sqrt(power / 10.0 ** (snr_db / 10.0) / 2.0))
+        g = torch.Generator(device=device)
+        g.manual_seed(int(seed) & ((1 << 63) - 1))
+        noise = torch.randn((n, 2), dtype=torch.float64, device=device, generator=g) * sd
+        x = x + torch.view_as_complex(noise)
+    return x.to(torch.complex64), support, values

@@ -235,6 +235,25 @@ def test_sfft_exact_fp32_matches_oracle(sf, m, k, batch):
     plan.close()
 
 
+@pytest.mark.parametrize("m,k,prec,batch", [(18, 512, 0, 3), (20, 1024, 0, 2), (16, 512, 1, 2)])
+def test_sfft_exact_large_k_matches_oracle(sf, m, k, prec, batch):
+    """B = 2048 and 4096 with zhat capacities of 2048 and 4096: the end-of-round arrays no longer fit
+    in shared memory and live in device memory; results are those of the oracle as before."""
+    n = 1 << m
+    f = exact_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f, prec), batch)
+    dt = np.complex128 if prec else np.complex64
+    sigs = [workloads.exact_sparse(n, k, workloads.seed_for(2, 300 + i), dtype=dt) for i in range(batch)]
+    seed = 77
+    got = _run_gpu(sf, plan, [s.x for s in sigs], seed, f["z_cap"])
+    for r, s in enumerate(sigs):
+        want = oracle.sfft_exact(P, s.x.astype(np.complex128), seed, r)
+        _compare(got[r], want, 1e-9 if prec else 1e-5)
+        assert np.array_equal(got[r][0], s.support)
+    plan.close()
+
+
 def test_sfft_exact_full_size_sampled(sf):
     """n = 2^22, k = 64, the benchmark's launch shape (a batch of 64 requests here), sampled requests
     checked against the oracle one by one."""

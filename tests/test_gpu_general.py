@@ -199,6 +199,27 @@ def test_sfft_general_l2l2_matches_oracle(sf, m, k, batch):
     plan.close()
 
 
+def test_sfft_general_large_k_matches_oracle(sf):
+    """k = 512 (B = 4096, zhat capacity 4096): the end-of-hashing and estimation arrays of the first
+    rounds no longer fit in shared memory and live in device memory; one request against the oracle."""
+    n, k = 1 << 18, 512
+    f = general_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f), 1)
+    s = workloads.general_noisy(n, k, workloads.seed_for(3, 60))
+    got = _run_gpu(sf, plan, [s.x], 555, f["z_cap"])[0]
+    x128 = s.x.astype(np.complex128)
+    X = np.fft.fft(x128)
+    oi, ov, of = oracle.sfft_general(P, x128, 555, 0)
+    rg, ro = _l2l2(X, got[0], got[1], k), _l2l2(X, oi, ov, k)
+    assert got[2] == 0
+    common = len(set(got[0].tolist()) & set(oi.astype(np.int64).tolist()))
+    assert common >= 0.9 * min(len(oi), len(got[0]))
+    assert abs(rg / ro - 1.0) <= 0.05, (rg, ro)
+    assert rg <= 1 + P.eps + 0.5
+    plan.close()
+
+
 def test_sfft_general_is_bit_reproducible(sf):
     n, k, batch = 1 << 16, 32, 5
     f = general_fields(n, k)
