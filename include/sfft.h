@@ -155,11 +155,17 @@ sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, u
  * sfft_execute with seed s equals a request {row r, s, r}.
  */
 typedef struct sfft_request {
-    const void* d_x;    /* device signal: n complex values of the plan's precision, 8-byte (FP32) or
-                           16-byte (FP64) aligned; caller-owned, valid until the work completes */
+    const void* d_x;    /* device signal: n complex values of the plan's precision (or `period` of them),
+                           8-byte (FP32) or 16-byte (FP64) aligned; caller-owned, valid until the work
+                           completes */
     uint64_t seed;      /* Philox key of the request's draws */
     uint32_t id;        /* request index of the Philox counter */
-    uint32_t reserved;  /* 0 */
+    uint32_t period;    /* 0: d_x holds the n samples.  Otherwise a power of two dividing n: d_x holds
+                           `period` samples and the transform is that of the periodic extension
+                           y_i = x_{i mod period}, each sample the algorithm asks for read in place
+                           (Sec. 5: with period k, Y is k-sparse on the multiples of n/k and
+                           Y_{j n/k} = (n/k) DFT_k(x)_j, so a k-point DFT comes out of the n-point
+                           sparse transform; thr should then scale with n/k) */
 } sfft_request;
 
 /*
@@ -167,7 +173,8 @@ typedef struct sfft_request {
  * device memory.  The table h_reqs (host memory) is copied into the plan before the call returns, so
  * it may be reused at once; the outputs are laid out as for sfft_execute (slot r = h_reqs[r]).
  * A plan serves one stream at a time: the table copy and the kernels go to `stream`.
- * Errors: INVALID_ARG (null pointer, batch out of range, cap == 0, a null or misaligned d_x), CUDA.
+ * Errors: INVALID_ARG (null pointer, batch out of range, cap == 0, a null or misaligned d_x, a period
+ * that is not a power of two dividing n), CUDA.
  */
 sfft_status sfft_execute_requests(sfft_plan plan, const sfft_request* h_reqs, uint32_t batch, void* stream,
                                   uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag);
@@ -215,7 +222,7 @@ typedef struct sfft_job {
     uint32_t* h_idx;      /* host output: up to cap recovered frequencies, ascending */
     double* h_val;        /* host output: their values as (re, im) doubles */
     uint32_t cap;         /* capacity of h_idx / h_val (entries) */
-    uint32_t reserved;    /* 0 */
+    uint32_t period;      /* 0, or x holds `period` samples of a periodic signal (as in sfft_request) */
 } sfft_job;
 
 typedef struct sfft_job_result {
@@ -364,6 +371,25 @@ sfft_status sfft_estimate_from_bins(sfft_plan plan, uint32_t r, uint32_t nrep, c
 sfft_status sfft_hash_to_bins_static(uint64_t n, uint32_t B, int64_t T, const float* d_taps, const double* d_wtab,
                                      const void* d_x, uint64_t sigma, uint64_t a, uint64_t b, const uint32_t* d_zidx,
                                      const double* d_zval, uint32_t nz, double* d_u, void* stream);
+
+/*
+ * Host only (no device needed): the flat-window taps g_0..g_T (g_{-t} = g_t) of bin count B, transition
+ * fraction alpha and tolerance delta at length n, as every plan builds them (Sec. 7, with this library's
+ * reading: a Gaussian of frequency std alpha / (4 B z), z = sqrt(2 ln(1/delta)), convolved with a
+ * box-car of half width (1 - alpha/2) / (2B), times n, cut at T = floor(4 B ln(1/delta) / (pi alpha))).
+ * *T receives T; h_taps (cap >= T + 1 entries) may be NULL to query T only.
+ */
+sfft_status sfft_window_taps(uint64_t n, uint32_t B, double alpha, double delta, int64_t* T, double* h_taps,
+                             uint64_t cap);
+
+/*
+ * Host only: the exact response of those taps, W(o) = (1/n) (g_0 + 2 sum_{t=1}^{T} g_t cos(2 pi o t / n)),
+ * for o = 0..len-1 (len <= n/2 + 1): the gain HashToBins applies to a coefficient at offset o from its
+ * bin centre (Lemma "hashtobins").  Plans hold it for |o| <= n/2B; callers of sfft_hash_to_bins_static
+ * pass it as d_wtab.  Computed by direct summation or, when that is costlier, as one chirp convolution
+ * of length >= len + 4T with a radix-2 FFT (absolute error of order 1e-13).
+ */
+sfft_status sfft_window_gains(uint64_t n, uint32_t B, double alpha, double delta, uint64_t len, double* h_W);
 
 /*
  * Philox4x32-10 as the device computes it (Salmon et al., SC 2011): for i < count, the four output

@@ -126,7 +126,8 @@ ExactArgs base_args(const sfft_plan_s* pl, const ExactRound& r, uint32_t t) {
 // sfft_execute_requests copies the caller's table byte for byte into the device table
 static_assert(sizeof(ReqDesc) == sizeof(sfft_request), "request table layout");
 static_assert(offsetof(ReqDesc, x) == offsetof(sfft_request, d_x) && offsetof(ReqDesc, seed) == offsetof(sfft_request, seed) &&
-                  offsetof(ReqDesc, id) == offsetof(sfft_request, id),
+                  offsetof(ReqDesc, id) == offsetof(sfft_request, id) &&
+                  offsetof(ReqDesc, period) == offsetof(sfft_request, period),
               "request table layout");
 
 sfft_status sfft::validate_params(const sfft_params* p) {
@@ -478,8 +479,11 @@ sfft_status sfft_execute_requests(sfft_plan plan, const sfft_request* h_reqs, ui
     if (!plan || !h_reqs || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
     if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
     const size_t align = plan->p.precision == SFFT_FP64 ? 16 : 8;
-    for (uint32_t r = 0; r < batch; ++r)
+    for (uint32_t r = 0; r < batch; ++r) {
         if (!h_reqs[r].d_x || ((uintptr_t)h_reqs[r].d_x % align) != 0) return SFFT_ERR_INVALID_ARG;
+        const uint32_t per = h_reqs[r].period;
+        if (per != 0 && (!is_pow2(per) || per > plan->p.n)) return SFFT_ERR_INVALID_ARG;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     // a pageable source is staged by the driver before the call returns, so h_reqs may be reused at once
     SFFT_CUDA(cudaMemcpyAsync(plan->d_reqs, h_reqs, (size_t)batch * sizeof(ReqDesc), cudaMemcpyHostToDevice, st),

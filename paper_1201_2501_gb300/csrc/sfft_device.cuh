@@ -62,15 +62,21 @@ __device__ __forceinline__ void sincospi_r(double x, double* s, double* c) { sin
 // Sample loads are cached in L2 only: the sigma-strided gather touches one 32-byte sector per sample
 // and an L1 fill would fetch the whole 128-byte line.
 // Request s of a launch: its signal row, its seed and the request index its random draws use.
+// xmask: a permuted sample index p (already reduced mod n, or a uint32 product, n | 2^32) reads
+// x[p & xmask]: n - 1, or period - 1 for a periodic extension.
 struct ReqView {
     const void* x;
     uint64_t seed;
     uint32_t id;
+    uint32_t xmask;
 };
 __device__ __forceinline__ ReqView req_view(const ReqDesc* reqs, const void* x, uint64_t row_bytes, uint64_t seed,
-                                            uint32_t s) {
-    if (reqs) return ReqView{reqs[s].x, reqs[s].seed, reqs[s].id};
-    return ReqView{static_cast<const unsigned char*>(x) + (size_t)s * row_bytes, seed, s};
+                                            uint32_t s, uint32_t nmask) {
+    if (reqs) {
+        const ReqDesc d = reqs[s];
+        return ReqView{d.x, d.seed, d.id, d.period ? d.period - 1u : nmask};
+    }
+    return ReqView{static_cast<const unsigned char*>(x) + (size_t)s * row_bytes, seed, s, nmask};
 }
 
 __device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldcg(p); }

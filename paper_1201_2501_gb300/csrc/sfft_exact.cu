@@ -196,8 +196,8 @@ __device__ int decode_bin(const DecodeCtx& d, uint32_t j, const double2* u, cons
 // The round kernel
 // ------------------------------------------------------------------------------------------------
 template <typename R>
-__device__ void gather_fold(const ExactArgs& a, const void* xrow, uint32_t s, uint32_t c, uint32_t sigma,
-                            uint32_t b, unsigned char* smem) {
+__device__ void gather_fold(const ExactArgs& a, const void* xrow, uint32_t xmask, uint32_t s, uint32_t c,
+                            uint32_t sigma, uint32_t b, unsigned char* smem) {
     using C = typename Cx<R>::T;
     C* stage = reinterpret_cast<C*>(smem);
     C* red = stage + a.stage;
@@ -216,7 +216,7 @@ __device__ void gather_fold(const ExactArgs& a, const void* xrow, uint32_t s, ui
 #pragma unroll
         for (int q = 0; q < kInFlight; ++q) {
             const uint32_t i = i0 + (uint32_t)q * kThreads;
-            if (i < cnt) v[q] = ldg_c(x + ((sigma * (uint32_t)(base + (int32_t)i)) & a.nmask));
+            if (i < cnt) v[q] = ldg_c(x + ((sigma * (uint32_t)(base + (int32_t)i)) & xmask));
         }
 #pragma unroll
         for (int q = 0; q < kInFlight; ++q) {
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_round(const ExactArgs a) 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_last;
     const uint32_t s = a.req_base + blockIdx.y, c = blockIdx.x;
-    const ReqView rq = req_view(a.reqs, a.x, a.n * sizeof(typename Cx<R>::T), a.seed, s);
+    const ReqView rq = req_view(a.reqs, a.x, a.n * sizeof(typename Cx<R>::T), a.seed, s, a.nmask);
     uint32_t sigma, b;
     if (a.bins_only) {
         sigma = a.e_sigma;
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_round(const ExactArgs a) 
     } else {
         exact_hash(rq.seed, rq.id, a.round, a.nmask, &sigma, &b);
     }
-    gather_fold<R>(a, rq.x, s, c, sigma, b, smem);
+    gather_fold<R>(a, rq.x, rq.xmask, s, c, sigma, b, smem);
     // arrival: the last CTA of request s finishes the round (nobody waits)
     __threadfence();
     __syncthreads();

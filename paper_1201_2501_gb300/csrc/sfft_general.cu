@@ -74,7 +74,7 @@ __device__ __forceinline__ HashDesc group_desc(const GenArgs& a, uint64_t seed, 
 
 // request s of a general-mode launch (signal row, seed, draw index)
 __device__ __forceinline__ ReqView gen_req(const GenArgs& a, uint32_t s) {
-    return req_view(a.reqs, a.x, a.n * sizeof(float2), a.seed, s);
+    return req_view(a.reqs, a.x, a.n * sizeof(float2), a.seed, s, a.nmask);
 }
 
 __device__ __forceinline__ uint32_t hash_index(const GenArgs& a, uint32_t g, uint32_t h) {
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) k_gen_gather(const GenArgs a) {
 #pragma unroll
                 for (int q = 0; q < 12; ++q) {
                     const uint32_t i = i0 + (uint32_t)q * kThreads;
-                    if (i < ntap) v[q] = __ldcg(x + ((h.sigma * (uint32_t)(base + (int32_t)i)) & a.nmask));
+                    if (i < ntap) v[q] = __ldcg(x + ((h.sigma * (uint32_t)(base + (int32_t)i)) & rq.xmask));
                 }
 #pragma unroll
                 for (int q = 0; q < 12; ++q) {

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <string>
 #include <thread>
@@ -53,20 +54,36 @@ void window_taps_host(uint64_t n, uint32_t B, double alpha, double delta, int64_
     }
 }
 
-// Exact response of the truncated taps, W(o) = (1/n) (g_0 + 2 sum_{t=1}^{T} g_t cos(2 pi o t / n)),
-// for o = 0..len-1 (the gain HashToBins applies to a coefficient at offset o from its bin centre).
-// Offsets are processed in blocks; within a block cos(2 pi o t / n) advances by a complex rotation
-// per step of t and is re-anchored to an exactly reduced phase every 128 steps.  Blocks run on all
-// host cores.
-void window_table_host(uint64_t n, const double* g, int64_t T, uint64_t len, double* W) {
-    const uint64_t blk = 256;
-    const uint64_t nblk = (len + blk - 1) / blk;
+// Runs f(lo, hi) over [0, count) in chunks of `grain` on all host cores.
+template <typename F>
+void parallel_for(uint64_t count, uint64_t grain, F f) {
+    const uint64_t nchunk = (count + grain - 1) / grain;
+    unsigned nth = std::thread::hardware_concurrency();
+    if (nth == 0) nth = 1;
+    if (nth > 64) nth = 64;
+    if ((uint64_t)nth > nchunk) nth = (unsigned)(nchunk ? nchunk : 1);
     std::atomic<uint64_t> next{0};
     auto work = [&]() {
-        std::vector<double> c(blk), s(blk), cr(blk), sr(blk), acc(blk);
         for (;;) {
-            const uint64_t bi = next.fetch_add(1);
-            if (bi >= nblk) break;
+            const uint64_t c = next.fetch_add(1);
+            if (c >= nchunk) break;
+            f(c * grain, std::min(count, (c + 1) * grain));
+        }
+    };
+    std::vector<std::thread> pool;
+    for (unsigned i = 1; i < nth; ++i) pool.emplace_back(work);
+    work();
+    for (auto& th : pool) th.join();
+}
+
+// W(o) for o = 0..len-1 by direct summation.  Offsets are processed in blocks; within a block
+// cos(2 pi o t / n) advances by a complex rotation per step of t and is re-anchored to an exactly
+// reduced phase every 128 steps.
+void window_table_direct(uint64_t n, const double* g, int64_t T, uint64_t len, double* W) {
+    const uint64_t blk = 256;
+    parallel_for((len + blk - 1) / blk, 1, [&](uint64_t b0, uint64_t b1) {
+        std::vector<double> c(blk), s(blk), cr(blk), sr(blk), acc(blk);
+        for (uint64_t bi = b0; bi < b1; ++bi) {
             const uint64_t o0 = bi * blk;
             const uint64_t m = std::min<uint64_t>(blk, len - o0);
             for (uint64_t q = 0; q < m; ++q) {
@@ -96,15 +113,94 @@ void window_table_host(uint64_t n, const double* g, int64_t T, uint64_t len, dou
             }
             for (uint64_t q = 0; q < m; ++q) W[o0 + q] = (g[0] + 2.0 * acc[q]) / (double)n;
         }
+    });
+}
+
+// In-place radix-2 FFT of a power-of-two length: a_j <- sum_m a_m e^{-+2 pi i j m / N} (unscaled),
+// sign - forward, + inverse.  Twiddles come from exactly reduced angles; each stage's butterflies
+// run on all host cores.
+void fft_pow2(std::vector<std::complex<double>>& a, bool inverse) {
+    const uint64_t N = a.size();
+    uint32_t logN = 0;
+    while ((uint64_t(1) << logN) < N) ++logN;
+    parallel_for(N, uint64_t(1) << 16, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t i = lo; i < hi; ++i) {
+            uint64_t r = 0;
+            for (uint32_t b = 0; b < logN; ++b) r |= ((i >> b) & 1u) << (logN - 1 - b);
+            if (r > i) std::swap(a[i], a[r]);
+        }
+    });
+    std::vector<std::complex<double>> tw(N / 2 > 0 ? N / 2 : 1);
+    const double sgn = inverse ? 1.0 : -1.0;
+    parallel_for(N / 2, uint64_t(1) << 16, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t j = lo; j < hi; ++j) {
+            const double ang = 2.0 * M_PI * (double)j / (double)N;
+            tw[j] = std::complex<double>(std::cos(ang), sgn * std::sin(ang));
+        }
+    });
+    for (uint64_t len = 2; len <= N; len <<= 1) {
+        const uint64_t half = len / 2, step = N / len;
+        parallel_for(N / 2, uint64_t(1) << 15, [&](uint64_t lo, uint64_t hi) {
+            for (uint64_t bf = lo; bf < hi; ++bf) {
+                const uint64_t grp = bf / half, j = bf - grp * half;
+                const uint64_t i0 = grp * len + j, i1 = i0 + half;
+                const std::complex<double> v = a[i1] * tw[j * step];
+                a[i1] = a[i0] - v;
+                a[i0] = a[i0] + v;
+            }
+        });
+    }
+}
+
+// W(o) for o = 0..len-1 as one chirp convolution (Bluestein): with c(m) = e^{-i pi m^2 / n},
+// e^{-2 pi i o t / n} = c(o) c(t) conj(c(o - t)), so sum_t g_|t| e^{-2 pi i o t / n} =
+// c(o) (A * H)[o + 2T] with A[t + T] = g_|t| c(t) (|t| <= T) and H[u] = conj(c(u - T)),
+// 0 <= u < len + 2T; a circular convolution of length N >= len + 4T equals the linear one there.
+// m^2 is reduced mod 2n in integers before the angle is formed.
+void window_table_chirp(uint64_t n, const double* g, int64_t T, uint64_t len, double* W) {
+    const uint64_t L = 2 * (uint64_t)T + 1, U = len + 2 * (uint64_t)T;
+    uint64_t N = 1;
+    while (N < len + 4 * (uint64_t)T) N <<= 1;
+    const uint64_t two_n = 2 * n;
+    auto chirp = [&](int64_t m) {
+        const uint64_t am = (uint64_t)(m < 0 ? -m : m);
+        const uint64_t r = (am * am) % two_n;  // |m| < 2^31 (len + 2T < n <= 2^30)
+        const double ang = M_PI * (double)r / (double)n;
+        return std::complex<double>(std::cos(ang), -std::sin(ang));
     };
-    unsigned nth = std::thread::hardware_concurrency();
-    if (nth == 0) nth = 1;
-    if (nth > 64) nth = 64;
-    if ((uint64_t)nth > nblk) nth = (unsigned)nblk;
-    std::vector<std::thread> pool;
-    for (unsigned i = 1; i < nth; ++i) pool.emplace_back(work);
-    work();
-    for (auto& th : pool) th.join();
+    std::vector<std::complex<double>> A(N), H(N);
+    parallel_for(N, uint64_t(1) << 16, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t i = lo; i < hi; ++i) {
+            const int64_t t = (int64_t)i - T;
+            A[i] = i < L ? g[t < 0 ? -t : t] * chirp(t) : std::complex<double>(0.0, 0.0);
+            H[i] = i < U ? std::conj(chirp((int64_t)i - T)) : std::complex<double>(0.0, 0.0);
+        }
+    });
+    fft_pow2(A, false);
+    fft_pow2(H, false);
+    parallel_for(N, uint64_t(1) << 16, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t i = lo; i < hi; ++i) A[i] *= H[i];
+    });
+    fft_pow2(A, true);
+    parallel_for(len, uint64_t(1) << 16, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t o = lo; o < hi; ++o)
+            W[o] = (chirp((int64_t)o) * A[o + 2 * (uint64_t)T]).real() / ((double)N * (double)n);
+    });
+}
+
+// Exact response of the truncated taps, W(o) = (1/n) (g_0 + 2 sum_{t=1}^{T} g_t cos(2 pi o t / n)),
+// for o = 0..len-1 (the gain HashToBins applies to a coefficient at offset o from its bin centre):
+// by direct summation when len T is small, else by the chirp convolution (O((len + T) log)).
+void window_table_host(uint64_t n, const double* g, int64_t T, uint64_t len, double* W) {
+    uint64_t N = 1;
+    while (N < len + 4 * (uint64_t)T) N <<= 1;
+    uint32_t logN = 0;
+    while ((uint64_t(1) << logN) < N) ++logN;
+    const double direct = (double)len * (double)T, chirp = 16.0 * (double)N * (double)logN;
+    if (direct <= chirp)
+        window_table_direct(n, g, T, len, W);
+    else
+        window_table_chirp(n, g, T, len, W);
 }
 
 void draw_exact_host(uint64_t seed, uint32_t request, uint32_t round, uint64_t n, uint64_t* sigma, uint64_t* b) {
@@ -308,5 +404,27 @@ const char* sfft_status_str(sfft_status s) {
 }
 
 const char* sfft_last_error(void) { return sfft::g_last_error.c_str(); }
+
+sfft_status sfft_window_taps(uint64_t n, uint32_t B, double alpha, double delta, int64_t* T, double* h_taps,
+                             uint64_t cap) {
+    if (!T || n < 64 || (n & (n - 1)) || B < 2 || (B & (B - 1)) || B > n / 2) return SFFT_ERR_INVALID_ARG;
+    if (!(alpha > 0 && alpha < 1) || !(delta > 0 && delta < 0.5)) return SFFT_ERR_INVALID_ARG;
+    *T = sfft::window_halfwidth(B, alpha, delta);
+    if (!h_taps) return SFFT_OK;
+    if (cap < (uint64_t)*T + 1) return SFFT_ERR_INVALID_ARG;
+    sfft::window_taps_host(n, B, alpha, delta, *T, h_taps);
+    return SFFT_OK;
+}
+
+sfft_status sfft_window_gains(uint64_t n, uint32_t B, double alpha, double delta, uint64_t len, double* h_W) {
+    int64_t T = 0;
+    const sfft_status st = sfft_window_taps(n, B, alpha, delta, &T, nullptr, 0);
+    if (st != SFFT_OK) return st;
+    if (!h_W || len == 0 || len > n / 2 + 1) return SFFT_ERR_INVALID_ARG;
+    std::vector<double> g((size_t)T + 1);
+    sfft::window_taps_host(n, B, alpha, delta, T, g.data());
+    sfft::window_table_host(n, g.data(), T, len, h_W);
+    return SFFT_OK;
+}
 
 }  // extern "C"

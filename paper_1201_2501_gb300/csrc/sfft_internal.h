@@ -21,12 +21,13 @@ constexpr size_t kFinSmemMax = 160 * 1024;  // largest on-chip finisher of the e
 // Per-request descriptor of a launch (device table, optional).  Without a table, request s of a
 // launch reads row s of the batch and draws its hashings with the launch's seed and request index s;
 // with one, request s reads x, draws with (seed, id), so its result does not depend on which slot of
-// which launch it ran in.
+// which launch it ran in.  period != 0: x holds `period` samples (a power of two dividing n) and the
+// transform is that of its periodic extension y_i = x_{i mod period} (Sec. 5), read in place.
 struct ReqDesc {
     const void* x;
     uint64_t seed;
     uint32_t id;
-    uint32_t reserved;
+    uint32_t period;
 };
 
 // One round of the exact schedule (Algorithm 1's loop t = 0..log k, with this library's readings).

@@ -544,7 +544,7 @@ void launch(sfft_server_s* S) {
                 in->h_table[r].x = j->d_stage ? j->d_stage : j->desc.x;
                 in->h_table[r].seed = j->desc.seed;
                 in->h_table[r].id = j->desc.id;
-                in->h_table[r].reserved = 0;
+                in->h_table[r].period = j->desc.period;
                 if (j->staged && e == cudaSuccess) e = cudaStreamWaitEvent(in->stream, j->staged, 0);
             }
             const uint32_t zc = ps.p.z_cap;
@@ -738,11 +738,12 @@ sfft_status sfft_submit(sfft_server S, const sfft_params* p, const sfft_job* job
     if (v != SFFT_OK) return v;
     const size_t elem = p->precision == SFFT_FP64 ? 16 : 8;
     if (job->x_on_device && ((uintptr_t)job->x % elem) != 0) return SFFT_ERR_INVALID_ARG;
+    if (job->period != 0 && ((job->period & (job->period - 1)) != 0 || job->period > p->n)) return SFFT_ERR_INVALID_ARG;
     auto* j = new (std::nothrow) Job();
     if (!j) return SFFT_ERR_OOM;
     j->key = make_key(*p, &j->p);
     j->desc = *job;
-    j->x_bytes = (size_t)p->n * elem;
+    j->x_bytes = (size_t)(job->period ? job->period : p->n) * elem;
     if (!job->x_on_device && j->x_bytes > S->cfg.mem_budget) {
         delete j;
         return SFFT_ERR_OOM;

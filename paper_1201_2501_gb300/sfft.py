@@ -66,7 +66,7 @@ class SfftRequest(ctypes.Structure):
     """Mirror of ``sfft_request``."""
 
     _fields_ = [("d_x", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("id", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("period", ctypes.c_uint32)]
 
 
 class SfftServerConfig(ctypes.Structure):
@@ -81,7 +81,7 @@ class SfftJob(ctypes.Structure):
 
     _fields_ = [("x", ctypes.c_void_p), ("x_on_device", ctypes.c_uint32), ("id", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("h_idx", ctypes.c_void_p), ("h_val", ctypes.c_void_p),
-                ("cap", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("cap", ctypes.c_uint32), ("period", ctypes.c_uint32)]
 
 
 class SfftJobResult(ctypes.Structure):
@@ -136,6 +136,8 @@ _SIGS = {
     "sfft_locate_votes": (ctypes.c_int, [_vp, _u32, _u64, _u64, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sfft_estimate_from_bins": (ctypes.c_int, [_vp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _u32, _u32, _vp, _vp, _vp,
                                                _vp]),
+    "sfft_window_taps": (ctypes.c_int, [_u64, _u32, _dbl, _dbl, _i64p, _dblp, _u64]),
+    "sfft_window_gains": (ctypes.c_int, [_u64, _u32, _dbl, _dbl, _u64, _dblp]),
     "sfft_execute_requests": (ctypes.c_int, [_vp, ctypes.POINTER(SfftRequest), _u32, _vp, _vp, _vp, _u32, _vp, _vp]),
     "sfft_server_create": (ctypes.c_int, [ctypes.POINTER(SfftServerConfig), ctypes.POINTER(_vp)]),
     "sfft_server_destroy": (ctypes.c_int, [_vp]),
@@ -288,9 +290,31 @@ def sfft_execute_host(plan: Plan, x, seed: int, cap: int, outputs=None, stream=N
     return outputs
 
 
-def sfft_execute_requests(plan: Plan, xs, seeds, ids, cap: int, outputs=None, stream=None):
-    """Run independent requests: ``xs`` a list of device tensors (n values each, anywhere in memory),
-    request r drawing with (seeds[r], ids[r]).  Outputs as for sfft_execute, slot r = request r."""
+def sfft_window_taps(n: int, B: int, alpha: float, delta: float):
+    """Host-only: the window taps g_0..g_T (numpy float64) every plan builds for (n, B, alpha, delta)."""
+    import numpy as np
+
+    T = ctypes.c_int64()
+    _check(lib().sfft_window_taps(n, B, alpha, delta, ctypes.byref(T), None, 0), "sfft_window_taps")
+    g = np.empty(T.value + 1, dtype=np.float64)
+    _check(lib().sfft_window_taps(n, B, alpha, delta, ctypes.byref(T), g.ctypes.data_as(_dblp), g.size),
+           "sfft_window_taps")
+    return g
+
+
+def sfft_window_gains(n: int, B: int, alpha: float, delta: float, length: int):
+    """Host-only: W(o), o = 0..length-1, the exact response of those taps (numpy float64)."""
+    import numpy as np
+
+    W = np.empty(length, dtype=np.float64)
+    _check(lib().sfft_window_gains(n, B, alpha, delta, length, W.ctypes.data_as(_dblp)), "sfft_window_gains")
+    return W
+
+
+def sfft_execute_requests(plan: Plan, xs, seeds, ids, cap: int, outputs=None, stream=None, periods=None):
+    """Run independent requests: ``xs`` a list of device tensors (n values each, anywhere in memory,
+    or periods[r] values of a periodic signal), request r drawing with (seeds[r], ids[r]).  Outputs as
+    for sfft_execute, slot r = request r."""
     import torch
 
     batch = len(xs)
@@ -305,7 +329,7 @@ def sfft_execute_requests(plan: Plan, xs, seeds, ids, cap: int, outputs=None, st
         table[r].d_x = _ptr(x)
         table[r].seed = int(sd)
         table[r].id = int(i)
-        table[r].reserved = 0
+        table[r].period = int(periods[r]) if periods is not None else 0
     idx, val, count, flag = outputs
     _check(lib().sfft_execute_requests(plan.handle, table, batch, _stream_ptr(stream), _ptr(idx), _ptr(val), cap,
                                        _ptr(count), _ptr(flag)), "sfft_execute_requests")
@@ -329,7 +353,7 @@ class Server:
         self._live = {}
         self._mu = threading.Lock()
 
-    def submit(self, params: SfftParams, x, seed: int, id: int = 0, cap: int = 0) -> int:
+    def submit(self, params: SfftParams, x, seed: int, id: int = 0, cap: int = 0, period: int = 0) -> int:
         import numpy as np
 
         cap = cap or params.z_cap
@@ -339,7 +363,7 @@ class Server:
         idx = np.empty(cap, dtype=np.uint32)
         val = np.empty((cap, 2), dtype=np.float64)
         job = SfftJob(_ptr(x) if hasattr(x, "data_ptr") else x.ctypes.data, 1 if on_dev else 0, id, seed,
-                      idx.ctypes.data, val.ctypes.data, cap, 0)
+                      idx.ctypes.data, val.ctypes.data, cap, period)
         t = ctypes.c_uint64()
         _check(lib().sfft_submit(self.handle, ctypes.byref(params), ctypes.byref(job), ctypes.byref(t)),
                "sfft_submit")
