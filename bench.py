@@ -618,6 +618,50 @@ def serving_measurement(sfft, args):
     }
 
 
+def precision_table(args):
+    """Error per recovered coefficient for the data-path precision (complex64 gather, fold and bin FFT
+    with FP64 decode, or FP64 throughout) and the subtraction gain (the taps' exact response W or the
+    paper's closed form Ghat'), exactly k-sparse signals with k = 64 and |X| = 1, n = 2^16..2^26.
+    Prints one JSON line per (n, variant)."""
+    import torch
+
+    from paper_1201_2501_gb300 import build, sfft, workloads
+
+    torch.cuda.set_device(0)
+    build.build()
+    k, batch = 64, args.precision_batch
+    for m in range(16, 27, 2):
+        n = 1 << m
+        seeds = [workloads.seed_for(6, 1000 * m + i) for i in range(batch)]
+        for prec in (sfft.SFFT_FP32, sfft.SFFT_FP64):
+            dt = torch.complex128 if prec == sfft.SFFT_FP64 else torch.complex64
+            x, sup, val = workloads.exact_sparse_batch_device(n, k, seeds, "cuda", dtype=dt)
+            for gain in (0, 1):
+                p = sfft.sfft_params_default(n, k, sfft.SFFT_EXACT, delta=DELTA)
+                p.precision, p.gain = prec, gain
+                plan = sfft.Plan(p, batch)
+                idx, vals, cnt, flag = (t.cpu().numpy() for t in sfft.sfft_execute(plan, x, SEED, p.z_cap))
+                plan.close()
+                ok, errs, flags = 0, [], 0
+                for r in range(batch):
+                    c = int(cnt[r])
+                    gi = idx[r, :c].view(np.uint32).astype(np.int64)
+                    gv = vals[r, :c, 0] + 1j * vals[r, :c, 1]
+                    flags += int(flag[r] != 0)
+                    if np.array_equal(gi, sup[r]):
+                        ok += 1
+                        errs.append(np.abs(gv - val[r]))
+                e = np.concatenate(errs) if errs else np.array([np.nan])
+                print(json.dumps({"table": "precision", "n": n, "k": k, "data_path": "f64" if prec else "f32",
+                                  "gain": "Ghat'" if gain else "W", "requests": batch,
+                                  "exact_support": ok, "flagged": flags, "err_median": float(np.median(e)),
+                                  "err_max": float(np.max(e)), "err_rms": float(np.sqrt(np.mean(e ** 2)))}),
+                      flush=True)
+            del x
+            torch.cuda.empty_cache()
+    return 0
+
+
 def general_measurement(sfft, stream, args):
     """The general (l2/l2) algorithm on its own workload: n = 2^22, k = 256 heavy coefficients with
     |X| log-uniform in [1, 10] plus complex Gaussian time noise at SNR 20 dB, a batch of 8."""
@@ -673,11 +717,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-general", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--precision-table", action="store_true", help="print the precision-variant table instead")
+    ap.add_argument("--precision-batch", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-serial", type=int, default=400)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.precision_table:
+        return precision_table(args)
     return run_ours(args)
 
 

@@ -79,6 +79,10 @@ typedef struct sfft_params {
     double est_gmin;       /* general: a hashing joins the median only if W(-o) >= est_gmin */
     uint32_t streams;      /* a batch is split over this many internal streams (0 -> 4) so that one
                               group's end-of-round work overlaps another group's gather */
+    uint32_t gain;         /* the window gain used to subtract recovered coefficients and to divide
+                              decoded values: 0 -> the exact response W(o) of the truncated taps
+                              (default); 1 -> the paper's closed form Ghat'(o) (Sec. 7: 1 on the pass
+                              band, 0 beyond n/2B, a difference of Gaussian cdfs in between) */
 } sfft_params;
 
 /* Fill *p with the library defaults for (n, k, mode); precision SFFT_FP32. */

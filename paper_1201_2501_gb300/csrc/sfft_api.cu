@@ -40,6 +40,7 @@ sfft_status validate(const sfft_params* p) {
     if (!(p->bins_per_k > 0) || p->B_min < 2 || !is_pow2(p->B_min)) return SFFT_ERR_INVALID_ARG;
     if (!(p->thr > 0) || !(p->tau_dec > 0 && p->tau_dec < 1) || !(p->iso_tol > 0)) return SFFT_ERR_INVALID_ARG;
     if (p->z_cap == 0 || p->z_cap > 4096) return SFFT_ERR_INVALID_ARG;
+    if (p->gain > 1) return SFFT_ERR_INVALID_ARG;
     return SFFT_OK;
 }
 

@@ -188,6 +188,24 @@ void window_table_chirp(uint64_t n, const double* g, int64_t T, uint64_t len, do
     });
 }
 
+// The paper's closed-form gain Ghat'(o) for o = 0..len-1 (Sec. 7): 1 for |o| <= (1 - alpha) n / 2B,
+// 0 for |o| >= n / 2B, and Phi((s + C) / sig_f) - Phi((s - C) / sig_f), s = o / n, in between, with
+// the window's C = (1 - alpha/2) / 2B and sig_f = alpha / (4 B z), z = sqrt(2 ln(1/delta)).
+void window_gprime_host(uint64_t n, uint32_t B, double alpha, double delta, uint64_t len, double* W) {
+    const double nn = (double)n, z = std::sqrt(2.0 * std::log(1.0 / delta));
+    const double C = (1.0 - alpha / 2.0) / (2.0 * (double)B), sf = alpha / (4.0 * (double)B * z);
+    auto cdf = [](double v) { return 0.5 * std::erfc(-v / std::sqrt(2.0)); };
+    for (uint64_t o = 0; o < len; ++o) {
+        const double ao = (double)o;
+        if (ao <= (1.0 - alpha) * nn / (2.0 * (double)B))
+            W[o] = 1.0;
+        else if (ao >= nn / (2.0 * (double)B))
+            W[o] = 0.0;
+        else
+            W[o] = cdf((ao / nn + C) / sf) - cdf((ao / nn - C) / sf);
+    }
+}
+
 // Exact response of the truncated taps, W(o) = (1/n) (g_0 + 2 sum_{t=1}^{T} g_t cos(2 pi o t / n)),
 // for o = 0..len-1 (the gain HashToBins applies to a coefficient at offset o from its bin centre):
 // by direct summation when len T is small, else by the chirp convolution (O((len + T) log)).
@@ -267,7 +285,10 @@ sfft_status build_exact_schedule(sfft_plan_s* pl) {
         pl->taps_host.resize(taps_off + (size_t)r.T + 1);
         window_taps_host(p.n, r.B, r.alpha, p.delta, r.T, pl->taps_host.data() + taps_off);
         pl->wtab_host.resize(wtab_off + Np / 2 + 1);
-        window_table_host(p.n, pl->taps_host.data() + taps_off, r.T, Np / 2 + 1, pl->wtab_host.data() + wtab_off);
+        if (p.gain == 1)
+            window_gprime_host(p.n, r.B, r.alpha, p.delta, Np / 2 + 1, pl->wtab_host.data() + wtab_off);
+        else
+            window_table_host(p.n, pl->taps_host.data() + taps_off, r.T, Np / 2 + 1, pl->wtab_host.data() + wtab_off);
         taps_off += (size_t)r.T + 1;
         wtab_off += Np / 2 + 1;
         pl->rounds.push_back(r);
@@ -343,7 +364,10 @@ sfft_status build_general_schedule(sfft_plan_s* pl) {
         pl->taps_host.resize(taps_off + (size_t)r.T + 1);
         window_taps_host(p.n, r.B, p.alpha0, p.delta, r.T, pl->taps_host.data() + taps_off);
         pl->wtab_host.resize(wtab_off + Np / 2 + 1);
-        window_table_host(p.n, pl->taps_host.data() + taps_off, r.T, Np / 2 + 1, pl->wtab_host.data() + wtab_off);
+        if (p.gain == 1)
+            window_gprime_host(p.n, r.B, p.alpha0, p.delta, Np / 2 + 1, pl->wtab_host.data() + wtab_off);
+        else
+            window_table_host(p.n, pl->taps_host.data() + taps_off, r.T, Np / 2 + 1, pl->wtab_host.data() + wtab_off);
         taps_off += (size_t)r.T + 1;
         wtab_off += Np / 2 + 1;
         pl->grounds.push_back(r);
@@ -375,7 +399,7 @@ void sfft_params_default(sfft_params* p, uint64_t n, uint32_t k, uint32_t mode) 
     p->gmin = 0.1;
     p->prune = 0.5;
     p->ref_lo = 1e-5;
-    p->ref_hi = 2e-3;
+    p->ref_hi = 2e-2;
     p->ref_tol = 0.1;
     p->z_cap = mode == SFFT_GENERAL ? (k * 8 > 64 ? k * 8 : 64) : (k * 4 > 64 ? k * 4 : 64);
     p->eps = 1.0;

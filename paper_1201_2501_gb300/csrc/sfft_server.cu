@@ -68,6 +68,7 @@ ParamKey make_key(const sfft_params& p, sfft_params* canon) {
     q.s = p.s;
     q.est_gmin = p.est_gmin;
     q.streams = p.streams;
+    q.gain = p.gain;
     ParamKey k;
     std::memcpy(k.bytes, &q, sizeof q);
     if (canon) *canon = q;

@@ -59,6 +59,7 @@ class SfftParams(ctypes.Structure):
         ("s", ctypes.c_double),
         ("est_gmin", ctypes.c_double),
         ("streams", ctypes.c_uint32),
+        ("gain", ctypes.c_uint32),
     ]
 
 

@@ -107,23 +107,25 @@ def exact_sparse_batch_spectra(n: int, k: int, seeds) -> tuple[np.ndarray, np.nd
     return sup, val
 
 
-def exact_sparse_batch_device(n: int, k: int, seeds, device, chunk: int = 16):
-    """A batch of exactly k-sparse signals built on a torch device (complex64, shape [N, n]).
+def exact_sparse_batch_device(n: int, k: int, seeds, device, chunk: int = 16, dtype=None):
+    """A batch of exactly k-sparse signals built on a torch device (shape [N, n], complex64 unless
+    `dtype` says otherwise).
 
     The spectra are those of ``exact_sparse_batch_spectra``; the inverse DFT runs in complex128 on
-    the device (input synthesis only) and is rounded once to complex64.  Returns (x, supports, values).
+    the device (input synthesis only) and is rounded once to the output type.  Returns (x, supports,
+    values).
     """
     import torch
 
     sup, val = exact_sparse_batch_spectra(n, k, seeds)
     N = len(seeds)
-    out = torch.empty((N, n), dtype=torch.complex64, device=device)
+    out = torch.empty((N, n), dtype=dtype or torch.complex64, device=device)
     for c0 in range(0, N, chunk):
         c1 = min(N, c0 + chunk)
         X = torch.zeros((c1 - c0, n), dtype=torch.complex128, device=device)
         rows = torch.arange(c1 - c0, device=device).unsqueeze(1).expand(-1, k)
         X[rows, torch.as_tensor(sup[c0:c1], device=device)] = torch.as_tensor(val[c0:c1], device=device)
-        out[c0:c1] = torch.fft.ifft(X, dim=-1).to(torch.complex64)
+        out[c0:c1] = torch.fft.ifft(X, dim=-1).to(out.dtype)
         del X
     return out, sup, val
 

@@ -13,7 +13,7 @@ FIELDS_DEFAULT = dict(
     gmin=0.1,
     prune=0.5,
     ref_lo=1e-5,
-    ref_hi=2e-3,
+    ref_hi=2e-2,
     ref_tol=0.1,
     eps=1.0,
     t_regions=0,

@@ -85,11 +85,15 @@ def test_schedule_window_and_draws_match_oracle(sf, n, k, delta, prec):
 
 
 # ------------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("n,k,prec,nz", [(1 << 14, 8, 1, 0), (1 << 14, 8, 1, 5), (1 << 18, 64, 0, 0),
-                                         (1 << 18, 64, 0, 40), (1 << 22, 64, 0, 20)])
-def test_hash_to_bins_matches_oracle(sf, n, k, prec, nz):
+@pytest.mark.parametrize("n,k,prec,nz,gain", [(1 << 14, 8, 1, 0, 0), (1 << 14, 8, 1, 5, 0), (1 << 18, 64, 0, 0, 0),
+                                              (1 << 18, 64, 0, 40, 0), (1 << 22, 64, 0, 20, 0), (1 << 14, 8, 1, 40, 1),
+                                              (1 << 18, 64, 0, 40, 1)])
+def test_hash_to_bins_matches_oracle(sf, n, k, prec, nz, gain):
+    """gain 0 subtracts with the taps' exact response W, gain 1 with the paper's closed form Ghat'."""
     f = exact_fields(n, k, delta=1e-8 if prec else 1e-6)
-    plan = sf.Plan(gpu_params(sf, f, prec), 1)
+    p = gpu_params(sf, f, prec)
+    p.gain = gain
+    plan = sf.Plan(p, 1)
     sig = workloads.exact_sparse(n, k, 777 + n % 97, dtype=np.complex128 if prec else np.complex64)
     x_dev = torch.as_tensor(sig.x).cuda()
     x128 = sig.x.astype(np.complex128)
@@ -107,7 +111,7 @@ def test_hash_to_bins_matches_oracle(sf, n, k, prec, nz):
             got = u_dev.cpu().numpy()
             got = got[:, 0] + 1j * got[:, 1]
             want = oracle.hash_to_bins(x128, sigma, a, b, info["B"], info["alpha"], f["delta"],
-                                       None if zi is None else zi.astype(np.uint64), zv)
+                                       None if zi is None else zi.astype(np.uint64), zv, use_gprime=bool(gain))
             scale = max(1.0, np.max(np.abs(want)))
             tol = 1e-9 if prec else 2e-5
             assert np.max(np.abs(got - want)) <= tol * scale
