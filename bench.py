@@ -312,8 +312,16 @@ def run_ours(args):
             torch.empty((batch,), dtype=torch.int32, device="cuda"),
             torch.empty((batch,), dtype=torch.int32, device="cuda"))
 
-    def step():
-        sfft.sfft_execute(plan, x, SEED, cap, outs, stream)
+    if args.path == "persistent":
+        bplan = sfft.BatchPlan([plan], batch)
+        prepared = bplan.prepare([0] * batch, [x[r] for r in range(batch)], [SEED] * batch, list(range(batch)))
+
+        def step():
+            bplan.execute_prepared(prepared, cap, outs, stream)
+    else:
+
+        def step():
+            sfft.sfft_execute(plan, x, SEED, cap, outs, stream)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -389,13 +397,16 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "n": n, "k": k, "batch_per_gpu": batch, "rounds": plan.rounds,
                        "precision": "complex64 gather/fold/bin FFT, FP64 subtraction and decode",
                        "l2": "inputs (8 GiB per GPU) exceed L2; no flush", "parallelism": f"replicas x{world}",
-                       "support_exact_fraction": exact / batch},
+                       "support_exact_fraction": exact / batch,
+                       "path": "one persistent launch per step (device queue of request-round-chunk items)"
+                               if args.path == "persistent" else "one kernel per round and stream group"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": profiled_traffic() if batch == 256 else None,
                          "kernel": "k_exact_round (all rounds of a step)",
                          "bytes_per_transform": bytes_tr, "samples_per_transform": samples_tr,
                          "peak_kind": peak_kind},
-            "e2e": e2e, "clocks": clk.summary(), "gpu_launches": plan.rounds * launch_groups(batch, params.streams) * args.steps,
+            "e2e": e2e, "clocks": clk.summary(), "gpu_launches": (args.steps if args.path == "persistent"
+                                                             else plan.rounds * launch_groups(batch, params.streams) * args.steps),
             "cpu_baseline": cpu,
         }
         line.update(extra)
@@ -717,6 +728,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-general", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--path", default="rounds", choices=["rounds", "persistent"],
+                    help="per-round launches (one kernel per round and stream group) or one persistent launch")
     ap.add_argument("--precision-table", action="store_true", help="print the precision-variant table instead")
     ap.add_argument("--precision-batch", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=2000)

@@ -184,6 +184,35 @@ sfft_status sfft_execute_requests(sfft_plan plan, const sfft_request* h_reqs, ui
                                   uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag);
 
 /* ---------------------------------------------------------------------------------------------- */
+/* Mixed batches in one persistent launch                                                          */
+/* ---------------------------------------------------------------------------------------------- */
+/*
+ * A batch plan groups exact-mode plans of any (n, k) (one precision) so that a batch mixing them runs
+ * as ONE persistent launch: CTAs take (request, round, chunk) items from a device queue, and the CTA
+ * that finishes a request's round (Algorithm 1's loop) queues that request's next round at once, so
+ * rounds of different requests overlap with no launch boundary between them.  Results are those of
+ * sfft_execute_requests on each request's own plan, bit for bit.  The batch plan owns a workspace for
+ * max_requests requests; the plans must outlive it.
+ * Errors: INVALID_ARG (null, nplans == 0, a general-mode plan, mixed precisions), OOM, CUDA.
+ */
+typedef struct sfft_batch_plan_s* sfft_batch_plan;
+sfft_status sfft_batch_plan_create(const sfft_plan* plans, uint32_t nplans, uint32_t max_requests,
+                                   sfft_batch_plan* out);
+sfft_status sfft_batch_plan_destroy(sfft_batch_plan bp);
+
+/*
+ * Run nreq (<= max_requests) requests: request r uses plans[h_plan_of[r]] and h_reqs[r] (signal, seed,
+ * id, period).  Outputs as for sfft_execute (slot r, capacity cap).  The host tables are staged in
+ * page-locked memory owned by the batch plan (two buffers, so consecutive calls on one stream do not
+ * wait for each other).  A request whose queue item was not published within about a second (a
+ * malfunction, never expected) ends with d_flag = SFFT_ERR_TIMEOUT.
+ * Errors: INVALID_ARG (null, nreq out of range, a plan index or request that is out of range), CUDA.
+ */
+sfft_status sfft_batch_execute(sfft_batch_plan bp, const uint32_t* h_plan_of, const sfft_request* h_reqs,
+                               uint32_t nreq, void* stream, uint32_t* d_idx, double* d_val, uint32_t cap,
+                               uint32_t* d_count, int32_t* d_flag);
+
+/* ---------------------------------------------------------------------------------------------- */
 /* Serving: continuous batching of independent transforms                                         */
 /* ---------------------------------------------------------------------------------------------- */
 /*

@@ -674,3 +674,259 @@ sfft_status sfft_estimate_from_bins(sfft_plan plan, uint32_t r, uint32_t nrep, c
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Batch plans: mixed exact-mode requests in one persistent launch
+// ------------------------------------------------------------------------------------------------
+struct sfft_batch_plan_s {
+    std::vector<sfft_plan> plans;
+    std::vector<uint32_t> rd0, rounds, chunks0, items_of;  // per plan: first descriptor, rounds,
+                                                          // round-0 chunks, items of a request
+    bool fp64 = false;
+    uint32_t max_req = 0;
+    size_t max_items = 0;         // items of the largest batch the workspace holds
+    ExactArgs* d_rdesc = nullptr;
+    unsigned char* d_ctl = nullptr;  // [reqs | rd0 | rounds | head, tail, error | flags] of one call
+    unsigned long long* d_items = nullptr;
+    unsigned char* d_part = nullptr;
+    size_t part_stride = 0;
+    uint32_t* d_counter = nullptr;
+    uint32_t* d_zidx = nullptr;
+    double2* d_zval = nullptr;
+    size_t z_stride = 0;
+    uint32_t* d_zcount = nullptr;
+    int32_t* d_zflag = nullptr;
+    unsigned char* d_fin = nullptr;
+    size_t fin_stride = 0;
+    size_t smem = 0;
+    int ctas = 0;
+    size_t ctl_bytes = 0;
+    unsigned char* h_stage[2] = {nullptr, nullptr};  // page-locked copies of the control block + items
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int cur = 0;
+};
+
+namespace {
+
+struct CtlLayout {
+    size_t reqs, rd0, rounds, ctr, flags, items, total;
+};
+CtlLayout ctl_layout(uint32_t nreq, size_t items0) {
+    CtlLayout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = (off + 15) & ~size_t(15);
+        off = o + bytes;
+        return o;
+    };
+    L.reqs = take((size_t)nreq * sizeof(ReqDesc));
+    L.rd0 = take((size_t)nreq * 4);
+    L.rounds = take((size_t)nreq * 4);
+    L.ctr = take(16);
+    L.flags = take((size_t)nreq * 4);
+    L.items = take(items0 * 8);
+    L.total = off;
+    return L;
+}
+
+void free_batch_plan(sfft_batch_plan_s* bp) {
+    if (!bp) return;
+    cudaFree(bp->d_rdesc);
+    cudaFree(bp->d_ctl);
+    cudaFree(bp->d_items);
+    cudaFree(bp->d_part);
+    cudaFree(bp->d_counter);
+    cudaFree(bp->d_zidx);
+    cudaFree(bp->d_zval);
+    cudaFree(bp->d_zcount);
+    cudaFree(bp->d_zflag);
+    cudaFree(bp->d_fin);
+    for (int i = 0; i < 2; ++i) {
+        cudaFreeHost(bp->h_stage[i]);
+        if (bp->ev[i]) cudaEventDestroy(bp->ev[i]);
+    }
+    delete bp;
+}
+
+}  // namespace
+
+extern "C" {
+
+sfft_status sfft_batch_plan_create(const sfft_plan* plans, uint32_t nplans, uint32_t max_requests,
+                                   sfft_batch_plan* out) {
+    if (!out) return SFFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!plans || nplans == 0 || max_requests == 0 || max_requests > (1u << 24)) return SFFT_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < nplans; ++i) {
+        if (!plans[i] || plans[i]->p.mode != SFFT_EXACT) return SFFT_ERR_INVALID_ARG;
+        if (plans[i]->p.precision != plans[0]->p.precision) return SFFT_ERR_INVALID_ARG;
+        if (plans[i]->rounds.size() > 255) return SFFT_ERR_INVALID_ARG;
+    }
+    auto* bp = new (std::nothrow) sfft_batch_plan_s();
+    if (!bp) return SFFT_ERR_OOM;
+    bp->plans.assign(plans, plans + nplans);
+    bp->fp64 = plans[0]->p.precision == SFFT_FP64;
+    bp->max_req = max_requests;
+    const size_t csize = bp->fp64 ? 16 : 8;
+    std::vector<ExactArgs> rdesc;
+    uint32_t max_items_req = 0, max_chunks0 = 0;
+    for (sfft_plan pl : bp->plans) {
+        bp->rd0.push_back((uint32_t)rdesc.size());
+        const uint32_t R = (uint32_t)pl->rounds.size();
+        bp->rounds.push_back(R);
+        uint32_t items = 0;
+        for (uint32_t t = 0; t < R; ++t) {
+            const ExactRound& r = pl->rounds[t];
+            if (r.chunks > 0xFFFFu) {
+                free_batch_plan(bp);
+                return SFFT_ERR_K_RANGE;
+            }
+            ExactArgs a = base_args(pl, r, t);
+            a.first_round = t == 0;
+            a.last_round = t + 1 == R;
+            rdesc.push_back(a);
+            items += r.chunks;
+            bp->smem = std::max(bp->smem, r.smem);
+            if (r.fin_global) bp->fin_stride = std::max(bp->fin_stride, (r.fin_bytes + 255) & ~size_t(255));
+        }
+        bp->chunks0.push_back(pl->rounds[0].chunks);
+        bp->items_of.push_back(items);
+        max_items_req = std::max(max_items_req, items);
+        max_chunks0 = std::max(max_chunks0, pl->rounds[0].chunks);
+        bp->part_stride = std::max(bp->part_stride, ((pl->part_stride * csize) + 255) & ~size_t(255));
+        bp->z_stride = std::max(bp->z_stride, (size_t)pl->p.z_cap);
+    }
+    bp->max_items = (size_t)max_items_req * max_requests;
+    if (bp->max_items >= (size_t)1 << 32) {
+        free_batch_plan(bp);
+        return SFFT_ERR_INVALID_ARG;
+    }
+    bp->ctl_bytes = ctl_layout(max_requests, (size_t)max_chunks0 * max_requests).total;
+    bool ok = cudaMalloc((void**)&bp->d_rdesc, rdesc.size() * sizeof(ExactArgs)) == cudaSuccess &&
+              cudaMalloc((void**)&bp->d_ctl, bp->ctl_bytes) == cudaSuccess &&
+              cudaMalloc((void**)&bp->d_items, bp->max_items * 8) == cudaSuccess &&
+              cudaMalloc((void**)&bp->d_part, bp->part_stride * max_requests) == cudaSuccess &&
+              cudaMalloc((void**)&bp->d_counter, (size_t)max_requests * 4) == cudaSuccess &&
+              cudaMalloc((void**)&bp->d_zidx, bp->z_stride * max_requests * 4) == cudaSuccess &&
+              cudaMalloc((void**)&bp->d_zval, bp->z_stride * max_requests * 16) == cudaSuccess &&
+              cudaMalloc((void**)&bp->d_zcount, (size_t)max_requests * 4) == cudaSuccess &&
+              cudaMalloc((void**)&bp->d_zflag, (size_t)max_requests * 4) == cudaSuccess &&
+              (bp->fin_stride == 0 || cudaMalloc((void**)&bp->d_fin, bp->fin_stride * max_requests) == cudaSuccess) &&
+              cudaMallocHost((void**)&bp->h_stage[0], bp->ctl_bytes) == cudaSuccess &&
+              cudaMallocHost((void**)&bp->h_stage[1], bp->ctl_bytes) == cudaSuccess &&
+              cudaEventCreateWithFlags(&bp->ev[0], cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&bp->ev[1], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        set_last_error(std::string("batch plan: ") + cudaGetErrorString(cudaGetLastError()));
+        free_batch_plan(bp);
+        return SFFT_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpy(bp->d_rdesc, rdesc.data(), rdesc.size() * sizeof(ExactArgs), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(bp->d_counter, 0, (size_t)max_requests * 4);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("batch plan: ") + cudaGetErrorString(e));
+        free_batch_plan(bp);
+        return SFFT_ERR_CUDA;
+    }
+    bp->ctas = exact_persistent_ctas(bp->smem, bp->fp64);
+    if (bp->ctas <= 0) {
+        set_last_error("batch plan: no CTA of the persistent kernel fits on the device");
+        free_batch_plan(bp);
+        return SFFT_ERR_K_RANGE;
+    }
+    *out = bp;
+    return SFFT_OK;
+}
+
+sfft_status sfft_batch_plan_destroy(sfft_batch_plan bp) {
+    if (!bp) return SFFT_OK;
+    cudaDeviceSynchronize();
+    free_batch_plan(bp);
+    return SFFT_OK;
+}
+
+sfft_status sfft_batch_execute(sfft_batch_plan bp, const uint32_t* h_plan_of, const sfft_request* h_reqs,
+                               uint32_t nreq, void* stream, uint32_t* d_idx, double* d_val, uint32_t cap,
+                               uint32_t* d_count, int32_t* d_flag) {
+    if (!bp || !h_plan_of || !h_reqs || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
+    if (nreq == 0 || nreq > bp->max_req) return SFFT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t align = bp->fp64 ? 16 : 8;
+    size_t items0 = 0, total = 0;
+    for (uint32_t r = 0; r < nreq; ++r) {
+        const uint32_t p = h_plan_of[r];
+        if (p >= bp->plans.size() || !h_reqs[r].d_x || ((uintptr_t)h_reqs[r].d_x % align) != 0)
+            return SFFT_ERR_INVALID_ARG;
+        const uint32_t per = h_reqs[r].period;
+        if (per != 0 && (!is_pow2(per) || per > bp->plans[p]->p.n)) return SFFT_ERR_INVALID_ARG;
+        items0 += bp->chunks0[p];
+        total += bp->items_of[p];
+    }
+    // stage the control block in this call's page-locked buffer (its previous copy has completed)
+    const int cur = bp->cur;
+    bp->cur ^= 1;
+    SFFT_CUDA(cudaEventSynchronize(bp->ev[cur]), "staging buffer");
+    unsigned char* h = bp->h_stage[cur];
+    const CtlLayout L = ctl_layout(nreq, items0);
+    ReqDesc* reqs = reinterpret_cast<ReqDesc*>(h + L.reqs);
+    uint32_t* rd0 = reinterpret_cast<uint32_t*>(h + L.rd0);
+    uint32_t* rounds = reinterpret_cast<uint32_t*>(h + L.rounds);
+    uint32_t* ctr = reinterpret_cast<uint32_t*>(h + L.ctr);
+    int32_t* flags = reinterpret_cast<int32_t*>(h + L.flags);
+    unsigned long long* items = reinterpret_cast<unsigned long long*>(h + L.items);
+    size_t q = 0;
+    for (uint32_t r = 0; r < nreq; ++r) {
+        const uint32_t p = h_plan_of[r];
+        std::memcpy(&reqs[r], &h_reqs[r], sizeof(ReqDesc));
+        rd0[r] = bp->rd0[p];
+        rounds[r] = bp->rounds[p];
+        flags[r] = SFFT_ERR_TIMEOUT;  // overwritten by the request's last round
+        for (uint32_t c = 0; c < bp->chunks0[p]; ++c)
+            items[q++] = (1ull << 63) | ((unsigned long long)r << 24) | c;
+    }
+    ctr[0] = 0;                 // head
+    ctr[1] = (uint32_t)items0;  // tail
+    ctr[2] = 0;                 // error
+    ctr[3] = 0;
+    unsigned char* d = bp->d_ctl;
+    SFFT_CUDA(cudaMemcpyAsync(d, h, L.items, cudaMemcpyHostToDevice, st), "copy control block");
+    SFFT_CUDA(cudaMemcpyAsync(bp->d_items, h + L.items, items0 * 8, cudaMemcpyHostToDevice, st), "copy items");
+    SFFT_CUDA(cudaEventRecord(bp->ev[cur], st), "staging event");
+    if (total > items0)
+        SFFT_CUDA(cudaMemsetAsync(bp->d_items + items0, 0, (total - items0) * 8, st), "clear items");
+    SFFT_CUDA(cudaMemcpyAsync(d_flag, d + L.flags, (size_t)nreq * 4, cudaMemcpyDeviceToDevice, st), "flags");
+    SFFT_CUDA(cudaMemsetAsync(d_count, 0, (size_t)nreq * 4, st), "counts");
+    SFFT_CUDA(cudaMemsetAsync(bp->d_zcount, 0, (size_t)nreq * 4, st), "clear zhat");
+    SFFT_CUDA(cudaMemsetAsync(bp->d_zflag, 0, (size_t)nreq * 4, st), "clear flags");
+    PersistArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.rdesc = bp->d_rdesc;
+    a.reqs = reinterpret_cast<const ReqDesc*>(d + L.reqs);
+    a.req_rd0 = reinterpret_cast<const uint32_t*>(d + L.rd0);
+    a.req_rounds = reinterpret_cast<const uint32_t*>(d + L.rounds);
+    a.items = bp->d_items;
+    a.head = reinterpret_cast<uint32_t*>(d + L.ctr);
+    a.tail = a.head + 1;
+    a.error = reinterpret_cast<int32_t*>(a.head + 2);
+    a.total = (uint32_t)total;
+    a.part = bp->d_part;
+    a.part_stride = bp->part_stride;
+    a.counter = bp->d_counter;
+    a.zidx = bp->d_zidx;
+    a.zval = bp->d_zval;
+    a.z_stride = bp->z_stride;
+    a.zcount = bp->d_zcount;
+    a.zflag = bp->d_zflag;
+    a.fin = bp->d_fin;
+    a.fin_stride = bp->fin_stride;
+    a.out_idx = d_idx;
+    a.out_val = reinterpret_cast<double2*>(d_val);
+    a.out_cap = cap;
+    a.out_count = d_count;
+    a.out_flag = d_flag;
+    const uint32_t ctas = (uint32_t)std::min<size_t>((size_t)bp->ctas, total);
+    SFFT_CUDA(launch_exact_persistent(a, ctas, bp->smem, st, bp->fp64), "persistent launch");
+    return SFFT_OK;
+}
+
+}  // extern "C"

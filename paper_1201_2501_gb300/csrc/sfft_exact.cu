@@ -210,7 +210,10 @@ __device__ void gather_fold(const ExactArgs& a, const void* xrow, uint32_t xmask
     const int32_t base = (int32_t)(t_lo - (int64_t)a.a_base - (int64_t)a.maxshift);  // sample held by stage[0]
     const uint32_t cnt = ntap + a.maxshift;
     // step 1a: gather the sigma-strided samples x_{sigma s}, s in [base, base + cnt) (12 loads in flight)
-    constexpr int kInFlight = 12;
+#ifndef SFFT_GATHER_IN_FLIGHT
+#define SFFT_GATHER_IN_FLIGHT 12
+#endif
+    constexpr int kInFlight = SFFT_GATHER_IN_FLIGHT;
     for (uint32_t i0 = tid; i0 < cnt; i0 += kThreads * kInFlight) {
         C v[kInFlight];
 #pragma unroll
@@ -450,8 +453,12 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     }
 }
 
+#ifndef SFFT_ROUND_MIN_BLOCKS
+#define SFFT_ROUND_MIN_BLOCKS 2  // resident CTAs per SM the register budget is sized for
+#endif
+
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 4) k_exact_round(const ExactArgs a) {
+__global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_round(const ExactArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_last;
     const uint32_t s = a.req_base + blockIdx.y, c = blockIdx.x;
@@ -473,6 +480,138 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_round(const ExactArgs a) 
     __threadfence();
     finish_round<R>(a, s, sigma, b, a.fin_scratch ? a.fin_scratch + (size_t)s * a.fin_stride : smem);
     if (threadIdx.x == 0) a.counter[s] = 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Persistent path: one launch, a device queue of (request, round, chunk) items
+// ------------------------------------------------------------------------------------------------
+constexpr unsigned long long kItemValid = 1ull << 63;
+constexpr uint32_t kSpinLimit = 1u << 23;  // x ~128 ns: a wait gives up after about a second
+
+__device__ __forceinline__ unsigned long long pack_item(uint32_t r, uint32_t t, uint32_t c) {
+    return kItemValid | ((unsigned long long)r << 24) | ((unsigned long long)t << 16) | c;
+}
+__device__ __forceinline__ unsigned long long load_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void store_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+#ifndef SFFT_PERSIST_MIN_BLOCKS
+#define SFFT_PERSIST_MIN_BLOCKS 2  // resident CTAs per SM the register budget is sized for
+#endif
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads, SFFT_PERSIST_MIN_BLOCKS) k_exact_persistent(const PersistArgs pa) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) ExactArgs sa;
+    __shared__ unsigned long long s_item;
+    __shared__ uint32_t s_last;
+    const uint32_t tid = threadIdx.x;
+    for (;;) {
+        // take the next item and wait (bounded) until it is published
+        if (tid == 0) {
+            const uint32_t slot = atomicAdd(pa.head, 1u);
+            unsigned long long it = 0;
+            if (slot < pa.total) {
+                for (uint32_t spin = 0;; ++spin) {
+                    it = load_acquire(pa.items + slot);
+                    if (it & kItemValid) break;
+                    if (spin >= kSpinLimit) {
+                        atomicExch(pa.error, 1);
+                        it = 0;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
+            s_item = it;
+        }
+        __syncthreads();
+        const unsigned long long it = s_item;
+        if (!it) return;
+        const uint32_t r = (uint32_t)((it >> 24) & 0xFFFFFFFFull), t = (uint32_t)((it >> 16) & 0xFFu),
+                       c = (uint32_t)(it & 0xFFFFu);
+        // the (plan, round) argument block, then the request's own workspace as slot 0
+        {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(pa.rdesc + pa.req_rd0[r] + t);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
+            for (uint32_t w = tid; w < sizeof(ExactArgs) / 4; w += kThreads) dst[w] = src[w];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            sa.reqs = pa.reqs + r;
+            sa.req_base = 0;
+            sa.part = pa.part + (size_t)r * pa.part_stride;
+            sa.part_stride = 0;
+            sa.counter = pa.counter + r;
+            sa.zidx = pa.zidx + (size_t)r * pa.z_stride;
+            sa.zval = pa.zval + (size_t)r * pa.z_stride;
+            sa.zcount = pa.zcount + r;
+            sa.zflag = pa.zflag + r;
+            sa.fin_scratch = sa.fin_scratch ? pa.fin + (size_t)r * pa.fin_stride : nullptr;
+            sa.fin_stride = 0;
+            sa.out_idx = pa.out_idx + (size_t)r * pa.out_cap;
+            sa.out_val = pa.out_val + (size_t)r * pa.out_cap;
+            sa.out_cap = pa.out_cap;
+            sa.out_count = pa.out_count + r;
+            sa.out_flag = pa.out_flag + r;
+        }
+        __syncthreads();
+        const ExactArgs& a = sa;
+        const ReqView rq = req_view(a.reqs, nullptr, 0, 0, 0, a.nmask);
+        uint32_t sigma, b;
+        exact_hash(rq.seed, rq.id, a.round, a.nmask, &sigma, &b);
+        gather_fold<R>(a, rq.x, rq.xmask, 0, c, sigma, b, smem);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_last = (atomicAdd(a.counter, 1u) == a.chunks - 1) ? 1u : 0u;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            finish_round<R>(a, 0, sigma, b, a.fin_scratch ? a.fin_scratch : smem);
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                *a.counter = 0;
+                if (t + 1 < pa.req_rounds[r]) {  // publish the request's next round
+                    const uint32_t nch = pa.rdesc[pa.req_rd0[r] + t + 1].chunks;
+                    const uint32_t base = atomicAdd(pa.tail, nch);
+                    for (uint32_t q = 0; q < nch; ++q) store_release(pa.items + base + q, pack_item(r, t + 1, q));
+                }
+            }
+        }
+        __syncthreads();  // sa and the shared arrays are rewritten by the next item
+    }
+}
+
+int exact_persistent_ctas(size_t smem, bool fp64) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e;
+    if (fp64) {
+        e = cudaFuncSetAttribute(k_exact_persistent<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_exact_persistent<double>, kThreads, smem);
+    } else {
+        e = cudaFuncSetAttribute(k_exact_persistent<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_exact_persistent<float>, kThreads, smem);
+    }
+    if (e != cudaSuccess) return 0;
+    return sms * per;
+}
+
+cudaError_t launch_exact_persistent(const PersistArgs& a, uint32_t ctas, size_t smem, cudaStream_t st, bool fp64) {
+    if (fp64)
+        k_exact_persistent<double><<<ctas, kThreads, smem, st>>>(a);
+    else
+        k_exact_persistent<float><<<ctas, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -92,6 +92,38 @@ struct ExactArgs {
     double2* ubins;
 };
 
+// The persistent exact path: requests of different plans (n, k, schedule) in one launch, their
+// rounds driven by a device work queue.  Item = (request, round, chunk); the CTA that finishes a
+// request's round publishes the chunks of its next round.  rdesc holds one argument block per
+// (plan, round) with the plan's tables; the per-request fields are pointed at the request's own
+// workspace (as slot 0) by the kernel.
+struct PersistArgs {
+    const ExactArgs* rdesc;         // [sum of the plans' rounds]
+    const ReqDesc* reqs;            // [nreq]
+    const uint32_t* req_rd0;        // [nreq] index in rdesc of the request's round 0
+    const uint32_t* req_rounds;     // [nreq]
+    unsigned long long* items;      // [total] (bit 63: published)
+    uint32_t* head;                 // items taken
+    uint32_t* tail;                 // items reserved
+    uint32_t total;
+    unsigned char* part;            // [nreq][part_stride] bytes
+    size_t part_stride;
+    uint32_t* counter;              // [nreq] (zero between rounds)
+    uint32_t* zidx;                 // [nreq][z_stride]
+    double2* zval;
+    size_t z_stride;
+    uint32_t* zcount;               // [nreq]
+    int32_t* zflag;                 // [nreq]
+    unsigned char* fin;             // [nreq][fin_stride] bytes (rounds with fin_global)
+    size_t fin_stride;
+    uint32_t* out_idx;              // [nreq][out_cap]
+    double2* out_val;
+    uint32_t out_cap;
+    uint32_t* out_count;            // [nreq]
+    int32_t* out_flag;              // [nreq]
+    int32_t* error;                 // set when a wait for an item ran out
+};
+
 struct DecodeArgs {
     uint64_t n;
     uint32_t nmask;
@@ -280,6 +312,9 @@ void set_last_error(const std::string& s);
 
 // device entry points (sfft_exact.cu)
 cudaError_t launch_exact_round(const ExactArgs& a, uint32_t batch, size_t smem, cudaStream_t st, bool fp64);
+// persistent path: CTAs that fit on the device at `smem`, and the launch
+int exact_persistent_ctas(size_t smem, bool fp64);
+cudaError_t launch_exact_persistent(const PersistArgs& a, uint32_t ctas, size_t smem, cudaStream_t st, bool fp64);
 cudaError_t launch_exact_decode(const DecodeArgs& a, cudaStream_t st);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                           uint32_t count, uint32_t* out, cudaStream_t st);

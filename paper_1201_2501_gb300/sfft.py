@@ -140,6 +140,10 @@ _SIGS = {
     "sfft_window_taps": (ctypes.c_int, [_u64, _u32, _dbl, _dbl, _i64p, _dblp, _u64]),
     "sfft_window_gains": (ctypes.c_int, [_u64, _u32, _dbl, _dbl, _u64, _dblp]),
     "sfft_execute_requests": (ctypes.c_int, [_vp, ctypes.POINTER(SfftRequest), _u32, _vp, _vp, _vp, _u32, _vp, _vp]),
+    "sfft_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _u32, ctypes.POINTER(_vp)]),
+    "sfft_batch_plan_destroy": (ctypes.c_int, [_vp]),
+    "sfft_batch_execute": (ctypes.c_int, [_vp, _u32p, ctypes.POINTER(SfftRequest), _u32, _vp, _vp, _vp, _u32, _vp,
+                                          _vp]),
     "sfft_server_create": (ctypes.c_int, [ctypes.POINTER(SfftServerConfig), ctypes.POINTER(_vp)]),
     "sfft_server_destroy": (ctypes.c_int, [_vp]),
     "sfft_submit": (ctypes.c_int, [_vp, _P, ctypes.POINTER(SfftJob), _u64p]),
@@ -335,6 +339,74 @@ def sfft_execute_requests(plan: Plan, xs, seeds, ids, cap: int, outputs=None, st
     _check(lib().sfft_execute_requests(plan.handle, table, batch, _stream_ptr(stream), _ptr(idx), _ptr(val), cap,
                                        _ptr(count), _ptr(flag)), "sfft_execute_requests")
     return outputs
+
+
+class BatchPlan:
+    """Exact-mode plans of any (n, k) run together in one persistent launch (``sfft_batch_*``)."""
+
+    def __init__(self, plans, max_requests: int):
+        self.plans = list(plans)  # the plans must outlive the batch plan
+        arr = (_vp * len(self.plans))(*[p.handle for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib().sfft_batch_plan_create(arr, len(self.plans), max_requests, ctypes.byref(h)),
+               "sfft_batch_plan_create")
+        self.handle = h
+        self.max_requests = max_requests
+
+    @staticmethod
+    def prepare(plan_of, xs, seeds, ids, periods=None):
+        """The host tables of a batch (plan indices and requests), reusable across calls."""
+        nreq = len(xs)
+        table = (SfftRequest * nreq)()
+        for r in range(nreq):
+            table[r].d_x = _ptr(xs[r])
+            table[r].seed = int(seeds[r])
+            table[r].id = int(ids[r])
+            table[r].period = int(periods[r]) if periods is not None else 0
+        po = (ctypes.c_uint32 * nreq)(*[int(p) for p in plan_of])
+        return po, table, nreq, list(xs)
+
+    def execute_prepared(self, prepared, cap: int, outputs, stream=None):
+        po, table, nreq, _ = prepared
+        idx, val, count, flag = outputs
+        _check(lib().sfft_batch_execute(self.handle, po, table, nreq, _stream_ptr(stream), _ptr(idx), _ptr(val),
+                                        cap, _ptr(count), _ptr(flag)), "sfft_batch_execute")
+        return outputs
+
+    def execute(self, plan_of, xs, seeds, ids, cap: int, outputs=None, stream=None, periods=None):
+        """Request r uses plans[plan_of[r]] on device tensor xs[r] with (seeds[r], ids[r]); outputs as
+        for sfft_execute."""
+        import torch
+
+        nreq = len(xs)
+        if outputs is None:
+            dev = xs[0].device
+            outputs = (torch.empty((nreq, cap), dtype=torch.int32, device=dev),
+                       torch.empty((nreq, cap, 2), dtype=torch.float64, device=dev),
+                       torch.empty((nreq,), dtype=torch.int32, device=dev),
+                       torch.empty((nreq,), dtype=torch.int32, device=dev))
+        table = (SfftRequest * nreq)()
+        for r in range(nreq):
+            table[r].d_x = _ptr(xs[r])
+            table[r].seed = int(seeds[r])
+            table[r].id = int(ids[r])
+            table[r].period = int(periods[r]) if periods is not None else 0
+        po = (ctypes.c_uint32 * nreq)(*[int(p) for p in plan_of])
+        idx, val, count, flag = outputs
+        _check(lib().sfft_batch_execute(self.handle, po, table, nreq, _stream_ptr(stream), _ptr(idx), _ptr(val),
+                                        cap, _ptr(count), _ptr(flag)), "sfft_batch_execute")
+        return outputs
+
+    def close(self):
+        if self.handle:
+            lib().sfft_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
