@@ -445,6 +445,21 @@ def context_measurements(sfft, plan, x, cap, stream, args):
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
     out["latency_us"] = {"p50": p50, "p99": p99, "runs": len(lat), "what": "one request per call, device time"}
+    # the same single request replayed as a CUDA graph (every round's launches in one graph launch)
+    g1 = sfft.Graph(p1, x[0:1], 1, SEED, cap, o1)
+    for _ in range(10):
+        g1.launch(stream)
+    torch.cuda.synchronize()
+    for i, (a, b) in enumerate(ev):
+        a.record(stream)
+        g1.launch(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    lat_g = sorted(a.elapsed_time(b) * 1000 for a, b in ev)
+    g1.close()
+    out["latency_graph_us"] = {"p50": lat_g[len(lat_g) // 2],
+                               "p99": lat_g[min(len(lat_g) - 1, int(math.ceil(0.99 * len(lat_g))) - 1)],
+                               "runs": len(lat_g), "what": "one request per graph launch (sfft_graph_launch), device time"}
     # plain GPU sFFT: the same kernels, one request at a time, no batching
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = min(x.shape[0], 256)

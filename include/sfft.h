@@ -184,6 +184,57 @@ sfft_status sfft_execute_requests(sfft_plan plan, const sfft_request* h_reqs, ui
                                   uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag);
 
 /* ---------------------------------------------------------------------------------------------- */
+/* CUDA graphs of a fixed batch                                                                    */
+/* ---------------------------------------------------------------------------------------------- */
+/*
+ * Capture one whole transform of a fixed batch (every round's launches, the internal stream fork and
+ * join, the clears) into an instantiated CUDA graph, replayed by sfft_graph_launch with one call.
+ * d_x != NULL: the batch is the rows of d_x with `seed` (as sfft_execute).  d_x == NULL: the batch is
+ * the plan's request table, refilled between replays with sfft_plan_set_requests (as
+ * sfft_execute_requests).  Outputs as for sfft_execute.  The plan must outlive the graph and serve
+ * one stream at a time (graph replays included).
+ * Errors: INVALID_ARG, CUDA (capture or instantiation failed).
+ */
+typedef struct sfft_graph_s* sfft_graph;
+sfft_status sfft_graph_create(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, uint32_t* d_idx,
+                              double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag, sfft_graph* out);
+sfft_status sfft_graph_launch(sfft_graph g, void* stream);
+sfft_status sfft_graph_destroy(sfft_graph g);
+
+/* Copy `batch` requests (host table) into the plan's request table on `stream` (for graphs captured
+ * with d_x == NULL).  Errors: INVALID_ARG (as sfft_execute_requests), CUDA. */
+sfft_status sfft_plan_set_requests(sfft_plan plan, const sfft_request* h_reqs, uint32_t batch, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Autotuner                                                                                       */
+/* ---------------------------------------------------------------------------------------------- */
+/*
+ * The paper leaves the bin count B = Theta(k) and the window's transition fraction alpha (hence its
+ * width w ~ B log(1/delta) / alpha) as constants; this library also splits a batch over internal
+ * streams.  sfft_autotune times candidate settings for base's (n, k, mode, delta, precision):
+ * bins_per_k in {2, 4, 8} (exact) or {4, 8, 16} (general), alpha0 in {0.25, 0.5, 0.75}, streams in
+ * {1, 2, 4, 8}, each on the same `batch` (<= 256) synthetic signals made on the device (exact: k
+ * unit-magnitude coefficients; general: k coefficients with |X| = 10^u, u uniform on [0, 1), plus
+ * complex Gaussian time noise at snr_db), `reps` timed transforms after one warm-up (CUDA events).
+ * Each candidate is scored against the planted coefficients; *best receives the fastest candidate
+ * that is at least as accurate as base's own settings (as many exact recoveries with values within
+ * 1e-4 in exact mode; a mean relative l2 error ||zhat - X_heavy|| / ||X_heavy|| within 5 % of base's
+ * in general mode).  report (may be NULL) receives up to report_cap entries, base's first.
+ * Allocates and synchronises the device; not for a latency-critical path.
+ */
+typedef struct sfft_tune_entry {
+    double bins_per_k, alpha0;
+    uint32_t streams;
+    int32_t status;          /* plan creation / run status of the candidate */
+    double us_per_transform; /* device time per transform */
+    uint32_t exact;          /* requests recovered exactly (exact mode) */
+    uint32_t chosen;         /* 1 for the candidate copied to *best */
+    double rel_err;          /* mean ||zhat - X_heavy|| / ||X_heavy|| */
+} sfft_tune_entry;
+sfft_status sfft_autotune(const sfft_params* base, uint32_t batch, double snr_db, uint64_t seed, uint32_t reps,
+                          sfft_params* best, sfft_tune_entry* report, uint32_t report_cap, uint32_t* n_report);
+
+/* ---------------------------------------------------------------------------------------------- */
 /* Mixed batches in one persistent launch                                                          */
 /* ---------------------------------------------------------------------------------------------- */
 /*

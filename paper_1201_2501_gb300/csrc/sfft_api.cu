@@ -475,21 +475,83 @@ sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64
     return execute_batch(plan, d_x, nullptr, batch, seed, (cudaStream_t)stream, d_idx, d_val, cap, d_count, d_flag);
 }
 
-sfft_status sfft_execute_requests(sfft_plan plan, const sfft_request* h_reqs, uint32_t batch, void* stream,
-                                  uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag) {
-    if (!plan || !h_reqs || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
-    if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
+sfft_status sfft_plan_set_requests(sfft_plan plan, const sfft_request* h_reqs, uint32_t batch, void* stream) {
+    if (!plan || !h_reqs || batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
     const size_t align = plan->p.precision == SFFT_FP64 ? 16 : 8;
     for (uint32_t r = 0; r < batch; ++r) {
         if (!h_reqs[r].d_x || ((uintptr_t)h_reqs[r].d_x % align) != 0) return SFFT_ERR_INVALID_ARG;
         const uint32_t per = h_reqs[r].period;
         if (per != 0 && (!is_pow2(per) || per > plan->p.n)) return SFFT_ERR_INVALID_ARG;
     }
-    cudaStream_t st = (cudaStream_t)stream;
     // a pageable source is staged by the driver before the call returns, so h_reqs may be reused at once
-    SFFT_CUDA(cudaMemcpyAsync(plan->d_reqs, h_reqs, (size_t)batch * sizeof(ReqDesc), cudaMemcpyHostToDevice, st),
+    SFFT_CUDA(cudaMemcpyAsync(plan->d_reqs, h_reqs, (size_t)batch * sizeof(ReqDesc), cudaMemcpyHostToDevice,
+                              (cudaStream_t)stream),
               "copy request table");
-    return execute_batch(plan, nullptr, plan->d_reqs, batch, 0, st, d_idx, d_val, cap, d_count, d_flag);
+    return SFFT_OK;
+}
+
+sfft_status sfft_execute_requests(sfft_plan plan, const sfft_request* h_reqs, uint32_t batch, void* stream,
+                                  uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag) {
+    if (!plan || !h_reqs || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
+    const sfft_status st = sfft_plan_set_requests(plan, h_reqs, batch, stream);
+    if (st != SFFT_OK) return st;
+    return execute_batch(plan, nullptr, plan->d_reqs, batch, 0, (cudaStream_t)stream, d_idx, d_val, cap, d_count,
+                         d_flag);
+}
+
+}  // extern "C"
+
+struct sfft_graph_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+sfft_status sfft_graph_create(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, uint32_t* d_idx,
+                              double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag, sfft_graph* out) {
+    if (!out) return SFFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!plan || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
+    if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
+    auto* g = new (std::nothrow) sfft_graph_s();
+    if (!g) return SFFT_ERR_OOM;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    sfft_status st = SFFT_OK;
+    if (e == cudaSuccess) {
+        st = execute_batch(plan, d_x, d_x ? nullptr : plan->d_reqs, batch, seed, cs, d_idx, d_val, cap, d_count,
+                           d_flag);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
+        if (st == SFFT_OK && e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess && st == SFFT_OK) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess || st != SFFT_OK) {
+        if (e != cudaSuccess) set_last_error(std::string("graph capture: ") + cudaGetErrorString(e));
+        cudaGetLastError();
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return st != SFFT_OK ? st : SFFT_ERR_CUDA;
+    }
+    *out = g;
+    return SFFT_OK;
+}
+
+sfft_status sfft_graph_launch(sfft_graph g, void* stream) {
+    if (!g) return SFFT_ERR_INVALID_ARG;
+    SFFT_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream), "graph launch");
+    return SFFT_OK;
+}
+
+sfft_status sfft_graph_destroy(sfft_graph g) {
+    if (!g) return SFFT_OK;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return SFFT_OK;
 }
 
 sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, uint64_t seed, void* stream,

@@ -1,0 +1,291 @@
+// sfft_tune.cu -- the autotuner behind sfft_autotune (include/sfft.h): synthetic signals made on the
+// device from host-known spectra, one plan per candidate setting, CUDA-event timing, and scoring
+// against the planted coefficients.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "philox.cuh"
+#include "sfft_internal.h"
+
+using namespace sfft;
+
+namespace {
+
+constexpr uint32_t kTuneKind = 7;  // Philox counter kind of the tuning signals (not a hashing draw)
+
+// x[s][t] = (1/n) sum_j X[s][j] e^{+2 pi i (f[s][j] t mod n) / n} (+ complex Gaussian noise of standard
+// deviation sd per component when sd > 0, Box-Muller on Philox words keyed by seed).
+template <typename C>
+__global__ void k_synth(C* x, uint64_t n, uint32_t k, uint32_t batch, const uint32_t* f, const float2* X, float sd,
+                        uint64_t seed) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t s = blockIdx.y;
+    if (t >= n || s >= batch) return;
+    const uint32_t nmask = (uint32_t)(n - 1);
+    const float inv = 2.0f / (float)n;
+    float re = 0.f, im = 0.f;
+    for (uint32_t j = 0; j < k; ++j) {
+        const uint32_t e = (f[(size_t)s * k + j] * (uint32_t)t) & nmask;  // exact phase numerator
+        const int32_t es = e > (nmask >> 1) ? (int32_t)((int64_t)e - (int64_t)n) : (int32_t)e;
+        float sn, cs;
+        sincospif((float)es * inv, &sn, &cs);
+        const float2 v = X[(size_t)s * k + j];
+        re += v.x * cs - v.y * sn;
+        im += v.x * sn + v.y * cs;
+    }
+    re /= (float)n;
+    im /= (float)n;
+    if (sd > 0.f) {
+        const Words4 w = philox4x32_10((uint32_t)t, (uint32_t)(t >> 32), s, kTuneKind, (uint32_t)seed,
+                                       (uint32_t)(seed >> 32));
+        const float u1 = ((float)(w.w[0] >> 8) + 1.0f) * (1.0f / 16777216.0f);  // (0, 1]
+        const float u2 = (float)(w.w[1] >> 8) * (1.0f / 16777216.0f);
+        const float r = sd * sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        re += r * cs;
+        im += r * sn;
+    }
+    C out;
+    out.x = re;
+    out.y = im;
+    x[(size_t)s * n + t] = out;
+}
+
+struct Truth {
+    std::vector<uint32_t> f;  // [batch][k] sorted frequencies
+    std::vector<float2> X;    // [batch][k]
+};
+
+// Spectra drawn on the host: k distinct frequencies (rejection on Philox words), unit magnitudes
+// (exact mode) or magnitudes 10^u, u uniform on [0, 1) (general mode), uniform phases.
+Truth draw_truth(uint64_t n, uint32_t k, uint32_t batch, bool general, uint64_t seed) {
+    Truth tr;
+    tr.f.resize((size_t)batch * k);
+    tr.X.resize((size_t)batch * k);
+    for (uint32_t s = 0; s < batch; ++s) {
+        std::vector<uint32_t> fs;
+        uint32_t ctr = 0;
+        while (fs.size() < k) {
+            const Words4 w = philox4x32_10(ctr++, s, kTuneKind, 1, (uint32_t)seed, (uint32_t)(seed >> 32));
+            for (int q = 0; q < 4 && fs.size() < k; ++q) {
+                const uint32_t v = w.w[q] & (uint32_t)(n - 1);
+                if (std::find(fs.begin(), fs.end(), v) == fs.end()) fs.push_back(v);
+            }
+        }
+        std::sort(fs.begin(), fs.end());
+        for (uint32_t j = 0; j < k; ++j) {
+            const Words4 w = philox4x32_10(j, s, kTuneKind, 2, (uint32_t)seed, (uint32_t)(seed >> 32));
+            const double u = (double)(w.w[0] >> 8) / 16777216.0, ph = 2.0 * M_PI * (double)(w.w[1] >> 8) / 16777216.0;
+            const double mag = general ? std::pow(10.0, u) : 1.0;
+            tr.f[(size_t)s * k + j] = fs[j];
+            tr.X[(size_t)s * k + j] = make_float2((float)(mag * std::cos(ph)), (float)(mag * std::sin(ph)));
+        }
+    }
+    return tr;
+}
+
+struct Score {
+    uint32_t exact = 0;   // requests whose support is exactly the planted one, values within 1e-4
+    double rel_err = 0;   // mean over requests of ||zhat - X_heavy|| / ||X_heavy||
+    double max_err = 0;   // largest value error among exact requests
+};
+
+Score score(const Truth& tr, uint32_t k, uint32_t batch, const std::vector<uint32_t>& idx,
+            const std::vector<double>& val, const std::vector<uint32_t>& cnt, uint32_t cap) {
+    Score sc;
+    for (uint32_t s = 0; s < batch; ++s) {
+        const uint32_t c = std::min(cnt[s], cap);
+        const uint32_t* f = &tr.f[(size_t)s * k];
+        const float2* X = &tr.X[(size_t)s * k];
+        double e2 = 0, x2 = 0, mx = 0;
+        uint32_t j = 0, matched = 0;
+        for (uint32_t q = 0; q < c; ++q) {  // both lists ascending
+            const uint32_t i = idx[(size_t)s * cap + q];
+            const double vr = val[((size_t)s * cap + q) * 2], vi = val[((size_t)s * cap + q) * 2 + 1];
+            while (j < k && f[j] < i) {
+                e2 += (double)X[j].x * X[j].x + (double)X[j].y * X[j].y;
+                ++j;
+            }
+            if (j < k && f[j] == i) {
+                const double dr = vr - X[j].x, di = vi - X[j].y;
+                e2 += dr * dr + di * di;
+                mx = std::max(mx, std::sqrt(dr * dr + di * di));
+                ++matched;
+                ++j;
+            } else {
+                e2 += vr * vr + vi * vi;
+            }
+        }
+        for (; j < k; ++j) e2 += (double)X[j].x * X[j].x + (double)X[j].y * X[j].y;
+        for (uint32_t q = 0; q < k; ++q) x2 += (double)X[q].x * X[q].x + (double)X[q].y * X[q].y;
+        sc.rel_err += std::sqrt(e2 / x2) / batch;
+        if (matched == k && c == k && mx <= 1e-4) {
+            ++sc.exact;
+            sc.max_err = std::max(sc.max_err, mx);
+        }
+    }
+    return sc;
+}
+
+}  // namespace
+
+extern "C" {
+
+sfft_status sfft_autotune(const sfft_params* base, uint32_t batch, double snr_db, uint64_t seed, uint32_t reps,
+                          sfft_params* best, sfft_tune_entry* report, uint32_t report_cap, uint32_t* n_report) {
+    if (!base || !best || batch == 0 || batch > 256) return SFFT_ERR_INVALID_ARG;
+    sfft_status st = validate_params(base);
+    if (st != SFFT_OK) return st;
+    const bool general = base->mode == SFFT_GENERAL, fp64 = base->precision == SFFT_FP64;
+    const uint64_t n = base->n;
+    const uint32_t k = base->k;
+    if (reps == 0) reps = 5;
+    // the synthetic batch (device) and its planted spectra (host)
+    const Truth tr = draw_truth(n, k, batch, general, seed);
+    double power = 0;  // mean |x_t|^2 of the clean signals (Parseval), for the noise level
+    for (const float2& v : tr.X) power += ((double)v.x * v.x + (double)v.y * v.y) / ((double)n * n * batch);
+    const float sd = general ? (float)std::sqrt(power / std::pow(10.0, snr_db / 10.0) / 2.0) : 0.f;
+    void* d_x = nullptr;
+    uint32_t* d_f = nullptr;
+    float2* d_X = nullptr;
+    const size_t csz = fp64 ? 16 : 8;
+    cudaError_t e = cudaMalloc(&d_x, (size_t)batch * n * csz);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_f, tr.f.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_X, tr.X.size() * 8);
+    auto cleanup = [&]() {
+        cudaFree(d_x);
+        cudaFree(d_f);
+        cudaFree(d_X);
+    };
+    if (e != cudaSuccess) {
+        cleanup();
+        set_last_error(std::string("autotune: ") + cudaGetErrorString(e));
+        cudaGetLastError();
+        return SFFT_ERR_OOM;
+    }
+    cudaMemcpy(d_f, tr.f.data(), tr.f.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_X, tr.X.data(), tr.X.size() * 8, cudaMemcpyHostToDevice);
+    const dim3 grid((unsigned)((n + 255) / 256), batch);
+    if (fp64)
+        k_synth<double2><<<grid, 256>>>(static_cast<double2*>(d_x), n, k, batch, d_f, d_X, sd, seed);
+    else
+        k_synth<float2><<<grid, 256>>>(static_cast<float2*>(d_x), n, k, batch, d_f, d_X, sd, seed);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+        cleanup();
+        set_last_error(std::string("autotune: ") + cudaGetErrorString(e));
+        return SFFT_ERR_CUDA;
+    }
+    // candidates: B = pow2(c k) (c = bins_per_k), window width via alpha0, internal stream groups
+    std::vector<double> cs = general ? std::vector<double>{4.0, 8.0, 16.0} : std::vector<double>{2.0, 4.0, 8.0};
+    std::vector<double> as = {0.25, 0.5, 0.75};
+    std::vector<uint32_t> ss = {1, 2, 4, 8};
+    struct Cand {
+        sfft_params p;
+        sfft_tune_entry r;
+    };
+    std::vector<Cand> cands;
+    {
+        Cand c0{*base, {}};  // the base settings first: the accuracy reference
+        cands.push_back(c0);
+    }
+    for (double c : cs)
+        for (double a : as)
+            for (uint32_t s : ss) {
+                sfft_params p = *base;
+                p.bins_per_k = c;
+                p.alpha0 = a;
+                p.streams = s;
+                if (p.bins_per_k == base->bins_per_k && p.alpha0 == base->alpha0 && p.streams == base->streams)
+                    continue;
+                cands.push_back(Cand{p, {}});
+            }
+    cudaStream_t stream = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    uint32_t* d_idx = nullptr;
+    double* d_val = nullptr;
+    uint32_t *d_cnt = nullptr, cap = 0;
+    int32_t* d_flag = nullptr;
+    std::vector<uint32_t> h_idx, h_cnt(batch);
+    std::vector<double> h_val;
+    for (Cand& c : cands) {
+        c.r.bins_per_k = c.p.bins_per_k;
+        c.r.alpha0 = c.p.alpha0;
+        c.r.streams = c.p.streams;
+        c.r.status = SFFT_OK;
+        sfft_plan plan = nullptr;
+        sfft_status ps = sfft_plan_create(&c.p, batch, &plan);
+        if (ps != SFFT_OK) {
+            c.r.status = ps;
+            continue;
+        }
+        if (c.p.z_cap > cap) {
+            cudaFree(d_idx);
+            cudaFree(d_val);
+            cudaFree(d_cnt);
+            cudaFree(d_flag);
+            cap = c.p.z_cap;
+            cudaMalloc((void**)&d_idx, (size_t)batch * cap * 4);
+            cudaMalloc((void**)&d_val, (size_t)batch * cap * 16);
+            cudaMalloc((void**)&d_cnt, (size_t)batch * 4);
+            cudaMalloc((void**)&d_flag, (size_t)batch * 4);
+            h_idx.resize((size_t)batch * cap);
+            h_val.resize((size_t)batch * cap * 2);
+        }
+        ps = sfft_execute(plan, d_x, batch, seed, stream, d_idx, d_val, cap, d_cnt, d_flag);  // warm-up
+        cudaEventRecord(e0, stream);
+        for (uint32_t q = 0; q < reps && ps == SFFT_OK; ++q)
+            ps = sfft_execute(plan, d_x, batch, seed, stream, d_idx, d_val, cap, d_cnt, d_flag);
+        cudaEventRecord(e1, stream);
+        if (ps == SFFT_OK && cudaStreamSynchronize(stream) == cudaSuccess) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            c.r.us_per_transform = 1000.0 * ms / ((double)reps * batch);
+            cudaMemcpy(h_idx.data(), d_idx, h_idx.size() * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(h_val.data(), d_val, h_val.size() * 8, cudaMemcpyDeviceToHost);
+            cudaMemcpy(h_cnt.data(), d_cnt, (size_t)batch * 4, cudaMemcpyDeviceToHost);
+            const Score sc = score(tr, k, batch, h_idx, h_val, h_cnt, cap);
+            c.r.exact = sc.exact;
+            c.r.rel_err = sc.rel_err;
+        } else {
+            c.r.status = ps != SFFT_OK ? ps : SFFT_ERR_CUDA;
+        }
+        sfft_plan_destroy(plan);
+    }
+    cudaFree(d_idx);
+    cudaFree(d_val);
+    cudaFree(d_cnt);
+    cudaFree(d_flag);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(stream);
+    cleanup();
+    // the fastest candidate at least as accurate as the base settings: as many exact recoveries
+    // (exact mode), a mean relative l2 error within 5 % of the base's (general mode)
+    const sfft_tune_entry& ref = cands[0].r;
+    if (ref.status != SFFT_OK) return (sfft_status)ref.status;
+    size_t pick = 0;
+    for (size_t i = 1; i < cands.size(); ++i) {
+        const sfft_tune_entry& r = cands[i].r;
+        if (r.status != SFFT_OK) continue;
+        const bool good = general ? r.rel_err <= 1.05 * ref.rel_err + 1e-12 : r.exact >= ref.exact;
+        if (good && r.us_per_transform < cands[pick].r.us_per_transform) pick = i;
+    }
+    *best = cands[pick].p;
+    if (n_report) *n_report = (uint32_t)cands.size();
+    if (report)
+        for (size_t i = 0; i < cands.size() && i < report_cap; ++i) {
+            report[i] = cands[i].r;
+            report[i].chosen = i == pick ? 1u : 0u;
+        }
+    return SFFT_OK;
+}
+
+}  // extern "C"

@@ -101,6 +101,14 @@ class SfftServerStats(ctypes.Structure):
                 ("p99_us", ctypes.c_double)]
 
 
+class SfftTuneEntry(ctypes.Structure):
+    """Mirror of ``sfft_tune_entry``."""
+
+    _fields_ = [("bins_per_k", ctypes.c_double), ("alpha0", ctypes.c_double), ("streams", ctypes.c_uint32),
+                ("status", ctypes.c_int32), ("us_per_transform", ctypes.c_double), ("exact", ctypes.c_uint32),
+                ("chosen", ctypes.c_uint32), ("rel_err", ctypes.c_double)]
+
+
 class SfftError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -140,6 +148,11 @@ _SIGS = {
     "sfft_window_taps": (ctypes.c_int, [_u64, _u32, _dbl, _dbl, _i64p, _dblp, _u64]),
     "sfft_window_gains": (ctypes.c_int, [_u64, _u32, _dbl, _dbl, _u64, _dblp]),
     "sfft_execute_requests": (ctypes.c_int, [_vp, ctypes.POINTER(SfftRequest), _u32, _vp, _vp, _vp, _u32, _vp, _vp]),
+    "sfft_autotune": (ctypes.c_int, [_P, _u32, _dbl, _u64, _u32, _P, ctypes.POINTER(SfftTuneEntry), _u32, _u32p]),
+    "sfft_graph_create": (ctypes.c_int, [_vp, _vp, _u32, _u64, _vp, _vp, _u32, _vp, _vp, ctypes.POINTER(_vp)]),
+    "sfft_graph_launch": (ctypes.c_int, [_vp, _vp]),
+    "sfft_graph_destroy": (ctypes.c_int, [_vp]),
+    "sfft_plan_set_requests": (ctypes.c_int, [_vp, ctypes.POINTER(SfftRequest), _u32, _vp]),
     "sfft_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _u32, ctypes.POINTER(_vp)]),
     "sfft_batch_plan_destroy": (ctypes.c_int, [_vp]),
     "sfft_batch_execute": (ctypes.c_int, [_vp, _u32p, ctypes.POINTER(SfftRequest), _u32, _vp, _vp, _vp, _u32, _vp,
@@ -339,6 +352,57 @@ def sfft_execute_requests(plan: Plan, xs, seeds, ids, cap: int, outputs=None, st
     _check(lib().sfft_execute_requests(plan.handle, table, batch, _stream_ptr(stream), _ptr(idx), _ptr(val), cap,
                                        _ptr(count), _ptr(flag)), "sfft_execute_requests")
     return outputs
+
+
+def sfft_autotune(base: SfftParams, batch: int = 16, snr_db: float = 20.0, seed: int = 1, reps: int = 5):
+    """Runs the library's autotuner for ``base``; returns (best SfftParams, list of report dicts)."""
+    best = SfftParams()
+    rep = (SfftTuneEntry * 64)()
+    nrep = ctypes.c_uint32()
+    _check(lib().sfft_autotune(ctypes.byref(base), batch, snr_db, seed, reps, ctypes.byref(best), rep, 64,
+                               ctypes.byref(nrep)), "sfft_autotune")
+    out = [{f: getattr(rep[i], f) for f, _ in SfftTuneEntry._fields_} for i in range(min(nrep.value, 64))]
+    return best, out
+
+
+class Graph:
+    """A whole transform of a fixed batch captured as a CUDA graph (``sfft_graph_*``).  x = None: the
+    batch is the plan's request table (refill it with ``set_requests``)."""
+
+    def __init__(self, plan: Plan, x, batch: int, seed: int, cap: int, outputs):
+        idx, val, count, flag = outputs
+        h = ctypes.c_void_p()
+        _check(lib().sfft_graph_create(plan.handle, _ptr(x) if x is not None else None, batch, seed, _ptr(idx),
+                                       _ptr(val), cap, _ptr(count), _ptr(flag), ctypes.byref(h)), "sfft_graph_create")
+        self.handle = h
+        self.plan = plan
+        self.outputs = outputs
+
+    def set_requests(self, xs, seeds, ids, stream=None, periods=None):
+        nreq = len(xs)
+        table = (SfftRequest * nreq)()
+        for r in range(nreq):
+            table[r].d_x = _ptr(xs[r])
+            table[r].seed = int(seeds[r])
+            table[r].id = int(ids[r])
+            table[r].period = int(periods[r]) if periods is not None else 0
+        _check(lib().sfft_plan_set_requests(self.plan.handle, table, nreq, _stream_ptr(stream)),
+               "sfft_plan_set_requests")
+
+    def launch(self, stream=None):
+        _check(lib().sfft_graph_launch(self.handle, _stream_ptr(stream)), "sfft_graph_launch")
+        return self.outputs
+
+    def close(self):
+        if self.handle:
+            lib().sfft_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BatchPlan:

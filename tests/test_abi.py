@@ -71,7 +71,8 @@ def test_binding_struct_layouts_match_the_header(tmp_path):
 
     mirrors = {"sfft_params": sfft.SfftParams, "sfft_request": sfft.SfftRequest,
                "sfft_server_config": sfft.SfftServerConfig, "sfft_job": sfft.SfftJob,
-               "sfft_job_result": sfft.SfftJobResult, "sfft_server_stats": sfft.SfftServerStats}
+               "sfft_job_result": sfft.SfftJobResult, "sfft_server_stats": sfft.SfftServerStats,
+               "sfft_tune_entry": sfft.SfftTuneEntry}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sfft.h"', "int main(void) {"]
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
