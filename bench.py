@@ -513,6 +513,8 @@ def context_measurements(sfft, plan, x, cap, stream, args):
         out["general_case"] = general_measurement(sfft, stream, args)
     if not args.no_serving:
         out["serving"] = serving_measurement(sfft, args)
+    if not args.no_mixed:
+        out["mixed_batch"] = mixed_batch_measurement(sfft, args)
     return out
 
 
@@ -644,6 +646,112 @@ def serving_measurement(sfft, args):
     }
 
 
+MIXED_EXPS = (16, 18, 20, 22, 24)
+MIXED_KS = (8, 32, 128, 512)
+
+
+def mixed_batch_measurement(sfft, args):
+    """Uneven instances in one batch: n = 2^e and k drawn uniformly from the grids above (log-uniform
+    over 2^16..2^24 and 8..512), half exactly k-sparse and half k heavy coefficients (|X| in [1, 10])
+    plus complex Gaussian time noise at SNR 20 dB, every signal resident on the device.  The exact half
+    runs as ONE persistent launch over all its plans (sfft_batch_execute); the noisy half as per-round
+    launches of each plan on a second stream, at the same time.  Device-timed with CUDA events."""
+    import torch
+
+    from paper_1201_2501_gb300 import workloads
+
+    rng = np.random.default_rng(0x5EED4000)
+    nreq = args.mixed_requests
+    reqs = []  # (mode, e, k, signal, support, values)
+    for i in range(nreq):
+        mode = sfft.SFFT_EXACT if i % 2 == 0 else sfft.SFFT_GENERAL
+        e, k = int(rng.choice(MIXED_EXPS)), int(rng.choice(MIXED_KS))
+        x, sup, val = workloads.sparse_signal_device(1 << e, k, workloads.seed_for(4, i), "cuda",
+                                                     snr_db=None if mode == sfft.SFFT_EXACT else 20.0)
+        reqs.append((mode, e, k, x, sup, val))
+    exact_types = sorted({(e, k) for m, e, k, *_ in reqs if m == sfft.SFFT_EXACT})
+    gen_types = sorted({(e, k) for m, e, k, *_ in reqs if m == sfft.SFFT_GENERAL})
+    xplans = [sfft.Plan(sfft.sfft_params_default(1 << e, k, sfft.SFFT_EXACT, delta=DELTA), 1) for e, k in exact_types]
+    ex = [(r, q) for r, q in enumerate(reqs) if q[0] == sfft.SFFT_EXACT]
+    bplan = sfft.BatchPlan(xplans, len(ex))
+    cap = max(p.params.z_cap for p in xplans)
+    prepared = bplan.prepare([exact_types.index((q[1], q[2])) for _, q in ex], [q[3] for _, q in ex],
+                             [SEED] * len(ex), [r for r, _ in ex])
+    xouts = (torch.empty((len(ex), cap), dtype=torch.int32, device="cuda"),
+             torch.empty((len(ex), cap, 2), dtype=torch.float64, device="cuda"),
+             torch.empty((len(ex),), dtype=torch.int32, device="cuda"),
+             torch.empty((len(ex),), dtype=torch.int32, device="cuda"))
+    gruns = []
+    for e, k in gen_types:
+        sel = [(r, q) for r, q in enumerate(reqs) if q[0] == sfft.SFFT_GENERAL and (q[1], q[2]) == (e, k)]
+        p = sfft.sfft_params_default(1 << e, k, sfft.SFFT_GENERAL, delta=DELTA)
+        gruns.append((sfft.Plan(p, len(sel)), sel, p.z_cap))
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run_exact():
+        bplan.execute_prepared(prepared, cap, xouts, sb)
+
+    gouts = [None] * len(gruns)
+
+    def run_general():
+        for gi, (pl, sel, zc) in enumerate(gruns):
+            gouts[gi] = sfft.sfft_execute_requests(pl, [q[3] for _, q in sel], [SEED] * len(sel), [r for r, _ in sel],
+                                                   zc, gouts[gi], sa)
+
+    def timed(fn_list):
+        cur = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for s in (sa, sb):
+            s.wait_stream(cur)
+        for fn in fn_list:
+            fn()
+        for s in (sa, sb):
+            cur.wait_stream(s)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    timed([run_exact, run_general])  # warm-up
+    ms_both = min(timed([run_exact, run_general]) for _ in range(2))
+    ms_exact = timed([run_exact])
+    ms_general = timed([run_general])
+    # accuracy against the planted coefficients
+    idx, val, cnt = (t.cpu().numpy() for t in xouts[:3])
+    exact_ok = sum(np.array_equal(idx[j, :cnt[j]].view(np.uint32).astype(np.int64), q[4]) for j, (_, q) in enumerate(ex))
+    rel = []
+    for (pl, sel, zc), go in zip(gruns, gouts):
+        gi, gv, gc = (t.cpu().numpy() for t in go[:3])
+        for j, (_, q) in enumerate(sel):
+            n = 1 << q[1]
+            Z = np.zeros(n, dtype=np.complex128)
+            c = int(gc[j])
+            Z[gi[j, :c].view(np.uint32).astype(np.int64)] = gv[j, :c, 0] + 1j * gv[j, :c, 1]
+            Xh = np.zeros(n, dtype=np.complex128)
+            Xh[q[4]] = q[5]
+            rel.append(float(np.linalg.norm(Z - Xh) / np.linalg.norm(q[5])))
+    bplan.close()
+    for p in xplans:
+        p.close()
+    for pl, _, _ in gruns:
+        pl.close()
+    del reqs
+    torch.cuda.empty_cache()
+    return {
+        "workload": "n = 2^e, e uniform on {16,18,20,22,24}; k uniform on {8,32,128,512}; half exactly k-sparse "
+                    "(|X| = 1), half k heavy (|X| = 10^U[0,1]) + complex Gaussian time noise at SNR 20 dB; "
+                    "library default B and w (bins_per_k 4 / 8, alpha0 1/2, delta 1e-6)",
+        "requests": nreq, "exact_requests": len(ex), "general_requests": nreq - len(ex),
+        "exact_plans_in_one_persistent_launch": len(xplans), "general_plans": len(gruns),
+        "ms_total": ms_both, "transforms_per_s": nreq / (ms_both / 1000.0),
+        "ms_exact_alone": ms_exact, "ms_general_alone": ms_general,
+        "exact_support_fraction": exact_ok / max(1, len(ex)),
+        "general_rel_l2_to_heavy_mean": float(np.mean(rel)) if rel else None,
+        "what": "device time of both halves launched together (persistent exact launch on one stream, "
+                "per-round general launches on another)",
+    }
+
+
 def precision_table(args):
     """Error per recovered coefficient for the data-path precision (complex64 gather, fold and bin FFT
     with FP64 decode, or FP64 throughout) and the subtraction gain (the taps' exact response W or the
@@ -743,6 +851,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-general", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed-requests", type=int, default=1024)
     ap.add_argument("--path", default="rounds", choices=["rounds", "persistent"],
                     help="per-round launches (one kernel per round and stream group) or one persistent launch")
     ap.add_argument("--precision-table", action="store_true", help="print the precision-variant table instead")
