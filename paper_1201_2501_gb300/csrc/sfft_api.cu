@@ -70,6 +70,8 @@ void free_plan(sfft_plan_s* pl) {
     cudaFree(pl->d_phase);
     cudaFree(pl->d_L);
     cudaFree(pl->d_nL);
+    cudaFree(pl->d_Lval);
+    cudaFree(pl->d_Lmag);
     for (int i = 0; i < sfft_plan_s::kMaxStreams; ++i) {
         if (pl->aux[i]) cudaStreamDestroy(pl->aux[i]);
         if (pl->ev_join[i]) cudaEventDestroy(pl->ev_join[i]);
@@ -230,6 +232,8 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         SFFT_ALLOC(pl->d_phase, pl->phase_stride * max_batch * sizeof(double));
         SFFT_ALLOC(pl->d_L, (size_t)maxB * max_batch * sizeof(uint32_t));
         SFFT_ALLOC(pl->d_nL, (size_t)max_batch * sizeof(uint32_t));
+        SFFT_ALLOC(pl->d_Lval, (size_t)maxB * max_batch * sizeof(double2));
+        SFFT_ALLOC(pl->d_Lmag, (size_t)maxB * max_batch * sizeof(double));
     }
 #undef SFFT_ALLOC
     auto fail = [&](cudaError_t err, const char* what) {
@@ -393,6 +397,8 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
             a.bins_stride = plan->bins_stride;
             a.phase_stride = plan->phase_stride;
             a.L = plan->d_L;
+            a.Lval = plan->d_Lval;
+            a.Lmag = plan->d_Lmag;
             a.nL = plan->d_nL;
             a.zidx = plan->d_zidx;
             a.zval = plan->d_zval;

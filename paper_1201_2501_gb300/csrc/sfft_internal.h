@@ -192,6 +192,8 @@ struct GenArgs {
     double* phase;         // [batch][npairs][B] phase(u_a conj(u_{a+beta})) / 2 pi
     size_t bins_stride, phase_stride;  // elements per request
     uint32_t* L;           // [batch][B] candidate frequencies
+    double2* Lval;         // [batch][B] EstimateValues' estimate of each bin's candidate
+    double* Lmag;          // [batch][B] its squared magnitude
     uint32_t* nL;          // [batch]
     uint32_t* zidx;        // [batch][zcap]
     double2* zval;
@@ -249,6 +251,8 @@ struct sfft_plan_s {
     double* d_phase = nullptr;
     uint32_t* d_L = nullptr;
     uint32_t* d_nL = nullptr;
+    double2* d_Lval = nullptr;
+    double* d_Lmag = nullptr;
     size_t bins_stride = 0, phase_stride = 0;
     std::vector<double> taps_host;  // every round's taps, FP64
     std::vector<double> wtab_host;  // every round's W(o), o = 0..n/2B
