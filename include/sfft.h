@@ -132,7 +132,8 @@ sfft_status sfft_plan_taps(sfft_plan plan, uint32_t t, double* h_taps, uint64_t 
 /* ---------------------------------------------------------------------------------------------- */
 /*
  * Run the sparse FFT on `batch` signals (batch <= max_batch) stored back to back in d_x
- * (batch x n complex values of the plan's precision).  Request r uses seed `seed`, request index r.
+ * (batch x n complex values of the plan's precision; device memory, or any memory the device can
+ * address, such as page-locked host memory, which is then read in place).  Request r uses seed `seed`, request index r.
  * Outputs, per request r, in caller-owned device arrays:
  *   d_idx[r*cap .. r*cap + count)  recovered frequencies, ascending (uint32)
  *   d_val[...]                    their values X_f as (re, im) doubles
@@ -145,10 +146,13 @@ sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64
                          uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag);
 
 /*
- * Same computation from host memory: copies h_x (batch x n) to a device staging buffer owned by the
- * plan, runs sfft_execute, copies the outputs back into host arrays and synchronises the stream.
- * h_x should be page-locked for full copy bandwidth.  The staging buffer is allocated on the first
- * call with a given batch (it is the one call besides plan creation that may allocate).
+ * Same computation from host memory, outputs copied back into host arrays; synchronises the stream.
+ * If h_x (batch x n) is page-locked host memory the device can address (cudaHostAlloc / registered;
+ * on Grace-Blackwell reached over NVLink-C2C), the kernels read the samples they need from it in
+ * place: a transform moves only its gathered samples across the link, not the whole signal.  Any
+ * other host memory is first copied whole to a device staging buffer owned by the plan.  Staging
+ * buffers are allocated on the first call with a given batch (the one call besides plan creation
+ * that may allocate).
  */
 sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, uint64_t seed, void* stream,
                               uint32_t* h_idx, double* h_val, uint32_t cap, uint32_t* h_count, int32_t* h_flag);

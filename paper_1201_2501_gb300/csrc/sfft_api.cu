@@ -176,6 +176,7 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     size_t part_elems = 0, max_smem = 0, gs_max = 0, fs_max = 0, ls_max = 0, es_max = 0;
     uint32_t maxB = 0;
     for (const ExactRound& r : pl->rounds) {
+        pl->samples += 2 * (uint64_t)r.T + 1 + r.shift[r.nshift - 1];
         const size_t e = (size_t)r.chunks * (1 + r.nshift) * r.B;
         if (e > part_elems) part_elems = e;
         if (r.smem > max_smem) max_smem = r.smem;
@@ -183,6 +184,7 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         if (r.fin_global && r.fin_bytes > pl->fin_stride) pl->fin_stride = (r.fin_bytes + 255) & ~size_t(255);
     }
     for (const GeneralRound& r : pl->grounds) {
+        pl->samples += (uint64_t)r.nhash * (2 * (uint64_t)r.T + 1);
         const size_t e = (size_t)r.ngroups * r.ctas * 2 * r.B;
         if (e > part_elems) part_elems = e;
         if ((size_t)r.nhash * r.B > pl->bins_stride) pl->bins_stride = (size_t)r.nhash * r.B;
@@ -566,7 +568,17 @@ sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, u
     if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t elem = plan->p.precision == SFFT_FP64 ? 16 : 8;
-    const size_t xbytes = (size_t)batch * plan->p.n * elem;
+    // Page-locked host signals are read in place by the kernels (over NVLink-C2C on Grace-Blackwell)
+    // when the gathered samples, at a 64-byte line each, weigh less than the whole signal: only they
+    // cross the link.  Otherwise (and for other host memory) the signals are staged whole.
+    const void* x_in_place = nullptr;
+    if (plan->samples * 64 < plan->p.n * elem) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, h_x) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer)
+            x_in_place = at.devicePointer;
+        cudaGetLastError();
+    }
+    const size_t xbytes = x_in_place ? 0 : (size_t)batch * plan->p.n * elem;
     if (plan->stage_bytes < xbytes || plan->out_cap < (size_t)batch * cap) {
         SFFT_CUDA(cudaStreamSynchronize(st), "sync before staging");
         cudaFree(plan->d_stage);
@@ -581,7 +593,7 @@ sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, u
         plan->d_out_flag = nullptr;
         plan->stage_bytes = 0;
         plan->out_cap = 0;
-        if (cudaMalloc(&plan->d_stage, xbytes) != cudaSuccess) return SFFT_ERR_OOM;
+        if (xbytes && cudaMalloc(&plan->d_stage, xbytes) != cudaSuccess) return SFFT_ERR_OOM;
         if (cudaMalloc((void**)&plan->d_out_idx, (size_t)batch * cap * 4) != cudaSuccess) return SFFT_ERR_OOM;
         if (cudaMalloc((void**)&plan->d_out_val, (size_t)batch * cap * 16) != cudaSuccess) return SFFT_ERR_OOM;
         if (cudaMalloc((void**)&plan->d_out_count, (size_t)batch * 4) != cudaSuccess) return SFFT_ERR_OOM;
@@ -589,9 +601,9 @@ sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, u
         plan->stage_bytes = xbytes;
         plan->out_cap = (size_t)batch * cap;
     }
-    SFFT_CUDA(cudaMemcpyAsync(plan->d_stage, h_x, xbytes, cudaMemcpyHostToDevice, st), "copy x to device");
-    sfft_status s = sfft_execute(plan, plan->d_stage, batch, seed, stream, plan->d_out_idx, plan->d_out_val, cap,
-                                 plan->d_out_count, plan->d_out_flag);
+    if (!x_in_place) SFFT_CUDA(cudaMemcpyAsync(plan->d_stage, h_x, xbytes, cudaMemcpyHostToDevice, st), "copy x to device");
+    sfft_status s = sfft_execute(plan, x_in_place ? x_in_place : plan->d_stage, batch, seed, stream, plan->d_out_idx,
+                                 plan->d_out_val, cap, plan->d_out_count, plan->d_out_flag);
     if (s != SFFT_OK) return s;
     SFFT_CUDA(cudaMemcpyAsync(h_count, plan->d_out_count, (size_t)batch * 4, cudaMemcpyDeviceToHost, st), "copy count");
     SFFT_CUDA(cudaMemcpyAsync(h_flag, plan->d_out_flag, (size_t)batch * 4, cudaMemcpyDeviceToHost, st), "copy flag");

@@ -279,6 +279,7 @@ struct sfft_plan_s {
     unsigned char* d_gest = nullptr;  // general mode: [max_batch][gest_stride]
     size_t gest_stride = 0;
     size_t dev_bytes = 0;          // device memory allocated at plan creation
+    uint64_t samples = 0;          // samples one transform gathers (all rounds, all hashings)
     // internal streams: a batch is split into groups whose rounds run on their own streams
     static constexpr int kMaxStreams = 8;
     uint32_t nstreams = 1;

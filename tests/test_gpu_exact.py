@@ -350,3 +350,25 @@ def test_edge_cases(sf):
         sf.sfft_execute(plan3, torch.zeros((2, 1 << 14), dtype=torch.complex64, device="cuda"), 1, 8)
     for p in (plan, plan2, plan3):
         p.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_execute_host_equals_device_path(sf, pinned):
+    """sfft_execute_host: page-locked signals are read in place, pageable ones staged whole; either way
+    the results are those of sfft_execute on device copies, bit for bit (exact and general plans)."""
+    for mode, (n, k) in ((0, (1 << 20, 32)), (1, (1 << 16, 16))):
+        batch = 6
+        p = sf.sfft_params_default(n, k, mode)
+        plan = sf.Plan(p, batch)
+        gen = workloads.exact_sparse if mode == 0 else workloads.general_noisy
+        xs = np.stack([gen(n, k, workloads.seed_for(12, i)).x for i in range(batch)])
+        hx = torch.as_tensor(xs)
+        if pinned:
+            hx = hx.pin_memory()
+        want = [t.cpu().numpy() for t in sf.sfft_execute(plan, hx.cuda(), 17, p.z_cap)]
+        got = [t.numpy() for t in sf.sfft_execute_host(plan, hx, 17, p.z_cap)]
+        assert np.array_equal(got[2], want[2]) and np.array_equal(got[3], want[3])
+        for r in range(batch):
+            c = int(got[2][r])
+            assert np.array_equal(got[0][r, :c], want[0][r, :c]) and np.array_equal(got[1][r, :c], want[1][r, :c])
+        plan.close()
