@@ -530,33 +530,57 @@ static uint32_t exact_decode(uint64_t n, uint32_t B, uint64_t sigma, uint64_t si
     return cnt;
 }
 
-/* zhat <- zhat + what, kept sorted by index; entries below drop_below are removed. */
+/* zhat <- zhat + what, kept sorted by index (a shared index adds the two values, zhat's first); entries
+ * below drop_below are removed.  Capacity reading (the paper's zhat is unbounded): when more than cap
+ * entries remain, the cap smallest indices are kept and *overflow is set. */
+typedef struct {
+    uint64_t i;
+    cplx v;
+} z_entry;
+static int cmp_z_entry(const void* a, const void* b) {
+    const uint64_t x = ((const z_entry*)a)->i, y = ((const z_entry*)b)->i;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
 static uint32_t z_merge(uint32_t nz, uint64_t* zi, cplx* zv, uint32_t nw, const uint64_t* wi, const cplx* wv,
                         double drop_below, uint32_t cap, int* overflow) {
-    /* insertion of each new entry into the sorted list */
+    z_entry* w = (z_entry*)malloc(sizeof(z_entry) * (nw ? nw : 1));
+    z_entry* t = (z_entry*)malloc(sizeof(z_entry) * (nz + nw ? nz + nw : 1));
     for (uint32_t e = 0; e < nw; ++e) {
-        uint32_t pos = 0;
-        while (pos < nz && zi[pos] < wi[e]) ++pos;
-        if (pos < nz && zi[pos] == wi[e]) {
-            zv[pos] += wv[e];
-            continue;
+        w[e].i = wi[e];
+        w[e].v = wv[e];
+    }
+    qsort(w, nw, sizeof(z_entry), cmp_z_entry); /* a round decodes each index at most once */
+    uint32_t a = 0, b = 0, m = 0;
+    while (a < nz || b < nw) {
+        if (b >= nw || (a < nz && zi[a] < w[b].i)) {
+            t[m].i = zi[a];
+            t[m].v = zv[a];
+            ++a;
+        } else if (a >= nz || w[b].i < zi[a]) {
+            t[m] = w[b];
+            ++b;
+        } else {
+            t[m].i = zi[a];
+            t[m].v = zv[a] + w[b].v;
+            ++a;
+            ++b;
         }
-        if (nz >= cap) {
-            *overflow = 1;
-            continue;
-        }
-        memmove(zi + pos + 1, zi + pos, sizeof(uint64_t) * (nz - pos));
-        memmove(zv + pos + 1, zv + pos, sizeof(cplx) * (nz - pos));
-        zi[pos] = wi[e];
-        zv[pos] = wv[e];
-        ++nz;
+        ++m;
     }
     uint32_t out = 0;
-    for (uint32_t e = 0; e < nz; ++e) {
-        if (cabs(zv[e]) < drop_below) continue;
-        zi[out] = zi[e];
-        zv[out] = zv[e];
+    for (uint32_t e = 0; e < m; ++e) {
+        if (cabs(t[e].v) < drop_below) continue;
+        if (out < cap) {
+            zi[out] = t[e].i;
+            zv[out] = t[e].v;
+        }
         ++out;
+    }
+    free(w);
+    free(t);
+    if (out > cap) {
+        *overflow = 1;
+        out = cap;
     }
     return out;
 }

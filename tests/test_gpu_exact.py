@@ -372,3 +372,47 @@ def test_execute_host_equals_device_path(sf, pinned):
             c = int(got[2][r])
             assert np.array_equal(got[0][r, :c], want[0][r, :c]) and np.array_equal(got[1][r, :c], want[1][r, :c])
         plan.close()
+
+
+def test_flags_and_limits_match_the_oracle(sf):
+    """More coefficients than k (the last round leaves bins above thr: NOT_CONVERGED), a zhat capacity
+    too small for the recovered coefficients (CAPACITY), and k at its n/4 maximum (B clamped to n/2):
+    the device path reports what the oracle reports, with the same entries."""
+    # 6k coefficients in a k-sparse plan
+    n, k = 1 << 14, 8
+    f = exact_fields(n, k, delta=1e-8)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f, 1), 3)
+    sigs = [workloads.exact_sparse(n, 6 * k, workloads.seed_for(13, i), dtype=np.complex128) for i in range(3)]
+    got = _run_gpu(sf, plan, [s.x for s in sigs], 8, f["z_cap"])
+    flags = []
+    for r, s in enumerate(sigs):
+        want = oracle.sfft_exact(P, s.x, 8, r)
+        assert np.array_equal(got[r][0], want[0].astype(np.int64))
+        want_flag = {0: sf.SFFT_OK, 1: sf.SFFT_ERR_NOT_CONVERGED, 2: sf.SFFT_ERR_CAPACITY}[want[2]]
+        assert got[r][2] == want_flag
+        flags.append(got[r][2])
+    assert sf.SFFT_ERR_NOT_CONVERGED in flags
+    plan.close()
+    # zhat capacity 8 for a 16-sparse signal
+    n, k = 1 << 14, 16
+    f = exact_fields(n, k, z_cap=8)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f, 0), 1)
+    s = workloads.exact_sparse(n, k, workloads.seed_for(13, 10))
+    got = _run_gpu(sf, plan, [s.x], 9, 64)[0]
+    want = oracle.sfft_exact(P, s.x.astype(np.complex128), 9, 0)
+    assert want[2] == 2 and got[2] == sf.SFFT_ERR_CAPACITY
+    assert np.array_equal(got[0], want[0].astype(np.int64))
+    plan.close()
+    # k = n / 4: B = pow2(4k) = n is clamped to n / 2
+    n, k = 1 << 10, 256
+    f = exact_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f, 1), 2)
+    assert plan.round_info(0)["B"] == n // 2
+    sigs = [workloads.exact_sparse(n, k, workloads.seed_for(13, 20 + i), dtype=np.complex128) for i in range(2)]
+    got = _run_gpu(sf, plan, [s.x for s in sigs], 10, f["z_cap"])
+    for r, s in enumerate(sigs):
+        _compare(got[r], oracle.sfft_exact(P, s.x, 10, r), 1e-9)
+    plan.close()

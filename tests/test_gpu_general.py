@@ -248,3 +248,31 @@ def test_sfft_general_full_size_sampled(sf):
     X1 = np.fft.fft(sigs[1].x.astype(np.complex128))
     assert _l2l2(X1, got[1][0], got[1][1], k) <= 1 + P.eps
     plan.close()
+
+
+def test_general_edge_cases(sf):
+    """A zero signal gives what the oracle gives (Algorithm 2 keeps the top k' estimates even when they
+    are all zero: here index 0 with value 0); k = 1 at small n matches the oracle's l2/l2 behaviour."""
+    n, k = 1 << 14, 8
+    f = general_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f), 1)
+    got = _run_gpu(sf, plan, [np.zeros(n, np.complex64)], 3, f["z_cap"])[0]
+    oi, ov, of = oracle.sfft_general(P, np.zeros(n, np.complex128), 3, 0)
+    assert np.array_equal(got[0], oi.astype(np.int64)) and got[2] == of == 0
+    assert np.all(got[1] == 0) and np.all(ov == 0)
+    plan.close()
+    n, k = 1 << 12, 1
+    f = general_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f), 2)
+    sigs = [workloads.general_noisy(n, k, workloads.seed_for(13, 30 + i)) for i in range(2)]
+    got = _run_gpu(sf, plan, [s.x for s in sigs], 4, f["z_cap"])
+    for r, s in enumerate(sigs):
+        x128 = s.x.astype(np.complex128)
+        X = np.fft.fft(x128)
+        oi, ov, of = oracle.sfft_general(P, x128, 4, r)
+        # the heavy coefficient is found on the device exactly when the oracle finds it
+        assert (s.support[0] in got[r][0].tolist()) == (s.support[0] in oi.astype(np.int64).tolist())
+        assert abs(_l2l2(X, got[r][0], got[r][1], k) / _l2l2(X, oi, ov, k) - 1.0) <= 0.05
+    plan.close()
