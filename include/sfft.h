@@ -83,6 +83,9 @@ typedef struct sfft_params {
                               decoded values: 0 -> the exact response W(o) of the truncated taps
                               (default); 1 -> the paper's closed form Ghat'(o) (Sec. 7: 1 on the pass
                               band, 0 beyond n/2B, a difference of Gaussian cdfs in between) */
+    uint32_t chunk_taps;   /* exact mode: window taps gathered per CTA (a power of two in [256, 8192];
+                              0 -> 2048); fewer taps spread one request over more CTAs (lower latency),
+                              more taps cut partial sums (batch throughput) */
 } sfft_params;
 
 /* Fill *p with the library defaults for (n, k, mode); precision SFFT_FP32. */
@@ -217,7 +220,8 @@ sfft_status sfft_plan_set_requests(sfft_plan plan, const sfft_request* h_reqs, u
  * width w ~ B log(1/delta) / alpha) as constants; this library also splits a batch over internal
  * streams.  sfft_autotune times candidate settings for base's (n, k, mode, delta, precision):
  * bins_per_k in {2, 4, 8} (exact) or {4, 8, 16} (general), alpha0 in {0.25, 0.5, 0.75}, streams in
- * {1, 2, 4, 8}, each on the same `batch` (<= 256) synthetic signals made on the device (exact: k
+ * {1, 2, 4, 8} and, in exact mode, chunk_taps (the gather's taps per CTA) in {1024, 2048}, each on the
+ * same `batch` (<= 256) synthetic signals made on the device (exact: k
  * unit-magnitude coefficients; general: k coefficients with |X| = 10^u, u uniform on [0, 1), plus
  * complex Gaussian time noise at snr_db), `reps` timed transforms after one warm-up (CUDA events).
  * Each candidate is scored against the planted coefficients; *best receives the fastest candidate
@@ -229,6 +233,7 @@ sfft_status sfft_plan_set_requests(sfft_plan plan, const sfft_request* h_reqs, u
 typedef struct sfft_tune_entry {
     double bins_per_k, alpha0;
     uint32_t streams;
+    uint32_t chunk_taps;     /* taps per CTA of the gather (exact mode) */
     int32_t status;          /* plan creation / run status of the candidate */
     double us_per_transform; /* device time per transform */
     uint32_t exact;          /* requests recovered exactly (exact mode) */

@@ -41,6 +41,8 @@ sfft_status validate(const sfft_params* p) {
     if (!(p->thr > 0) || !(p->tau_dec > 0 && p->tau_dec < 1) || !(p->iso_tol > 0)) return SFFT_ERR_INVALID_ARG;
     if (p->z_cap == 0 || p->z_cap > 4096) return SFFT_ERR_INVALID_ARG;
     if (p->gain > 1) return SFFT_ERR_INVALID_ARG;
+    if (p->chunk_taps != 0 && (!is_pow2(p->chunk_taps) || p->chunk_taps < 256 || p->chunk_taps > 8192))
+        return SFFT_ERR_INVALID_ARG;
     return SFFT_OK;
 }
 
@@ -99,6 +101,7 @@ ExactArgs base_args(const sfft_plan_s* pl, const ExactRound& r, uint32_t t) {
         a.shift64[l + 1] = r.shift[l];
     }
     a.chunks = r.chunks;
+    a.ctaps = r.ctaps;
     a.stage = r.stage;
     a.maxshift = (uint32_t)r.shift[r.nshift - 1];
     a.taps32 = pl->d_taps32 + r.taps_off;
@@ -629,7 +632,7 @@ sfft_status sfft_hash_to_bins(sfft_plan plan, uint32_t t, const void* d_x, uint6
     args.a_base = (uint32_t)a;
     args.a[0] = 0;
     args.maxshift = 0;
-    args.stage = kChunkTaps;
+    args.stage = r.ctaps;
     args.bins_only = 1;
     args.e_sigma = (uint32_t)sigma;
     args.e_b = (uint32_t)b;

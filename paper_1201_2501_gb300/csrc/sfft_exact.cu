@@ -204,8 +204,8 @@ __device__ void gather_fold(const ExactArgs& a, const void* xrow, uint32_t xmask
     const uint32_t tid = threadIdx.x;
     const C* __restrict__ x = reinterpret_cast<const C*>(xrow);
     const R* __restrict__ taps = taps_of<R>(a);
-    const int64_t t_lo = -a.T + (int64_t)c * kChunkTaps;
-    const int64_t t_hi = min(t_lo + (int64_t)kChunkTaps, a.T + 1);
+    const int64_t t_lo = -a.T + (int64_t)c * a.ctaps;
+    const int64_t t_hi = min(t_lo + (int64_t)a.ctaps, a.T + 1);
     const uint32_t ntap = (uint32_t)(t_hi - t_lo);
     const int32_t base = (int32_t)(t_lo - (int64_t)a.a_base - (int64_t)a.maxshift);  // sample held by stage[0]
     const uint32_t cnt = ntap + a.maxshift;

@@ -270,8 +270,9 @@ sfft_status build_exact_schedule(sfft_plan_s* pl) {
         const uint64_t maxshift = r.shift[r.nshift - 1];
         if (maxshift > 8192) return SFFT_ERR_K_RANGE;
         const uint64_t w = 2 * (uint64_t)r.T + 1;
-        r.chunks = (uint32_t)((w + kChunkTaps - 1) / kChunkTaps);
-        r.stage = (uint32_t)(kChunkTaps + maxshift);
+        r.ctaps = p.chunk_taps ? p.chunk_taps : (uint32_t)kChunkTaps;
+        r.chunks = (uint32_t)((w + r.ctaps - 1) / r.ctaps);
+        r.stage = (uint32_t)(r.ctaps + maxshift);
         r.taps_off = taps_off;
         r.wtab_off = wtab_off;
         const size_t gs = exact_gather_smem(r.stage, fp64) + (size_t)(1 + r.nshift) * (B > (uint64_t)kThreads ? B : kThreads) *
@@ -409,6 +410,8 @@ void sfft_params_default(sfft_params* p, uint64_t n, uint32_t k, uint32_t mode) 
     p->s = 0.25;
     p->est_gmin = 0.25;
     p->streams = 4;
+    p->gain = 0;
+    p->chunk_taps = 2048;
 }
 
 const char* sfft_status_str(sfft_status s) {

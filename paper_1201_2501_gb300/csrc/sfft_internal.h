@@ -38,7 +38,8 @@ struct ExactRound {
     uint32_t nshift = 0;      // ladder length L
     uint64_t shift[4] = {0, 0, 0, 0};
     uint32_t chunks = 0;      // CTAs per request in the gather phase
-    uint32_t stage = 0;       // samples staged per CTA: kChunkTaps + largest shift
+    uint32_t ctaps = 0;       // taps per CTA (sfft_params.chunk_taps)
+    uint32_t stage = 0;       // samples staged per CTA: ctaps + largest shift
     size_t taps_off = 0;      // offset of this round's taps in the tap arrays
     size_t wtab_off = 0;      // offset of this round's W(o), o = 0..n/2B, in the W table
     size_t smem = 0;          // dynamic shared memory of the round kernel
@@ -62,6 +63,7 @@ struct ExactArgs {
     uint32_t a[kMaxHash];      // a[0] = 0, a[l] = beta_l
     uint64_t shift64[kMaxHash];
     uint32_t chunks, stage, maxshift;
+    uint32_t ctaps;            // taps per CTA: chunk c gathers taps [-T + c ctaps, -T + (c + 1) ctaps)
     const float* taps32;
     const double* taps64;
     const double* wtab;

@@ -69,6 +69,7 @@ ParamKey make_key(const sfft_params& p, sfft_params* canon) {
     q.est_gmin = p.est_gmin;
     q.streams = p.streams;
     q.gain = p.gain;
+    q.chunk_taps = p.chunk_taps;
     ParamKey k;
     std::memcpy(k.bytes, &q, sizeof q);
     if (canon) *canon = q;

@@ -85,6 +85,7 @@ extern "C" sfft_status sfft_hash_to_bins_static(uint64_t n, uint32_t B, int64_t 
     args.a_base = (uint32_t)a;
     args.chunks = (uint32_t)chunks;
     args.stage = kChunkTaps;
+    args.ctaps = kChunkTaps;
     args.maxshift = 0;
     args.taps32 = d_taps;
     args.wtab = d_wtab;

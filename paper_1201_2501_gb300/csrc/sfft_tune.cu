@@ -184,6 +184,8 @@ sfft_status sfft_autotune(const sfft_params* base, uint32_t batch, double snr_db
     std::vector<double> cs = general ? std::vector<double>{4.0, 8.0, 16.0} : std::vector<double>{2.0, 4.0, 8.0};
     std::vector<double> as = {0.25, 0.5, 0.75};
     std::vector<uint32_t> ss = {1, 2, 4, 8};
+    // taps per CTA (the gather's block shape; exact mode only: the general path keeps 2048)
+    std::vector<uint32_t> ts = general ? std::vector<uint32_t>{base->chunk_taps} : std::vector<uint32_t>{1024, 2048};
     struct Cand {
         sfft_params p;
         sfft_tune_entry r;
@@ -195,15 +197,18 @@ sfft_status sfft_autotune(const sfft_params* base, uint32_t batch, double snr_db
     }
     for (double c : cs)
         for (double a : as)
-            for (uint32_t s : ss) {
-                sfft_params p = *base;
-                p.bins_per_k = c;
-                p.alpha0 = a;
-                p.streams = s;
-                if (p.bins_per_k == base->bins_per_k && p.alpha0 == base->alpha0 && p.streams == base->streams)
-                    continue;
-                cands.push_back(Cand{p, {}});
-            }
+            for (uint32_t s : ss)
+                for (uint32_t ct : ts) {
+                    sfft_params p = *base;
+                    p.bins_per_k = c;
+                    p.alpha0 = a;
+                    p.streams = s;
+                    p.chunk_taps = ct;
+                    if (p.bins_per_k == base->bins_per_k && p.alpha0 == base->alpha0 && p.streams == base->streams &&
+                        p.chunk_taps == base->chunk_taps)
+                        continue;
+                    cands.push_back(Cand{p, {}});
+                }
     cudaStream_t stream = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
@@ -219,6 +224,7 @@ sfft_status sfft_autotune(const sfft_params* base, uint32_t batch, double snr_db
         c.r.bins_per_k = c.p.bins_per_k;
         c.r.alpha0 = c.p.alpha0;
         c.r.streams = c.p.streams;
+        c.r.chunk_taps = c.p.chunk_taps;
         c.r.status = SFFT_OK;
         sfft_plan plan = nullptr;
         sfft_status ps = sfft_plan_create(&c.p, batch, &plan);

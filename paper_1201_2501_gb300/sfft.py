@@ -60,6 +60,7 @@ class SfftParams(ctypes.Structure):
         ("est_gmin", ctypes.c_double),
         ("streams", ctypes.c_uint32),
         ("gain", ctypes.c_uint32),
+        ("chunk_taps", ctypes.c_uint32),
     ]
 
 
@@ -105,7 +106,7 @@ class SfftTuneEntry(ctypes.Structure):
     """Mirror of ``sfft_tune_entry``."""
 
     _fields_ = [("bins_per_k", ctypes.c_double), ("alpha0", ctypes.c_double), ("streams", ctypes.c_uint32),
-                ("status", ctypes.c_int32), ("us_per_transform", ctypes.c_double), ("exact", ctypes.c_uint32),
+                ("chunk_taps", ctypes.c_uint32), ("status", ctypes.c_int32), ("us_per_transform", ctypes.c_double), ("exact", ctypes.c_uint32),
                 ("chosen", ctypes.c_uint32), ("rel_err", ctypes.c_double)]
 
 
@@ -357,11 +358,11 @@ def sfft_execute_requests(plan: Plan, xs, seeds, ids, cap: int, outputs=None, st
 def sfft_autotune(base: SfftParams, batch: int = 16, snr_db: float = 20.0, seed: int = 1, reps: int = 5):
     """Runs the library's autotuner for ``base``; returns (best SfftParams, list of report dicts)."""
     best = SfftParams()
-    rep = (SfftTuneEntry * 64)()
+    rep = (SfftTuneEntry * 128)()
     nrep = ctypes.c_uint32()
-    _check(lib().sfft_autotune(ctypes.byref(base), batch, snr_db, seed, reps, ctypes.byref(best), rep, 64,
+    _check(lib().sfft_autotune(ctypes.byref(base), batch, snr_db, seed, reps, ctypes.byref(best), rep, 128,
                                ctypes.byref(nrep)), "sfft_autotune")
-    out = [{f: getattr(rep[i], f) for f, _ in SfftTuneEntry._fields_} for i in range(min(nrep.value, 64))]
+    out = [{f: getattr(rep[i], f) for f, _ in SfftTuneEntry._fields_} for i in range(min(nrep.value, 128))]
     return best, out
 
 
