@@ -675,13 +675,13 @@ def context_measurements(sfft, plan, x, cap, stream, args):
         out["general_case"] = general_measurement(sfft, stream, args)
     if not args.no_serving:
         out["serving"] = serving_measurement(sfft, args)
-    if not args.no_mixed:
+    if args.mixed:
         out["mixed_batch"] = mixed_batch_measurement(sfft, args)
     return out
 
 
-SERVE_EXPS = (16, 18, 20, 22)
-SERVE_K_EXACT = (8, 32, 128, 512)
+SERVE_EXPS = (16, 18, 20, 22, 24, 26)
+SERVE_K_EXACT = (8, 32, 128, 512, 1024)
 SERVE_K_GENERAL = (8, 32, 128)
 
 
@@ -792,8 +792,9 @@ def serving_measurement(sfft, args):
     del sigs
     torch.cuda.empty_cache()
     return {
-        "workload": "n = 2^e, e uniform on {16,18,20,22}; half exactly k-sparse (k uniform on {8,32,128,512}), "
-                    "half k heavy + complex Gaussian time noise at SNR 20 dB (k uniform on {8,32,128}); "
+        "workload": "n = 2^e, e uniform on {16,18,20,22,24,26}; k uniform on {8,32,128,512,1024} for the exactly "
+                    "k-sparse half, on {8,32,128} for the half with k heavy coefficients + complex Gaussian time "
+                    "noise at SNR 20 dB; "
                     f"{len(types)} parameter sets x {per_type} resident signals; Poisson arrivals; "
                     "latency = submission to completion on the host clock",
         "requests": len(seq),
@@ -1015,7 +1016,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--workload", default="exact", choices=["exact", "general"],
                     help="exact: the n=2^22, k=64 benchmark; general: the noisy n=2^22, k=256 case as the timed step")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed", action="store_true", help="also time the uneven mixed batch (1024 requests)")
     ap.add_argument("--mixed-requests", type=int, default=1024)
     ap.add_argument("--path", default="rounds", choices=["rounds", "persistent"],
                     help="per-round launches (one kernel per round and stream group) or one persistent launch")

@@ -181,8 +181,9 @@ typedef struct sfft_request {
 
 /*
  * sfft_execute over `batch` independent requests (batch <= max_batch) whose signals lie anywhere in
- * device memory.  The table h_reqs (host memory) is copied into the plan before the call returns, so
- * it may be reused at once; the outputs are laid out as for sfft_execute (slot r = h_reqs[r]).
+ * device memory.  The table h_reqs (host memory) is copied into page-locked memory owned by the plan
+ * before the call returns, so it may be reused or freed at once; the outputs are laid out as for
+ * sfft_execute (slot r = h_reqs[r]).
  * A plan serves one stream at a time: the table copy and the kernels go to `stream`.
  * Errors: INVALID_ARG (null pointer, batch out of range, cap == 0, a null or misaligned d_x, a period
  * that is not a power of two dividing n), CUDA.

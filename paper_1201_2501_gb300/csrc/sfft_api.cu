@@ -60,6 +60,10 @@ void free_plan(sfft_plan_s* pl) {
     cudaFree(pl->d_ubins);
     cudaFree(pl->d_aux);
     cudaFree(pl->d_reqs);
+    for (int i = 0; i < 2; ++i) {
+        cudaFreeHost(pl->h_reqs[i]);
+        if (pl->ev_reqs[i]) cudaEventDestroy(pl->ev_reqs[i]);
+    }
     cudaFree(pl->d_fin);
     cudaFree(pl->d_gfin);
     cudaFree(pl->d_gest);
@@ -72,8 +76,6 @@ void free_plan(sfft_plan_s* pl) {
     cudaFree(pl->d_phase);
     cudaFree(pl->d_L);
     cudaFree(pl->d_nL);
-    cudaFree(pl->d_Lval);
-    cudaFree(pl->d_Lmag);
     for (int i = 0; i < sfft_plan_s::kMaxStreams; ++i) {
         if (pl->aux[i]) cudaStreamDestroy(pl->aux[i]);
         if (pl->ev_join[i]) cudaEventDestroy(pl->ev_join[i]);
@@ -229,6 +231,15 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     SFFT_ALLOC(pl->d_ubins, (size_t)maxB * kMaxHash * sizeof(double2));
     SFFT_ALLOC(pl->d_aux, 64 * sizeof(uint32_t));
     SFFT_ALLOC(pl->d_reqs, (size_t)max_batch * sizeof(ReqDesc));
+    for (int i = 0; i < 2; ++i) {
+        if (cudaMallocHost((void**)&pl->h_reqs[i], (size_t)max_batch * sizeof(ReqDesc)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->ev_reqs[i], cudaEventDisableTiming) != cudaSuccess) {
+            set_last_error("page-locked request table");
+            cudaGetLastError();
+            free_plan(pl);
+            return SFFT_ERR_OOM;
+        }
+    }
     if (pl->fin_stride) SFFT_ALLOC(pl->d_fin, pl->fin_stride * max_batch);
     if (pl->gfin_stride) SFFT_ALLOC(pl->d_gfin, pl->gfin_stride * pl->gfin_groups * max_batch);
     if (pl->gest_stride) SFFT_ALLOC(pl->d_gest, pl->gest_stride * max_batch);
@@ -237,8 +248,6 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         SFFT_ALLOC(pl->d_phase, pl->phase_stride * max_batch * sizeof(double));
         SFFT_ALLOC(pl->d_L, (size_t)maxB * max_batch * sizeof(uint32_t));
         SFFT_ALLOC(pl->d_nL, (size_t)max_batch * sizeof(uint32_t));
-        SFFT_ALLOC(pl->d_Lval, (size_t)maxB * max_batch * sizeof(double2));
-        SFFT_ALLOC(pl->d_Lmag, (size_t)maxB * max_batch * sizeof(double));
     }
 #undef SFFT_ALLOC
     auto fail = [&](cudaError_t err, const char* what) {
@@ -402,8 +411,6 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
             a.bins_stride = plan->bins_stride;
             a.phase_stride = plan->phase_stride;
             a.L = plan->d_L;
-            a.Lval = plan->d_Lval;
-            a.Lmag = plan->d_Lmag;
             a.nL = plan->d_nL;
             a.zidx = plan->d_zidx;
             a.zval = plan->d_zval;
@@ -494,10 +501,18 @@ sfft_status sfft_plan_set_requests(sfft_plan plan, const sfft_request* h_reqs, u
         const uint32_t per = h_reqs[r].period;
         if (per != 0 && (!is_pow2(per) || per > plan->p.n)) return SFFT_ERR_INVALID_ARG;
     }
-    // a pageable source is staged by the driver before the call returns, so h_reqs may be reused at once
-    SFFT_CUDA(cudaMemcpyAsync(plan->d_reqs, h_reqs, (size_t)batch * sizeof(ReqDesc), cudaMemcpyHostToDevice,
-                              (cudaStream_t)stream),
+    // The table goes through one of the plan's two page-locked buffers (its previous copy has completed):
+    // an asynchronous copy from the caller's array could run after the caller has freed it (on
+    // Grace-Blackwell the GPU reads pageable memory directly, without staging it at the call).
+    const int cur = plan->reqs_cur;
+    plan->reqs_cur ^= 1;
+    SFFT_CUDA(cudaEventSynchronize(plan->ev_reqs[cur]), "request table buffer");
+    std::memcpy(plan->h_reqs[cur], h_reqs, (size_t)batch * sizeof(ReqDesc));
+    cudaStream_t st = (cudaStream_t)stream;
+    SFFT_CUDA(cudaMemcpyAsync(plan->d_reqs, plan->h_reqs[cur], (size_t)batch * sizeof(ReqDesc), cudaMemcpyHostToDevice,
+                              st),
               "copy request table");
+    SFFT_CUDA(cudaEventRecord(plan->ev_reqs[cur], st), "request table event");
     return SFFT_OK;
 }
 

@@ -276,11 +276,10 @@ constexpr int kVoteGuard = 16;  // extra fraction bits of the fixed-point bounda
 // Boundaries of the vote arc (c - s/2, c + s/2) in units of 1/M, as 64-bit fixed point with
 // kVoteGuard fraction bits: c M 2^G is one exact scaling of c (truncated to an integer, an error
 // below 2^-G units), so only one double operation is spent per (bin, round).
-// scale = 2^(logM + kVoteGuard), the same double every time (computed once by the caller)
-__device__ __forceinline__ VoteBounds vote_bounds_scaled(double c, double scale, int64_t hw_fix, uint32_t logM) {
+__device__ __forceinline__ VoteBounds vote_bounds(double c, int64_t hw_fix, uint32_t logM) {
     VoteBounds v;
     const int64_t one = int64_t(1) << kVoteGuard, frac_mask = one - 1;
-    const int64_t xfix = (int64_t)(c * scale);
+    const int64_t xfix = (int64_t)(c * ldexp(1.0, (int)logM + kVoteGuard));
     const int64_t blf = xfix - hw_fix, bhf = xfix + hw_fix;
     const uint64_t mask = (uint64_t(1) << logM) - 1;
     const int64_t ilo = (blf >> kVoteGuard) + 1;                  // smallest integer > bl
@@ -294,9 +293,6 @@ __device__ __forceinline__ VoteBounds vote_bounds_scaled(double c, double scale,
                           : (fh > 3 * (one / 4) ? ((uint64_t)((bhf >> kVoteGuard) + 1) & mask) : ~0ull);
     v.c = c;
     return v;
-}
-__device__ __forceinline__ VoteBounds vote_bounds(double c, int64_t hw_fix, uint32_t logM) {
-    return vote_bounds_scaled(c, ldexp(1.0, (int)logM + kVoteGuard), hw_fix, logM);
 }
 // half width s M / 2 of the vote arc in the same fixed point
 __device__ __forceinline__ int64_t vote_halfwidth(double s, uint32_t logM) {
@@ -379,88 +375,25 @@ __device__ uint32_t sort_unique_u32(uint32_t* key, uint32_t m, uint32_t* tmp, ui
     return total;
 }
 
-// One hashing's estimate of X_i (Algorithm 2, EstimateValues): e = u_{h(i)} w^{-a sigma i} / W(-o(i)),
-// or nothing when the window gain W(-o(i)) < gmin.
-template <typename BinFn>
-__device__ __forceinline__ bool est_term(uint32_t i, uint32_t q, uint32_t sq, uint32_t bq, uint32_t aq, BinFn bin,
-                                         uint32_t n, uint32_t nmask, uint32_t logNp, const double* wtab, double gmin,
-                                         double* x, double* y) {
-    const uint32_t p = (sq * (i - bq)) & nmask;
-    uint32_t j;
-    const int32_t o = gen_offset(p, n, nmask, logNp, &j);
-    const double gain = wtab[o < 0 ? -o : o];
-    if (!(gain >= gmin)) return false;
-    const uint32_t e = (aq * sq * i) & nmask;
-    const double2 w = root_pow<double>(e, nmask);
-    const double2 v = mul_conj_rn(bin(q, j), w);
-    *x = __ddiv_rn(v.x, gain);
-    *y = __ddiv_rn(v.y, gain);
-    return true;
-}
-// insertion of (x, y) into the sorted prefixes re[0..m), im[0..m)
-__device__ __forceinline__ void median_insert(double* re, double* im, uint32_t& m, double x, double y) {
-    uint32_t pr = m, pi = m;
-    while (pr > 0 && re[pr - 1] > x) {
-        re[pr] = re[pr - 1];
-        --pr;
-    }
-    re[pr] = x;
-    while (pi > 0 && im[pi - 1] > y) {
-        im[pi] = im[pi - 1];
-        --pi;
-    }
-    im[pi] = y;
-    ++m;
-}
-// lower medians of the inserted terms; 0 when there are none
-__device__ __forceinline__ double2 median_of(const double* re, const double* im, uint32_t m) {
-    if (m == 0) return make_double2(0.0, 0.0);
-    return make_double2(re[(m - 1) / 2], im[(m - 1) / 2]);
-}
-
-// w_i = median_q Re e_q + i median_q Im e_q over the hashings q whose window gain at i is >= est_gmin,
-// e_q = u^{(q)}_{h_q(i)} w^{-a_q sigma_q i} / W(-o_q(i)); lower median; 0 when no hashing qualifies.
-template <typename BinFn>
-__device__ double2 estimate_one(uint32_t i, uint32_t nrep, const uint64_t* sig, const uint64_t* bb, const uint64_t* aa,
-                                BinFn bin, uint32_t n, uint32_t nmask, uint32_t logNp, const double* wtab, double gmin) {
-    double re[kMaxRest], im[kMaxRest];
-    uint32_t m = 0;
-    for (uint32_t q = 0; q < nrep; ++q) {
-        double x, y;
-        if (est_term(i, q, (uint32_t)sig[q], (uint32_t)bb[q], (uint32_t)aa[q], bin, n, nmask, logNp, wtab, gmin, &x, &y))
-            median_insert(re, im, m, x, y);
-    }
-    return median_of(re, im, m);
-}
-
-// LocateSignal with t lanes per bin: lane q holds sub-region q of the bin's current region.  At each
-// level the lane counts the votes of its sub-region over the R_loc rounds (the same integers as
-// locate_bin: e_q = e_0 + q (beta w / t) mod M), and the bin's lanes agree through shuffles of width t
-// on bottom (no sub-region with a majority) or on the first window of four consecutive sub-regions
-// with the most votes.  Every lane of a warp takes part in every shuffle (bins already at bottom and
-// lanes past B compute on clamped data and discard it).  A request spreads over ceil(B t / kThreads)
-// CTAs.  The candidate of bin j (pi^{-1} of the integer nearest the centre of its last region, or ~0
-// for bottom) goes to L[s B + j]; EstimateValues sorts and de-duplicates them.
+// LocateSignal for one bin per thread: the bins of a request are independent until L is formed, so
+// a request spreads over ceil(B / kThreads) CTAs.  The candidate of bin j (pi^{-1} of the integer
+// nearest the centre of its last region, or ~0 for bottom) goes to L[s B + j]; EstimateValues sorts
+// and de-duplicates them.
 __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
     __shared__ uint64_t s_beta[kMaxRloc];
     const uint32_t s = a.req_base + blockIdx.y, tid = threadIdx.x;
-    const uint32_t t = a.t;  // 8, 16 or 32: divides the warp
-    const uint32_t q = tid & (t - 1);
-    const uint32_t j = blockIdx.x * (kThreads / t) + tid / t;
+    const uint32_t j = blockIdx.x * kThreads + tid;
     const uint32_t B = a.B;
-    const uint32_t jc = j < B ? j : B - 1;  // clamped for loads
     const ReqView rq = gen_req(a, s);
     uint32_t sigma, b;
     locate_sigma_b(rq.seed, rq.id, a.round, a.nmask, &sigma, &b);
     const uint64_t n = a.n, Np = n >> a.logB;
     const uint32_t logM = (uint32_t)(63 - __clzll((long long)n)) + kFracBits;
-    const uint64_t M = uint64_t(1) << logM, mask = M - 1;
-    const double scale = ldexp(1.0, (int)logM + kVoteGuard);
     const int64_t hw_fix = vote_halfwidth(a.s, logM);
     const uint64_t sb_fp = ((uint64_t)((sigma * b) & a.nmask)) << kFracBits;
     // the region of bin j starts centred on the bin: [j n/B - n/2B, + n/B)
-    uint64_t l_fp = ((((uint64_t)jc * Np) + n - Np / 2) & (n - 1)) << kFracBits;
-    bool valid = j < B;
+    uint64_t l_fp = ((((uint64_t)j * Np) + n - Np / 2) & (n - 1)) << kFracBits;
+    uint8_t valid = j < B ? 1 : 0;
     const double* phase = a.phase + (size_t)s * a.phase_stride;
     for (uint32_t D = 0; D < a.dmax; ++D) {
         __syncthreads();
@@ -471,79 +404,27 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
             s_beta[tid] = be;
         }
         __syncthreads();
+        if (!valid) continue;
         const uint64_t w_fp = (Np << kFracBits) >> ((uint64_t)D * a.logtp);
-        const uint64_t half_step = w_fp / (2 * (uint64_t)t), step = w_fp / t;
         const double* ph = phase + (size_t)D * a.R_loc * B;
-        uint32_t v = 0;
-        for (uint32_t r = 0; r < a.R_loc; ++r) {
-            const VoteBounds vb = vote_bounds_scaled(ph[(size_t)r * B + jc], scale, hw_fix, logM);
-            const uint64_t e0 = (s_beta[r] * ((l_fp + half_step + sb_fp) & mask)) & mask;
-            const uint64_t de = (s_beta[r] * step) & mask;
-            if (vote_hit(vb, (e0 + (uint64_t)q * de) & mask, M, a.s)) ++v;
-        }
-        // a majority anywhere in the bin's region?
-        uint32_t maj = 2u * v > a.R_loc ? 1u : 0u;
-        for (uint32_t o = t >> 1; o > 0; o >>= 1) maj |= __shfl_xor_sync(0xFFFFFFFFu, maj, (int)o, (int)t);
-        // window of four sub-regions starting at q: most votes, first such window on ties
-        const uint32_t v1 = __shfl_down_sync(0xFFFFFFFFu, v, 1, (int)t);
-        const uint32_t v2 = __shfl_down_sync(0xFFFFFFFFu, v, 2, (int)t);
-        const uint32_t v3 = __shfl_down_sync(0xFFFFFFFFu, v, 3, (int)t);
-        uint32_t key = q + 4 <= t ? ((v + v1 + v2 + v3) << 6) | (63u - q) : 0u;
-        for (uint32_t o = t >> 1; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xFFFFFFFFu, key, (int)o, (int)t));
-        if (valid) {
-            if (!maj)
-                valid = false;
-            else
-                l_fp = (l_fp + (uint64_t)(63u - (key & 63u)) * step) & mask;
-        }
+        locate_bin(a.t, a.R_loc, s_beta, [&](uint32_t r) { return ph[(size_t)r * B + j]; }, sb_fp, w_fp, logM, a.s,
+                   hw_fix, l_fp, valid, nullptr);
     }
+    if (j >= B) return;
     uint32_t cand = 0xFFFFFFFFu;
     if (valid) {
         const uint64_t wlast = (Np << kFracBits) >> ((uint64_t)a.dmax * a.logtp);
         const uint32_t tau = (uint32_t)(((l_fp + wlast / 2 + (1ull << (kFracBits - 1))) >> kFracBits) & (n - 1));
         cand = ((inverse_odd(sigma) & a.nmask) * tau + b) & a.nmask;
     }
-    // EstimateValues' estimate of the candidate (Algorithm 2): the bin's lanes share the R_est
-    // hashings (lane q takes hashings q and q + t), lane 0 inserts the terms in hashing order and takes
-    // the medians (the arithmetic of estimate_one).  Bottom bins compute on a stand-in and discard it.
-    const uint32_t ic = valid ? cand : 0u;
-    const double2* ebins = a.bins + (size_t)s * a.bins_stride + (size_t)2 * a.npairs * B;
-    const uint32_t logNp = (uint32_t)(63 - __clzll((long long)n)) - a.logB;
-    double tx[2] = {0.0, 0.0}, ty[2] = {0.0, 0.0};
-    uint32_t tok[2] = {0u, 0u};
-    for (uint32_t h = 0; h < 2; ++h) {
-        const uint32_t qq = q + h * t;
-        if (qq >= a.R_est) continue;
-        const Words4 w = draw(rq.seed, rq.id, a.round, qq, kKindEstimate);
-        tok[h] = est_term(ic, qq, (w.w[0] & a.nmask) | 1u, w.w[1] & a.nmask, w.w[2] & a.nmask,
-                          [&](uint32_t r, uint32_t jb) { return ebins[(size_t)r * B + jb]; }, (uint32_t)n, a.nmask,
-                          logNp, a.wtab, a.est_gmin, &tx[h], &ty[h])
-                     ? 1u
-                     : 0u;
-    }
-    double re[kMaxRest], im[kMaxRest];
-    uint32_t m = 0;
-    for (uint32_t qq = 0; qq < a.R_est; ++qq) {  // uniform over the warp: every lane shuffles
-        const uint32_t src = qq & (t - 1), h = qq / t;
-        const double x = __shfl_sync(0xFFFFFFFFu, h ? tx[1] : tx[0], (int)src, (int)t);
-        const double y = __shfl_sync(0xFFFFFFFFu, h ? ty[1] : ty[0], (int)src, (int)t);
-        const uint32_t ok = __shfl_sync(0xFFFFFFFFu, h ? tok[1] : tok[0], (int)src, (int)t);
-        if (q == 0 && ok) median_insert(re, im, m, x, y);
-    }
-    if (j >= B || q != 0) return;
     a.L[(size_t)s * B + j] = cand;
-    if (valid) {
-        const double2 wv = median_of(re, im, m);
-        a.Lval[(size_t)s * B + j] = wv;
-        a.Lmag[(size_t)s * B + j] = __dadd_rn(__dmul_rn(wv.x, wv.x), __dmul_rn(wv.y, wv.y));
-    }
 }
 
 // ------------------------------------------------------------------------------------------------
 // 4. EstimateValues, top k', zhat += w_J
 // ------------------------------------------------------------------------------------------------
 struct EstLayout {
-    size_t w, mag, perm, topi, topv, out_idx, out_val, keep, scan, k64, Ls, total;
+    size_t w, mag, perm, topi, topv, out_idx, out_val, keep, scan, draws, Lk, Lt, total;
     uint32_t P;
 };
 __host__ __device__ inline EstLayout est_layout(uint32_t B, uint32_t kprime, uint32_t zcap) {
@@ -561,12 +442,50 @@ __host__ __device__ inline EstLayout est_layout(uint32_t B, uint32_t kprime, uin
     L.out_val = gtake(&off, (size_t)(zcap + kprime) * 16);
     L.keep = gtake(&off, (size_t)(zcap + kprime > B ? zcap + kprime : B) * 4);
     L.scan = gtake(&off, (size_t)(kThreads + 8) * 4);
-    L.k64 = gtake(&off, (size_t)P * 8);
-    L.Ls = gtake(&off, (size_t)B * 4);
+    L.draws = gtake(&off, (size_t)kMaxRest * 3 * 8);
+    L.Lk = gtake(&off, (size_t)B * 4);
+    L.Lt = gtake(&off, (size_t)B * 4);
     L.total = off;
     return L;
 }
 size_t general_estimate_smem(uint32_t B, uint32_t kprime, uint32_t zcap) { return est_layout(B, kprime, zcap).total; }
+
+// w_i = median_q Re e_q + i median_q Im e_q over the hashings q whose window gain at i is >= est_gmin,
+// e_q = u^{(q)}_{h_q(i)} w^{-a_q sigma_q i} / W(-o_q(i)); lower median; 0 when no hashing qualifies.
+template <typename BinFn>
+__device__ double2 estimate_one(uint32_t i, uint32_t nrep, const uint64_t* sig, const uint64_t* bb, const uint64_t* aa,
+                                BinFn bin, uint32_t n, uint32_t nmask, uint32_t logNp, const double* wtab, double gmin) {
+    double re[kMaxRest], im[kMaxRest];
+    uint32_t m = 0;
+    for (uint32_t q = 0; q < nrep; ++q) {
+        const uint32_t sq = (uint32_t)sig[q];
+        const uint32_t p = (sq * (i - (uint32_t)bb[q])) & nmask;
+        uint32_t j;
+        const int32_t o = gen_offset(p, n, nmask, logNp, &j);
+        const double gain = wtab[o < 0 ? -o : o];
+        if (!(gain >= gmin)) continue;
+        const uint32_t e = ((uint32_t)aa[q] * sq * i) & nmask;
+        const double2 w = root_pow<double>(e, nmask);
+        const double2 u = bin(q, j);
+        const double2 v = mul_conj_rn(u, w);
+        const double x = __ddiv_rn(v.x, gain), y = __ddiv_rn(v.y, gain);
+        // insertion into the sorted prefixes
+        uint32_t pr = m, pi = m;
+        while (pr > 0 && re[pr - 1] > x) {
+            re[pr] = re[pr - 1];
+            --pr;
+        }
+        re[pr] = x;
+        while (pi > 0 && im[pi - 1] > y) {
+            im[pi] = im[pi - 1];
+            --pi;
+        }
+        im[pi] = y;
+        ++m;
+    }
+    if (m == 0) return make_double2(0.0, 0.0);
+    return make_double2(re[(m - 1) / 2], im[(m - 1) / 2]);
+}
 
 // (mag2 descending, index ascending) order of candidates via a bitonic sort of a permutation
 __device__ void sort_by_magnitude(const double* mag, const uint32_t* idx, uint32_t m, uint32_t P, uint32_t* perm) {
@@ -597,25 +516,6 @@ __device__ void sort_by_magnitude(const double* mag, const uint32_t* idx, uint32
     }
 }
 
-// ascending bitonic sort of P (a power of two) 64-bit keys in shared or global memory, one CTA
-__device__ void bitonic_sort_u64(uint64_t* k, uint32_t P) {
-    for (uint32_t kk = 2; kk <= P; kk <<= 1) {
-        for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P; i += kThreads) {
-                const uint32_t ixj = i ^ jj;
-                if (ixj > i) {
-                    const uint64_t x = k[i], y = k[ixj];
-                    if ((i & kk) == 0 ? x > y : x < y) {
-                        k[i] = y;
-                        k[ixj] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
 __global__ void __launch_bounds__(kThreads) k_gen_estimate(const GenArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t s = a.req_base + blockIdx.x, tid = threadIdx.x, B = a.B;
@@ -631,35 +531,38 @@ __global__ void __launch_bounds__(kThreads) k_gen_estimate(const GenArgs a) {
     double2* out_val = reinterpret_cast<double2*>(eb + Ly.out_val);
     uint32_t* keep = reinterpret_cast<uint32_t*>(eb + Ly.keep);
     uint32_t* scan = reinterpret_cast<uint32_t*>(eb + Ly.scan);
-    // L: the candidates of the bins that LocateSignal did not reject, sorted and de-duplicated, with
-    // the estimates the locate kernel made (a candidate found by several bins has one estimate)
-    uint64_t* k64 = reinterpret_cast<uint64_t*>(eb + Ly.k64);
-    uint32_t* L = reinterpret_cast<uint32_t*>(eb + Ly.Ls);
+    uint64_t* dr = reinterpret_cast<uint64_t*>(eb + Ly.draws);  // sigma, b, a per hashing
+    const ReqView rq = gen_req(a, s);
+    if (tid < a.R_est) {
+        const Words4 w = draw(rq.seed, rq.id, a.round, tid, kKindEstimate);
+        dr[tid] = (w.w[0] & a.nmask) | 1u;
+        dr[kMaxRest + tid] = w.w[1] & a.nmask;
+        dr[2 * kMaxRest + tid] = w.w[2] & a.nmask;
+    }
+    __syncthreads();
+    // L: the candidates of the bins that LocateSignal did not reject, sorted and de-duplicated
+    uint32_t* Lk = reinterpret_cast<uint32_t*>(eb + Ly.Lk);
+    uint32_t* Lt = reinterpret_cast<uint32_t*>(eb + Ly.Lt);
     __shared__ uint32_t s_m;
     if (tid == 0) s_m = 0;
     __syncthreads();
     for (uint32_t j = tid; j < B; j += kThreads) {
         const uint32_t c = a.L[(size_t)s * B + j];
-        if (c != 0xFFFFFFFFu) k64[atomicAdd(&s_m, 1u)] = ((uint64_t)c << 32) | j;
+        if (c != 0xFFFFFFFFu) Lk[atomicAdd(&s_m, 1u)] = c;
     }
     __syncthreads();
-    const uint32_t m = s_m;
-    for (uint32_t p = m + tid; p < Ly.P; p += kThreads) k64[p] = ~0ull;
-    __syncthreads();
-    bitonic_sort_u64(k64, Ly.P);
-    for (uint32_t p = tid; p < m; p += kThreads)
-        keep[p] = (p == 0 || (k64[p - 1] >> 32) != (k64[p] >> 32)) ? 1u : 0u;
-    __syncthreads();
-    const uint32_t nL = block_exclusive_scan(keep, m, scan);
-    for (uint32_t p = tid; p < m; p += kThreads) {
-        const uint32_t nxt = p + 1 < m ? keep[p + 1] : nL;
-        if (nxt == keep[p]) continue;
-        const uint32_t c = keep[p], jj = (uint32_t)(k64[p] & 0xFFFFFFFFull);
-        L[c] = (uint32_t)(k64[p] >> 32);
-        wv[c] = a.Lval[(size_t)s * B + jj];
-        mag[c] = a.Lmag[(size_t)s * B + jj];
-    }
+    const uint32_t nL = sort_unique_u32(Lk, s_m, Lt, keep, scan);
+    const uint32_t* L = Lk;
     if (tid == 0) a.nL[s] = nL;
+    const double2* bins = a.bins + (size_t)s * a.bins_stride + (size_t)2 * a.npairs * B;
+    const uint32_t logNp = (uint32_t)(63 - __clzll((long long)a.n)) - a.logB;
+    for (uint32_t c = tid; c < nL; c += kThreads) {
+        const double2 w = estimate_one(L[c], a.R_est, dr, dr + kMaxRest, dr + 2 * kMaxRest,
+                                       [&](uint32_t q, uint32_t j) { return bins[(size_t)q * B + j]; }, (uint32_t)a.n,
+                                       a.nmask, logNp, a.wtab, a.est_gmin);
+        wv[c] = w;
+        mag[c] = __dadd_rn(__dmul_rn(w.x, w.x), __dmul_rn(w.y, w.y));
+    }
     __syncthreads();
     sort_by_magnitude(mag, L, nL, Ly.P, perm);
     const uint32_t nJ = nL < a.kprime ? nL : a.kprime;
@@ -826,7 +729,7 @@ cudaError_t launch_general_round(const GenArgs& a, uint32_t batch, const General
     if (e != cudaSuccess) return e;
     k_gen_finish<<<dim3(r.ngroups, batch), kThreads, r.fin_global ? 0 : r.smem_finish, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_gen_locate<<<dim3((r.B * r.t + kThreads - 1) / kThreads, batch), kThreads, 0, st>>>(a);
+    k_gen_locate<<<dim3((r.B + kThreads - 1) / kThreads, batch), kThreads, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_gen_estimate<<<batch, kThreads, r.est_global ? 0 : r.smem_estimate, st>>>(a);
     return cudaGetLastError();

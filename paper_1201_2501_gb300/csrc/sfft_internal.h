@@ -194,8 +194,6 @@ struct GenArgs {
     double* phase;         // [batch][npairs][B] phase(u_a conj(u_{a+beta})) / 2 pi
     size_t bins_stride, phase_stride;  // elements per request
     uint32_t* L;           // [batch][B] candidate frequencies
-    double2* Lval;         // [batch][B] EstimateValues' estimate of each bin's candidate
-    double* Lmag;          // [batch][B] its squared magnitude
     uint32_t* nL;          // [batch]
     uint32_t* zidx;        // [batch][zcap]
     double2* zval;
@@ -253,8 +251,6 @@ struct sfft_plan_s {
     double* d_phase = nullptr;
     uint32_t* d_L = nullptr;
     uint32_t* d_nL = nullptr;
-    double2* d_Lval = nullptr;
-    double* d_Lmag = nullptr;
     size_t bins_stride = 0, phase_stride = 0;
     std::vector<double> taps_host;  // every round's taps, FP64
     std::vector<double> wtab_host;  // every round's W(o), o = 0..n/2B
@@ -274,6 +270,11 @@ struct sfft_plan_s {
     double2* d_ubins = nullptr;
     uint32_t* d_aux = nullptr;
     sfft::ReqDesc* d_reqs = nullptr;  // [max_batch] request table of sfft_execute_requests
+    // page-locked copies of the table the caller passes (two, used in turn): the copy to d_reqs reads
+    // them asynchronously, so a caller's array (possibly freed at once) is never read by the device
+    sfft::ReqDesc* h_reqs[2] = {nullptr, nullptr};
+    cudaEvent_t ev_reqs[2] = {nullptr, nullptr};
+    int reqs_cur = 0;
     unsigned char* d_fin = nullptr;   // [max_batch][fin_stride] finisher arrays of rounds with fin_global
     size_t fin_stride = 0;
     unsigned char* d_gfin = nullptr;  // general mode: [max_batch][ngroups][gfin_stride]
