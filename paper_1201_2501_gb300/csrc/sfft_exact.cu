@@ -37,8 +37,8 @@ __device__ __forceinline__ const double* taps_of<double>(const ExactArgs& a) {
 // shared-memory layout of the finishing phase
 // ------------------------------------------------------------------------------------------------
 struct FinLayout {
-    size_t U, ent_idx, ent_bin, ent_val, ent_gain, ent_sub, bin_cnt, bin_start, bin_list, cand_idx, cand_val, srt_idx,
-        srt_val, out_idx, out_val, keep, scan;
+    size_t U, ent_idx, ent_bin, ent_val, ent_gain, ent_sub, bin_cnt, bin_start, bin_list, cand_idx, cand_bin, cand_gain,
+        cand_val, srt_idx, srt_val, out_idx, out_val, keep, scan;
     size_t total;
 };
 __host__ __device__ inline size_t fin_take(size_t* off, size_t bytes) {
@@ -59,6 +59,8 @@ __host__ __device__ inline FinLayout fin_layout(uint32_t B, uint32_t H, uint32_t
     L.bin_start = fin_take(&off, (size_t)(B + 1) * 4);
     L.bin_list = fin_take(&off, (size_t)zcap * 4);
     L.cand_idx = fin_take(&off, (size_t)B * 4);
+    L.cand_bin = fin_take(&off, (size_t)B * 4);
+    L.cand_gain = fin_take(&off, (size_t)B * 8);
     L.cand_val = fin_take(&off, (size_t)B * 16);
     L.srt_idx = fin_take(&off, (size_t)B * 4);
     L.srt_val = fin_take(&off, (size_t)B * 16);
@@ -85,6 +87,8 @@ struct DecodeCtx {
     uint32_t logR[kMaxHash];   // log2(beta_l / B)
     const double* wtab;
     double thr, iso_tol, gmin, ref_lo, ref_hi, ref_tol;
+    // the same thresholds for the FP32 decisions (ref_lo_f, ref_hi_f already scaled by thr)
+    float thr_f, iso_tol_f, ref_lo_f, ref_hi_f, ref_tol_f, inv_n_f;
 };
 
 __device__ __forceinline__ int32_t offset_of(uint32_t p, const DecodeCtx& d, uint32_t* jbin) {
@@ -118,15 +122,29 @@ __device__ void fill_ctx(DecodeCtx& d, uint64_t n, uint32_t nmask, uint32_t B, u
     d.ref_lo = ref_lo;
     d.ref_hi = ref_hi;
     d.ref_tol = ref_tol;
+    d.thr_f = (float)thr;
+    d.iso_tol_f = (float)iso_tol;
+    d.ref_lo_f = (float)(ref_lo * thr);
+    d.ref_hi_f = (float)(ref_hi * thr);
+    d.ref_tol_f = (float)ref_tol;
+    d.inv_n_f = __int_as_float((127 - (int)ilog2_u32(d.n)) << 23);  // 2^-log2 n, exact
 }
 
-// Returns 0 (nothing), 1 (a decode of J kept) or 2 (a re-estimate of a known entry).
-// *above is set when |u_0| > thr.  The zhat entries hashed to bin j are list[0..nbin) (entry ids),
-// with indices ent_idx[] and window gains ent_gain[].
-template <typename R>
-__device__ int decode_bin(const DecodeCtx& d, uint32_t j, const double2* u, const uint32_t* list, uint32_t nbin,
-                          const uint32_t* ent_idx, const double* ent_gain, uint32_t* oi, double2* ov, bool* above) {
-    const double mag0 = cmag<R>(u[0]);
+// Decode of one bin (NoiselessSparseFFTInner's loop body).  u[0..H) are the bin's hashings after the
+// subtraction of zhat, in the precision R of the data path.  Returns 0 (nothing), 1 (a decode of J
+// kept) or 2 (a re-estimate of a known entry), with the index in *oi and the window gain that divides
+// u_0 in *gain (the caller forms the FP64 value).  *above is set when |u_0| > thr.  The zhat entries
+// hashed to bin j are list[0..nbin) (entry ids), with indices ent_idx[] and window gains ent_gain[].
+//
+// The FP64 data path decides in FP64.  The FP32 path takes every decision (magnitudes, phases, the
+// location ladder, isolation and re-estimation tests) in FP32: its bins carry ~1e-6 of rounding, the
+// ladder keeps a tolerance of at least tau_dec per level and GB300 issues FP64 at 1/64 of FP32, so FP64
+// arithmetic there would cost most of the finisher's time and change no decision outside a
+// measure-zero band at the thresholds.
+__device__ int decode_bin_fp64(const DecodeCtx& d, uint32_t j, const double2* u, const uint32_t* list, uint32_t nbin,
+                               const uint32_t* ent_idx, const double* ent_gain, uint32_t* oi, double* gout,
+                               bool* above) {
+    const double mag0 = cmag<double>(u[0]);
     const uint32_t L = d.H - 1;
     *above = false;
     if (!(mag0 > d.thr)) {
@@ -134,8 +152,8 @@ __device__ int decode_bin(const DecodeCtx& d, uint32_t j, const double2* u, cons
         if (nbin == 0 || !(mag0 > d.ref_lo * d.thr && mag0 <= d.ref_hi * d.thr)) return 0;
         double th[kMaxHash];
         for (uint32_t l = 0; l < L; ++l) {
-            if (fabs(cmag<R>(u[l + 1]) - mag0) > 0.25 * mag0) return 0;
-            th[l] = phase01<R>(mul_conj(u[0], u[l + 1]));
+            if (fabs(cmag<double>(u[l + 1]) - mag0) > 0.25 * mag0) return 0;
+            th[l] = phase01<double>(mul_conj(u[0], u[l + 1]));
         }
         uint32_t matches = 0, who = 0;
         double gw = 1.0;
@@ -159,19 +177,19 @@ __device__ int decode_bin(const DecodeCtx& d, uint32_t j, const double2* u, cons
         }
         if (matches != 1) return 0;
         *oi = who;
-        *ov = make_double2(u[0].x / gw, u[0].y / gw);
+        *gout = gw;
         return 2;
     }
     *above = true;
     // location ladder, coarsest shift first: q = sigma i mod n/B.  Every modulus is a power of two,
     // so mod and division are masks and exact scalings.
     uint32_t logM = d.logNp - d.logR[L - 1];
-    const double th = phase01<R>(mul_conj(u[0], u[L]));
+    const double th = phase01<double>(mul_conj(u[0], u[L]));
     uint64_t c = (uint64_t)(int64_t)floor(th * ldexp(1.0, (int)logM) + 0.5) & ((uint64_t(1) << logM) - 1);
     for (int l = (int)L - 2; l >= 0; --l) {
         const uint32_t logMp = d.logNp - d.logR[l];
         const uint32_t logRatio = logMp - logM;
-        const double thl = phase01<R>(mul_conj(u[0], u[l + 1]));
+        const double thl = phase01<double>(mul_conj(u[0], u[l + 1]));
         const double y = thl * ldexp(1.0, (int)logRatio) - ldexp((double)c, -(int)logM);
         const int64_t h = (int64_t)floor(y + 0.5) & (int64_t)((uint64_t(1) << logRatio) - 1);
         c += (uint64_t(1) << logM) * (uint64_t)h;
@@ -184,12 +202,141 @@ __device__ int decode_bin(const DecodeCtx& d, uint32_t j, const double2* u, cons
     const uint32_t si = (p + d.sb) & d.nmask;
     const uint32_t i = (d.sigma_inv * si) & d.nmask;
     for (uint32_t l = 0; l < L; ++l)
-        if (fabs(cmag<R>(u[l + 1]) - mag0) > d.iso_tol * mag0) return 0;
+        if (fabs(cmag<double>(u[l + 1]) - mag0) > d.iso_tol * mag0) return 0;
     const double gain = d.wtab[o < 0 ? -o : o];
     if (!(gain >= d.gmin)) return 0;
     *oi = i;
-    *ov = make_double2(u[0].x / gain, u[0].y / gain);
+    *gout = gain;
     return 1;
+}
+
+__device__ __forceinline__ float2 mul_conj_f(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// phase(z) / 2 pi in [0, 1)
+__device__ __forceinline__ float phase01_f(float2 z) {
+    float p = atan2f(z.y, z.x) * 0.159154943091895336f;
+    if (p < 0.0f) p += 1.0f;
+    if (p >= 1.0f) p -= 1.0f;
+    return p;
+}
+__device__ __forceinline__ float pow2_f(int e) { return __int_as_float((127 + e) << 23); }  // 2^e, |e| < 127
+
+__device__ int decode_bin_fp32(const DecodeCtx& d, uint32_t j, const float2* u, const uint32_t* list, uint32_t nbin,
+                               const uint32_t* ent_idx, const double* ent_gain, uint32_t* oi, double* gout,
+                               bool* above) {
+    const float mag0 = hypotf(u[0].x, u[0].y);
+    const uint32_t L = d.H - 1;
+    *above = false;
+    if (!(mag0 > d.thr_f)) {
+        // re-estimation of a known value: exactly one entry of the bin must explain the residual
+        if (nbin == 0 || !(mag0 > d.ref_lo_f && mag0 <= d.ref_hi_f)) return 0;
+        float th[kMaxHash];
+        for (uint32_t l = 0; l < L; ++l) {
+            if (fabsf(hypotf(u[l + 1].x, u[l + 1].y) - mag0) > 0.25f * mag0) return 0;
+            th[l] = phase01_f(mul_conj_f(u[0], u[l + 1]));
+        }
+        uint32_t matches = 0, who = 0;
+        double gw = 1.0;
+        for (uint32_t x = 0; x < nbin; ++x) {
+            const uint32_t e = list[x];
+            const uint32_t i = ent_idx[e];
+            const double gain = ent_gain[e];
+            if (!(gain >= d.gmin)) continue;
+            bool ok = true;
+            for (uint32_t l = 0; l < L && ok; ++l) {
+                const uint32_t ph = (d.shift[l] * d.sigma * i) & d.nmask;
+                float dist = fabsf(th[l] - (float)ph * d.inv_n_f);
+                if (dist > 0.5f) dist = 1.0f - dist;
+                ok = dist * 6.28318530717958648f < d.ref_tol_f;
+            }
+            if (ok) {
+                ++matches;
+                who = i;
+                gw = gain;
+            }
+        }
+        if (matches != 1) return 0;
+        *oi = who;
+        *gout = gw;
+        return 2;
+    }
+    *above = true;
+    // location ladder, coarsest shift first (as decode_bin_fp64).  Products with powers of two are
+    // exact; c < 2^logM <= 2^30 stays an integer held in 64 bits.
+    uint32_t logM = d.logNp - d.logR[L - 1];
+    const float th = phase01_f(mul_conj_f(u[0], u[L]));
+    uint64_t c = (uint64_t)(int64_t)floorf(th * pow2_f((int)logM) + 0.5f) & ((uint64_t(1) << logM) - 1);
+    for (int l = (int)L - 2; l >= 0; --l) {
+        const uint32_t logMp = d.logNp - d.logR[l];
+        const uint32_t logRatio = logMp - logM;
+        const float thl = phase01_f(mul_conj_f(u[0], u[l + 1]));
+        const float y = thl * pow2_f((int)logRatio) - (float)c * pow2_f(-(int)logM);
+        const int64_t h = (int64_t)floorf(y + 0.5f) & (int64_t)((uint64_t(1) << logRatio) - 1);
+        c += (uint64_t(1) << logM) * (uint64_t)h;
+        logM = logMp;
+    }
+    const uint32_t q = (uint32_t)c;
+    const uint32_t dd = (q + d.Np - (d.sb & (d.Np - 1)) + (d.Np >> 1)) & (d.Np - 1);
+    const int32_t o = (int32_t)dd - (int32_t)(d.Np >> 1);
+    const uint32_t p = (j * d.Np + (uint32_t)o) & d.nmask;
+    const uint32_t si = (p + d.sb) & d.nmask;
+    const uint32_t i = (d.sigma_inv * si) & d.nmask;
+    for (uint32_t l = 0; l < L; ++l)
+        if (fabsf(hypotf(u[l + 1].x, u[l + 1].y) - mag0) > d.iso_tol_f * mag0) return 0;
+    const double gain = d.wtab[o < 0 ? -o : o];
+    if (!(gain >= d.gmin)) return 0;
+    *oi = i;
+    *gout = gain;
+    return 1;
+}
+
+__device__ __forceinline__ int decode_bin(const DecodeCtx& d, uint32_t j, const double2* u, const uint32_t* list,
+                                          uint32_t nbin, const uint32_t* ent_idx, const double* ent_gain, uint32_t* oi,
+                                          double* gout, bool* above) {
+    return decode_bin_fp64(d, j, u, list, nbin, ent_idx, ent_gain, oi, gout, above);
+}
+__device__ __forceinline__ int decode_bin(const DecodeCtx& d, uint32_t j, const float2* u, const uint32_t* list,
+                                          uint32_t nbin, const uint32_t* ent_idx, const double* ent_gain, uint32_t* oi,
+                                          double* gout, bool* above) {
+    return decode_bin_fp32(d, j, u, list, nbin, ent_idx, ent_gain, oi, gout, above);
+}
+
+// Bin j's hashings after the subtraction of zhat: u_h = U_h - sum over the bin's entries e (in list
+// order) of sub[e H + h], summed in FP64.  The FP32 path keeps U_h itself when the bin holds no entry
+// and rounds the FP64 difference to FP32 otherwise.
+template <typename C, typename V>
+__device__ __forceinline__ void subtracted_bin(const C* U, uint32_t B, uint32_t H, uint32_t j, const uint32_t* list,
+                                               uint32_t nbin, const double2* sub, V* u) {
+    for (uint32_t h = 0; h < H; ++h) {
+        const C v = U[h * B + j];
+        if (sizeof(V) == sizeof(float2) && nbin == 0) {
+            u[h].x = v.x;
+            u[h].y = v.y;
+            continue;
+        }
+        double2 w = make_double2((double)v.x, (double)v.y);
+        for (uint32_t x = 0; x < nbin; ++x) {
+            const uint32_t e = list[x];
+            w.x -= sub[e * H + h].x;
+            w.y -= sub[e * H + h].y;
+        }
+        u[h].x = w.x;
+        u[h].y = w.y;
+    }
+}
+// u_0 of bin j after the subtraction, in FP64 (the first row of subtracted_bin, same order)
+template <typename C>
+__device__ __forceinline__ double2 subtracted_u0(const C* U, uint32_t H, uint32_t j, const uint32_t* list,
+                                                 uint32_t nbin, const double2* sub) {
+    const C v = U[j];
+    double2 w = make_double2((double)v.x, (double)v.y);
+    for (uint32_t x = 0; x < nbin; ++x) {
+        const uint32_t e = list[x];
+        w.x -= sub[e * H].x;
+        w.y -= sub[e * H].y;
+    }
+    return w;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -291,6 +438,8 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     uint32_t* bin_start = reinterpret_cast<uint32_t*>(smem + Ly.bin_start);
     uint32_t* bin_list = reinterpret_cast<uint32_t*>(smem + Ly.bin_list);
     uint32_t* cand_idx = reinterpret_cast<uint32_t*>(smem + Ly.cand_idx);
+    uint32_t* cand_bin = reinterpret_cast<uint32_t*>(smem + Ly.cand_bin);
+    double* cand_gain = reinterpret_cast<double*>(smem + Ly.cand_gain);
     double2* cand_val = reinterpret_cast<double2*>(smem + Ly.cand_val);
     uint32_t* srt_idx = reinterpret_cast<uint32_t*>(smem + Ly.srt_idx);
     double2* srt_val = reinterpret_cast<double2*>(smem + Ly.srt_val);
@@ -351,43 +500,43 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     block_fft_rows<R>(U, H, a.logB);  // ends with a barrier
     bucket_entries(ent_bin, nz, B, bin_cnt, bin_start, bin_list, scan);
 
-    // step 4 and the decode, one bin per thread
+    if (a.bins_only) {  // single-hashing mode: the subtracted bins u_0 in FP64, no decode
+        for (uint32_t j = tid; j < B; j += kThreads)
+            a.ubins[j] = subtracted_u0(U, H, j, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_sub);
+        return;
+    }
+    // step 4 and the decode, one bin per thread: decisions in the data path's precision
     for (uint32_t j = tid; j < B; j += kThreads) {
-        double2 u[kMaxHash];
-        for (uint32_t h = 0; h < H; ++h) {
-            const C v = U[h * B + j];
-            u[h] = make_double2((double)v.x, (double)v.y);
-        }
-        for (uint32_t x = bin_start[j]; x < bin_start[j + 1]; ++x) {
-            const uint32_t e = bin_list[x];
-            for (uint32_t h = 0; h < H; ++h) {
-                u[h].x -= ent_sub[e * H + h].x;
-                u[h].y -= ent_sub[e * H + h].y;
-            }
-        }
-        if (a.bins_only) {
-            a.ubins[j] = u[0];
-            continue;
-        }
+        C u[kMaxHash];
+        const uint32_t* list = bin_list + bin_start[j];
+        const uint32_t nbin = bin_start[j + 1] - bin_start[j];
+        subtracted_bin(U, B, H, j, list, nbin, ent_sub, u);
         uint32_t oi = 0;
-        double2 ov;
+        double gain = 1.0;
         bool above;
-        const int kind = decode_bin<R>(d, j, u, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_idx,
-                                       ent_gain, &oi, &ov, &above);
+        const int kind = decode_bin(d, j, u, list, nbin, ent_idx, ent_gain, &oi, &gain, &above);
         if (above) atomicAdd(&s_above, 1u);
         if (kind == 1) atomicAdd(&s_kept, 1u);
         if (kind != 0) {
             const uint32_t slot = atomicAdd(&s_nw, 1u);
             cand_idx[slot] = oi;
-            cand_val[slot] = ov;
+            cand_bin[slot] = j;
+            cand_gain[slot] = gain;
         }
     }
     __syncthreads();
-    if (a.bins_only) return;
+    // values of the decoded bins: u_0 (step 4 in FP64) / W(-o), for the candidates only
+    const uint32_t nw = s_nw;
+    for (uint32_t c = tid; c < nw; c += kThreads) {
+        const uint32_t j = cand_bin[c];
+        const double2 u0 = subtracted_u0(U, H, j, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_sub);
+        const double g = cand_gain[c];
+        cand_val[c] = make_double2(u0.x / g, u0.y / g);
+    }
+    __syncthreads();
 
     // merge what into zhat (NoiselessSparseFFT: zhat <- zhat + what), zhat first on equal indices,
     // then drop entries below prune * thr
-    const uint32_t nw = s_nw;
     const uint32_t tot = nz + nw;
     rank_sort(cand_idx, cand_val, nw, srt_idx, srt_val);
     for (uint32_t e = tid; e < nz; e += kThreads) {
@@ -656,19 +805,23 @@ __global__ void __launch_bounds__(kThreads) k_exact_decode(const DecodeArgs a) {
     __syncthreads();
     bucket_entries(ent_bin, a.nz, B, bin_cnt, bin_start, bin_list, scan);
     for (uint32_t j = tid; j < B; j += kThreads) {
-        double2 u[kMaxHash];
-        for (uint32_t h = 0; h < a.H; ++h) u[h] = U[h * B + j];
+        using C = typename Cx<R>::T;
+        C u[kMaxHash];  // the caller's bins, in the precision of the decisions
+        for (uint32_t h = 0; h < a.H; ++h) {
+            u[h].x = U[h * B + j].x;
+            u[h].y = U[h * B + j].y;
+        }
         uint32_t oi = 0;
-        double2 ov;
+        double gain = 1.0;
         bool above;
-        const int kind = decode_bin<R>(d, j, u, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_idx,
-                                       ent_gain, &oi, &ov, &above);
+        const int kind = decode_bin(d, j, u, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_idx,
+                                    ent_gain, &oi, &gain, &above);
         if (above) atomicAdd(&s_above, 1u);
         if (kind == 1) atomicAdd(&s_kept, 1u);
         if (kind != 0) {
             const uint32_t slot = atomicAdd(&s_nw, 1u);
             cand_idx[slot] = oi;
-            cand_val[slot] = ov;
+            cand_val[slot] = make_double2(U[j].x / gain, U[j].y / gain);
         }
     }
     __syncthreads();
