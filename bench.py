@@ -138,11 +138,11 @@ def replica_value(units_per_rank, world, steps, ms_local):
 
 
 KERNEL_SOURCES = ("sfft_exact.cu", "sfft_device.cuh", "sfft_internal.h", "philox.cuh")
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_exact_round_n22_k64_b256_launches.md")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_exact_step_n22_k64_b256_launches.md")
 
 
 def kernel_fingerprint():
-    """First 16 hex digits of sha256 over the sha256 hex digests of the exact round kernel's sources."""
+    """First 16 hex digits of sha256 over the sha256 hex digests of the exact kernel's sources."""
     import hashlib
 
     h = hashlib.sha256()
@@ -153,7 +153,7 @@ def kernel_fingerprint():
 
 
 def profiled_traffic():
-    """DRAM bytes (read + write) of one step of the round kernel, from the committed ncu launch list
+    """DRAM bytes (read + write) of one step of the exact kernel, from the committed ncu launch list
     of the same workload; None when the kernel sources changed since that capture."""
     import re
 
@@ -170,7 +170,7 @@ def profiled_traffic():
 
 
 def launch_groups(batch, streams):
-    """Stream groups sfft_execute splits an exact-mode batch into (one round kernel each per round)."""
+    """Stream groups sfft_execute splits an exact-mode batch into (one k_exact_step launch each per step)."""
     g = streams if streams else 4
     g = min(g, 8, batch)
     return 1 if batch < 8 else g
@@ -561,14 +561,14 @@ def run_ours(args):
                        "l2": "inputs (8 GiB per GPU) exceed L2; no flush", "parallelism": f"replicas x{world}",
                        "support_exact_fraction": exact / batch,
                        "path": "one persistent launch per step (device queue of request-round-chunk items)"
-                               if args.path == "persistent" else "one kernel per round and stream group"},
+                               if args.path == "persistent" else "one kernel per step and stream group (all rounds)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": profiled_traffic() if batch == 256 else None,
-                         "kernel": "k_exact_round (all rounds of a step)",
+                         "kernel": "k_exact_step (all rounds of a step)",
                          "bytes_per_transform": bytes_tr, "samples_per_transform": samples_tr,
                          "peak_kind": peak_kind},
             "e2e": e2e, "clocks": clk.summary(), "gpu_launches": (args.steps if args.path == "persistent"
-                                                             else plan.rounds * launch_groups(batch, params.streams) * args.steps),
+                                                             else launch_groups(batch, params.streams) * args.steps),
             "cpu_baseline": cpu,
         }
         line.update(extra)

@@ -77,8 +77,10 @@ typedef struct sfft_params {
     uint32_t R_est;        /* general: hashings of EstimateValues */
     double s;              /* general: vote half-width s pi */
     double est_gmin;       /* general: a hashing joins the median only if W(-o) >= est_gmin */
-    uint32_t streams;      /* a batch is split over this many internal streams (0 -> 4) so that one
-                              group's end-of-round work overlaps another group's gather */
+    uint32_t streams;      /* a batch is split over this many internal streams so that one group's
+                              end-of-round work overlaps another group's gather (0 -> 1 in exact
+                              mode, whose one launch per group already overlaps its rounds; 4 in
+                              general mode) */
     uint32_t gain;         /* the window gain used to subtract recovered coefficients and to divide
                               decoded values: 0 -> the exact response W(o) of the truncated taps
                               (default); 1 -> the paper's closed form Ghat'(o) (Sec. 7: 1 on the pass

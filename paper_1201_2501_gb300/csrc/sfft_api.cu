@@ -180,10 +180,17 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     for (size_t i = 0; i < ntaps; ++i) t32[i] = (float)pl->taps_host[i];
     size_t part_elems = 0, max_smem = 0, gs_max = 0, fs_max = 0, ls_max = 0, es_max = 0;
     uint32_t maxB = 0;
+    // exact mode: every round's partial folds live at once (the one-launch path gathers all rounds
+    // before their finishers), round t at part_off[t] of a request's region
+    std::vector<size_t> part_off;
+    if (!general && pl->rounds.size() > kMaxRounds) {
+        free_plan(pl);
+        return SFFT_ERR_K_RANGE;
+    }
     for (const ExactRound& r : pl->rounds) {
         pl->samples += 2 * (uint64_t)r.T + 1 + r.shift[r.nshift - 1];
-        const size_t e = (size_t)r.chunks * (1 + r.nshift) * r.B;
-        if (e > part_elems) part_elems = e;
+        part_off.push_back(part_elems);
+        part_elems += (size_t)r.chunks * (1 + r.nshift) * r.B;
         if (r.smem > max_smem) max_smem = r.smem;
         if (r.B > maxB) maxB = r.B;
         if (r.fin_global && r.fin_bytes > pl->fin_stride) pl->fin_stride = (r.fin_bytes + 255) & ~size_t(255);
@@ -223,7 +230,9 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     SFFT_ALLOC(pl->d_taps64, ntaps * sizeof(double));
     SFFT_ALLOC(pl->d_wtab, pl->wtab_len * sizeof(double));
     SFFT_ALLOC(pl->d_part, pl->part_bytes);
-    SFFT_ALLOC(pl->d_counter, (size_t)max_batch * sizeof(uint32_t));
+    const size_t ncounters = (size_t)max_batch * (general ? 1 : pl->rounds.size());
+    SFFT_ALLOC(pl->d_counter, ncounters * sizeof(uint32_t));
+
     SFFT_ALLOC(pl->d_zidx, (size_t)max_batch * p->z_cap * sizeof(uint32_t));
     SFFT_ALLOC(pl->d_zval, (size_t)max_batch * p->z_cap * sizeof(double2));
     SFFT_ALLOC(pl->d_zcount, (size_t)max_batch * sizeof(uint32_t));
@@ -263,9 +272,23 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     if ((e = cudaMemcpy(pl->d_wtab, pl->wtab_host.data(), pl->wtab_len * sizeof(double), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return fail(e, "upload window table");
-    if ((e = cudaMemset(pl->d_counter, 0, (size_t)max_batch * sizeof(uint32_t))) != cudaSuccess)
+    if ((e = cudaMemset(pl->d_counter, 0, ncounters * sizeof(uint32_t))) != cudaSuccess)
         return fail(e, "clear counters");
-    pl->nstreams = p->streams == 0 ? 4 : p->streams;
+    if (!general) {  // the round blocks of the one-launch path (each launch fills in its own fields)
+        const size_t csize = fp64 ? 16 : 8;
+        for (uint32_t t = 0; t < (uint32_t)pl->rounds.size(); ++t) {
+            ExactArgs a = base_args(pl, pl->rounds[t], t);
+            a.part = static_cast<unsigned char*>(pl->d_part) + part_off[t] * csize;
+            a.counter = pl->d_counter + (size_t)t * max_batch;
+            a.first_round = t == 0;
+            a.last_round = t + 1 == pl->rounds.size();
+            pl->rdesc.push_back(a);
+        }
+        pl->step_smem = max_smem;
+    }
+    // default stream groups: one for the exact path (its single launch per batch already overlaps
+    // rounds; groups only add concurrent tails), four for the general path's per-round kernel chain
+    pl->nstreams = p->streams != 0 ? p->streams : (general ? 4 : 1);
     if (pl->nstreams > (uint32_t)sfft_plan_s::kMaxStreams) pl->nstreams = sfft_plan_s::kMaxStreams;
     if ((e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming)) != cudaSuccess)
         return fail(e, "create event");
@@ -446,9 +469,10 @@ sfft_status sfft::execute_batch(sfft_plan plan, const void* d_x, const ReqDesc* 
     SFFT_CUDA(cudaMemsetAsync(plan->d_zcount, 0, batch * sizeof(uint32_t), st), "clear zhat");
     SFFT_CUDA(cudaMemsetAsync(plan->d_zflag, 0, batch * sizeof(int32_t), st), "clear flags");
     const uint32_t R = (uint32_t)plan->rounds.size();
-    // Requests are independent, so the batch is cut into groups whose round chains run on separate
-    // streams: while one group's last requests finish a round, the others gather.  The groups fork
-    // from and join back into the caller's stream with events (capturable in a CUDA graph).
+    // One launch per group covers every round (k_exact_step).  Requests are independent, so the batch
+    // may be cut into groups on separate streams: one group's last finishers overlap the next group's
+    // gathers.  The groups fork from and join back into the caller's stream with events (capturable
+    // in a CUDA graph).
     uint32_t groups = plan->nstreams;
     if (groups > batch) groups = batch;
     if (batch < 8) groups = 1;
@@ -460,22 +484,21 @@ sfft_status sfft::execute_batch(sfft_plan plan, const void* d_x, const ReqDesc* 
         const uint32_t r0 = (uint32_t)((uint64_t)batch * g / groups);
         const uint32_t r1 = (uint32_t)((uint64_t)batch * (g + 1) / groups);
         cudaStream_t gs = groups > 1 ? plan->aux[g] : st;
+        ExactArgs rounds[kMaxRounds];
         for (uint32_t t = 0; t < R; ++t) {
-            const ExactRound& r = plan->rounds[t];
-            ExactArgs a = base_args(plan, r, t);
+            ExactArgs& a = rounds[t];
+            a = plan->rdesc[t];
             a.x = d_x;
             a.reqs = d_reqs;
             a.seed = seed;
             a.req_base = r0;
-            a.first_round = t == 0;
-            a.last_round = t + 1 == R;
             a.out_idx = d_idx;
             a.out_val = reinterpret_cast<double2*>(d_val);
             a.out_cap = cap;
             a.out_count = d_count;
             a.out_flag = d_flag;
-            SFFT_CUDA(launch_exact_round(a, r1 - r0, r.smem, gs, fp64), "exact round");
         }
+        SFFT_CUDA(launch_exact_step(rounds, R, r1 - r0, plan->step_smem, gs, fp64), "exact step");
         if (groups > 1) {
             SFFT_CUDA(cudaEventRecord(plan->ev_join[g], gs), "join");
             SFFT_CUDA(cudaStreamWaitEvent(st, plan->ev_join[g], 0), "join");

@@ -1,15 +1,20 @@
-// sfft_exact.cu -- the exact-mode round of the sparse FFT on sm_103a (Algorithm 1 of Hassanieh, Indyk,
-// Katabi, Price), as one kernel per round for a whole batch of requests.
+// sfft_exact.cu -- the exact-mode sparse FFT on sm_103a (Algorithm 1 of Hassanieh, Indyk, Katabi,
+// Price) for a whole batch of requests.
 //
-// Grid (chunks, batch).  Every CTA performs steps 1-2 of HashToBins (proof of Lemma "hashtobins") for
-// 2048 consecutive window taps of one request and all hashings of the round (a = 0 and the ladder
-// shifts share one staged run of samples, since x_{sigma(t - beta)} is sample t - beta of the
-// sigma-strided sequence): it gathers the permuted samples, applies window and modulation, folds
-// them modulo B and stores the partial fold.  The last CTA of a request to arrive (arrival counter,
-// no waiting) sums the partials in chunk order, runs the B-point FFTs (step 3), subtracts the
-// recovered coefficients in FP64 (step 4), decodes locations and values
+// Work unit: one chunk (by default 2048 consecutive window taps) of one round of one request.  Its
+// CTA performs steps 1-2 of HashToBins (proof of Lemma "hashtobins") for all hashings of the round
+// (a = 0 and the ladder shifts share one staged run of samples, since x_{sigma(t - beta)} is sample
+// t - beta of the sigma-strided sequence): it gathers the permuted samples, applies window and
+// modulation, folds them modulo B and stores the partial fold.  The last arrival of a request's round
+// (arrival counter, no waiting) sums the partials in chunk order, runs the B-point FFTs (step 3),
+// subtracts the recovered coefficients in FP64 (step 4), decodes locations and values
 // (NoiselessSparseFFTInner's loop over J) and merges the result into zhat (NoiselessSparseFFT).
-// Every reduction has a fixed order and no floating-point atomics exist, so results are
+//
+// k_exact_step runs every round of the batch in one launch: the sample positions of all rounds are
+// known up front (sigma, b come from the counter-based draws, never from zhat), so all chunks are
+// gathered at once and only the finishers are ordered, round t's by the arrival of round t - 1's.
+// k_exact_round runs one round (single-hashing entry points and the persistent queue reuse its
+// pieces).  Every reduction has a fixed order and no floating-point atomics exist, so results are
 // bit-reproducible.
 #include <cuda_runtime.h>
 
@@ -451,16 +456,17 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
 
     // zhat of this request and its per-entry subtraction terms (independent of the bins: done first,
     // in parallel, so that the bin threads below only add)
-    const uint32_t nz = a.bins_only ? a.e_nz : min(a.zcount[s], a.zcap);
+    // zhat is read through L2 only: in the one-launch path another CTA of this launch wrote it
+    const uint32_t nz = a.bins_only ? a.e_nz : min(__ldcg(a.zcount + s), a.zcap);
     DecodeCtx d;
     uint64_t ladder[kMaxHash];
     for (int l = 0; l < kMaxHash; ++l) ladder[l] = l + 1 < kMaxHash ? a.shift64[l + 1] : 0;
     fill_ctx(d, a.n, a.nmask, B, a.logB, H, ladder, sigma, b, a.wtab, a.thr, a.iso_tol, a.gmin, a.ref_lo, a.ref_hi,
              a.ref_tol);
     for (uint32_t e = tid; e < nz; e += kThreads) {
-        const uint32_t i = a.zidx[(size_t)s * a.zcap + e];
+        const uint32_t i = __ldcg(a.zidx + (size_t)s * a.zcap + e);
         ent_idx[e] = i;
-        ent_val[e] = a.zval[(size_t)s * a.zcap + e];
+        ent_val[e] = __ldcg(a.zval + (size_t)s * a.zcap + e);
         uint32_t jb;
         const int32_t o = offset_of((sigma * (i - b)) & a.nmask, d, &jb);
         ent_bin[e] = jb;
@@ -593,7 +599,7 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
             const uint32_t kept_count = overflow ? a.zcap : newcount;
             a.out_count[s] = kept_count < a.out_cap ? kept_count : a.out_cap;
             int32_t flag = SFFT_OK;
-            if (a.zflag[s] || kept_count > a.out_cap)
+            if (__ldcg(a.zflag + s) || kept_count > a.out_cap)
                 flag = SFFT_ERR_CAPACITY;
             else if (s_above > s_kept)
                 flag = SFFT_ERR_NOT_CONVERGED;
@@ -629,6 +635,42 @@ __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_round
     __threadfence();
     finish_round<R>(a, s, sigma, b, a.fin_scratch ? a.fin_scratch + (size_t)s * a.fin_stride : smem);
     if (threadIdx.x == 0) a.counter[s] = 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// One launch per batch: all rounds' chunks, finishers chained by arrival counters
+// ------------------------------------------------------------------------------------------------
+template <typename R, int NR>
+__global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_step(const __grid_constant__ StepParams<NR> sp) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_last;
+    const uint32_t tid = threadIdx.x;
+    uint32_t t = 0;
+    while (t + 1 < sp.R && blockIdx.x >= sp.seg[t + 1]) ++t;
+    const ExactArgs* a = &sp.r[t];
+    const uint32_t local = blockIdx.x - sp.seg[t];
+    const uint32_t c = local % a->chunks;
+    const uint32_t s = a->req_base + local / a->chunks;
+    const ReqView rq = req_view(a->reqs, a->x, a->n * sizeof(typename Cx<R>::T), a->seed, s, a->nmask);
+    uint32_t sigma, b;
+    exact_hash(rq.seed, rq.id, t, a->nmask, &sigma, &b);
+    gather_fold<R>(*a, rq.x, rq.xmask, s, c, sigma, b, smem);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(a->counter + s, 1u) + 1u == a->chunks + (t > 0 ? 1u : 0u)) ? 1u : 0u;
+    __syncthreads();
+    while (s_last) {
+        __threadfence();
+        finish_round<R>(*a, s, sigma, b, a->fin_scratch ? a->fin_scratch + (size_t)s * a->fin_stride : smem);
+        __threadfence();  // zhat of round t is visible before round t + 1 counts this arrival
+        __syncthreads();
+        if (tid == 0) a->counter[s] = 0;  // every arrival of round t has happened
+        if (t + 1 >= sp.R) break;
+        a = &sp.r[++t];
+        if (tid == 0) s_last = (atomicAdd(a->counter + s, 1u) == a->chunks) ? 1u : 0u;
+        __syncthreads();
+        if (s_last) exact_hash(rq.seed, rq.id, t, a->nmask, &sigma, &b);
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -858,10 +900,18 @@ cudaError_t set_exact_smem_limit(size_t bytes, bool fp64) {
     size_t& cur = limit[fp64 ? 1 : 0];
     if (bytes <= cur) return cudaSuccess;
     cudaError_t e;
-    if (fp64)
-        e = cudaFuncSetAttribute(k_exact_round<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    else
-        e = cudaFuncSetAttribute(k_exact_round<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const int b = (int)bytes;
+    if (fp64) {
+        e = cudaFuncSetAttribute(k_exact_round<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_exact_step<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_exact_step<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_exact_step<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    } else {
+        e = cudaFuncSetAttribute(k_exact_round<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_exact_step<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_exact_step<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_exact_step<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    }
     if (e == cudaSuccess) cur = bytes;
     return e;
 }
@@ -873,6 +923,35 @@ cudaError_t launch_exact_round(const ExactArgs& a, uint32_t batch, size_t smem, 
     else
         k_exact_round<float><<<grid, kThreads, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int NR>
+static cudaError_t launch_step_nr(const ExactArgs* rounds, uint32_t R, uint32_t batch, size_t smem, cudaStream_t st,
+                                  bool fp64) {
+    StepParams<NR> sp;
+    sp.R = R;
+    sp.seg[0] = 0;
+    for (uint32_t t = 0; t < R; ++t) {
+        const uint64_t end = (uint64_t)sp.seg[t] + (uint64_t)rounds[t].chunks * batch;
+        if (end > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;  // grid limit
+        sp.seg[t + 1] = (uint32_t)end;
+        sp.r[t] = rounds[t];
+    }
+    const uint32_t ctas = sp.seg[R];
+    if (ctas == 0) return cudaSuccess;
+    if (fp64)
+        k_exact_step<double, NR><<<ctas, kThreads, smem, st>>>(sp);
+    else
+        k_exact_step<float, NR><<<ctas, kThreads, smem, st>>>(sp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_step(const ExactArgs* rounds, uint32_t R, uint32_t batch, size_t smem, cudaStream_t st,
+                              bool fp64) {
+    if (R == 0 || R > kMaxRounds) return cudaErrorInvalidValue;
+    if (R <= 8) return launch_step_nr<8>(rounds, R, batch, smem, st, fp64);
+    if (R <= 16) return launch_step_nr<16>(rounds, R, batch, smem, st, fp64);
+    return launch_step_nr<32>(rounds, R, batch, smem, st, fp64);
 }
 
 cudaError_t launch_exact_decode(const DecodeArgs& a, cudaStream_t st) {

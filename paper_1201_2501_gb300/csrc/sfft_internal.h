@@ -17,6 +17,7 @@ constexpr int kMaxHash = 4;       // hashings per exact round: a = 0 plus up to 
 constexpr uint32_t kMaxB = 4096;  // largest B of the fused exact round
 constexpr uint32_t kNoIndex = 0xFFFFFFFFu;
 constexpr size_t kFinSmemMax = 160 * 1024;  // largest on-chip finisher of the exact round
+constexpr uint32_t kMaxRounds = 32;         // rounds of an exact plan (ceil(log2 k) + 1 + extra)
 
 // Per-request descriptor of a launch (device table, optional).  Without a table, request s of a
 // launch reads row s of the batch and draws its hashings with the launch's seed and request index s;
@@ -92,6 +93,20 @@ struct ExactArgs {
     int bins_only;
     uint32_t e_sigma, e_b, e_nz;
     double2* ubins;
+};
+
+// One launch of the exact algorithm over a batch: every round's gather chunks at once, grouped by
+// round (segment t = chunks_t x batch CTAs, request-major, chunk fastest), since no sample position
+// depends on zhat.  Round t of request s is finished by whichever arrives last: its t-th round's final
+// chunk or round t - 1's finisher (arrival counter t of s, target chunks_t + [t > 0]).  That CTA then
+// arrives on round t + 1 and, if last there too, finishes it as well.  Nobody waits.  The round
+// blocks (tables, workspace and this launch's signal and outputs) travel in the kernel parameters,
+// NR of them (8, 16 or 32: the smallest that holds the plan's rounds).
+template <int NR>
+struct StepParams {
+    uint32_t R;
+    uint32_t seg[NR + 1];  // first CTA of each round's segment; seg[R] = grid size
+    ExactArgs r[NR];
 };
 
 // The persistent exact path: requests of different plans (n, k, schedule) in one launch, their
@@ -261,7 +276,9 @@ struct sfft_plan_s {
     void* d_part = nullptr;
     size_t part_bytes = 0;
     size_t part_stride = 0;  // elements of the partial-fold buffer owned by one request
-    uint32_t* d_counter = nullptr;
+    uint32_t* d_counter = nullptr;  // [R][max_batch] arrival counters (zero between launches)
+    std::vector<sfft::ExactArgs> rdesc;  // [R] round blocks of the one-launch exact path
+    size_t step_smem = 0;                // its dynamic shared memory (largest round)
     uint32_t* d_zidx = nullptr;
     double2* d_zval = nullptr;
     uint32_t* d_zcount = nullptr;
@@ -320,6 +337,9 @@ void set_last_error(const std::string& s);
 
 // device entry points (sfft_exact.cu)
 cudaError_t launch_exact_round(const ExactArgs& a, uint32_t batch, size_t smem, cudaStream_t st, bool fp64);
+// rounds[0..R) with this launch's fields filled in; grid = sum over rounds of chunks x batch
+cudaError_t launch_exact_step(const ExactArgs* rounds, uint32_t R, uint32_t batch, size_t smem, cudaStream_t st,
+                              bool fp64);
 // persistent path: CTAs that fit on the device at `smem`, and the launch
 int exact_persistent_ctas(size_t smem, bool fp64);
 cudaError_t launch_exact_persistent(const PersistArgs& a, uint32_t ctas, size_t smem, cudaStream_t st, bool fp64);
