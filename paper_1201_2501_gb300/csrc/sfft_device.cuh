@@ -208,13 +208,44 @@ __device__ inline void rank_sort(const uint32_t* idx, const double2* val, uint32
 
 // In-place radix-2 decimation-in-time FFTs of H rows of B = 2^logB points held in bit-reversed
 // order: a_j <- sum_r a_r exp(-2 pi i j r / B) in natural order (Lemma "hashtobins", step 3).
-// All rows advance together, one barrier per stage.
+// The first min(5, logB) stages pair elements less than 32 apart: each warp holds 32 consecutive
+// elements (one per lane) and exchanges partners by shuffles, with the twiddles exp(-i pi k / 16),
+// k < 16, computed once per lane and shuffled to where they are needed.  The remaining stages run
+// in place in shared memory, all rows together, one barrier per stage.  Butterfly arithmetic and
+// twiddle values are the same in both forms.  Ends with a barrier.
 template <typename R>
 __device__ void block_fft_rows(typename Cx<R>::T* a, uint32_t H, uint32_t logB) {
     using C = typename Cx<R>::T;
     const uint32_t B = 1u << logB;
     const uint32_t halfB = B >> 1;
-    for (uint32_t st = 1; st <= logB; ++st) {
+    const uint32_t total = H * B, lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t S = logB < 5 ? logB : 5;
+    __syncthreads();  // the rows are in place
+    {
+        R ts, tc;
+        sincospi_r(-(R)(lane & 15u) / (R)16, &ts, &tc);  // exp(-i pi k / 16), k = lane mod 16
+        for (uint32_t g0 = warp * 32u; g0 < total; g0 += (uint32_t)kThreads) {
+            const uint32_t i = g0 + lane;
+            C v = i < total ? a[i] : mkc((R)0, (R)0);
+            for (uint32_t st = 1; st <= S; ++st) {
+                const uint32_t half = 1u << (st - 1);
+                const uint32_t pos = lane & (half - 1);
+                C w;
+                w.x = __shfl_sync(0xffffffffu, tc, (int)(pos << (5 - st)));
+                w.y = __shfl_sync(0xffffffffu, ts, (int)(pos << (5 - st)));
+                C p;
+                p.x = __shfl_xor_sync(0xffffffffu, v.x, (int)half);
+                p.y = __shfl_xor_sync(0xffffffffu, v.y, (int)half);
+                const bool upper = (lane & half) != 0;
+                const C bv = cmul(upper ? v : p, w);
+                const C av = upper ? p : v;
+                v = upper ? csub(av, bv) : cadd(av, bv);
+            }
+            if (i < total) a[i] = v;
+        }
+    }
+    __syncthreads();
+    for (uint32_t st = S + 1; st <= logB; ++st) {
         const uint32_t half = 1u << (st - 1);
         for (uint32_t idx = threadIdx.x; idx < H * halfB; idx += kThreads) {
             const uint32_t h = idx >> (logB - 1);
@@ -238,6 +269,11 @@ __device__ void block_fft_rows(typename Cx<R>::T* a, uint32_t H, uint32_t logB) 
 // each bin, ascending).  ent_bin must be filled.
 __device__ inline void bucket_entries(const uint32_t* ent_bin, uint32_t nz, uint32_t B, uint32_t* bin_cnt,
                                uint32_t* bin_start, uint32_t* bin_list, uint32_t* scan_tmp) {
+    if (nz == 0) {  // no entries: every bin list is empty
+        for (uint32_t j = threadIdx.x; j <= B; j += kThreads) bin_start[j] = 0;
+        __syncthreads();
+        return;
+    }
     for (uint32_t j = threadIdx.x; j <= B; j += kThreads) bin_cnt[j] = 0;
     __syncthreads();
     for (uint32_t e = threadIdx.x; e < nz; e += kThreads) atomicAdd(&bin_cnt[ent_bin[e]], 1u);

@@ -42,7 +42,7 @@ __device__ __forceinline__ const double* taps_of<double>(const ExactArgs& a) {
 // shared-memory layout of the finishing phase
 // ------------------------------------------------------------------------------------------------
 struct FinLayout {
-    size_t U, ent_idx, ent_bin, ent_val, ent_gain, ent_sub, bin_cnt, bin_start, bin_list, cand_idx, cand_bin, cand_gain,
+    size_t U, ent_idx, ent_bin, ent_val, ent_gain, ent_sub, ent_sub_f, bin_cnt, bin_start, bin_list, cand_idx, cand_bin, cand_gain,
         cand_val, srt_idx, srt_val, out_idx, out_val, keep, scan;
     size_t total;
 };
@@ -60,6 +60,7 @@ __host__ __device__ inline FinLayout fin_layout(uint32_t B, uint32_t H, uint32_t
     L.ent_val = fin_take(&off, (size_t)zcap * 16);
     L.ent_gain = fin_take(&off, (size_t)zcap * 8);
     L.ent_sub = fin_take(&off, (size_t)zcap * H * 16);
+    L.ent_sub_f = fin_take(&off, (size_t)zcap * H * 8);
     L.bin_cnt = fin_take(&off, (size_t)(B + 1) * 4);
     L.bin_start = fin_take(&off, (size_t)(B + 1) * 4);
     L.bin_list = fin_take(&off, (size_t)zcap * 4);
@@ -307,27 +308,34 @@ __device__ __forceinline__ int decode_bin(const DecodeCtx& d, uint32_t j, const 
     return decode_bin_fp32(d, j, u, list, nbin, ent_idx, ent_gain, oi, gout, above);
 }
 
-// Bin j's hashings after the subtraction of zhat: u_h = U_h - sum over the bin's entries e (in list
-// order) of sub[e H + h], summed in FP64.  The FP32 path keeps U_h itself when the bin holds no entry
-// and rounds the FP64 difference to FP32 otherwise.
-template <typename C, typename V>
-__device__ __forceinline__ void subtracted_bin(const C* U, uint32_t B, uint32_t H, uint32_t j, const uint32_t* list,
-                                               uint32_t nbin, const double2* sub, V* u) {
+// Bin j's hashings after the subtraction of zhat, for the decisions: u_h = U_h - sum over the bin's
+// entries e (in list order) of sub[e H + h], in the data path's precision (FP64 terms and sums for
+// the FP64 path; the terms rounded to FP32 and summed in FP32 for the FP32 path, whose bins carry
+// ~1e-6 of rounding).  The values of decoded bins are formed separately from subtracted_u0 in FP64.
+__device__ __forceinline__ void subtracted_bin(const double2* U, uint32_t B, uint32_t H, uint32_t j,
+                                               const uint32_t* list, uint32_t nbin, const double2* sub,
+                                               const float2* /*sub_f*/, double2* u) {
     for (uint32_t h = 0; h < H; ++h) {
-        const C v = U[h * B + j];
-        if (sizeof(V) == sizeof(float2) && nbin == 0) {
-            u[h].x = v.x;
-            u[h].y = v.y;
-            continue;
-        }
-        double2 w = make_double2((double)v.x, (double)v.y);
+        double2 w = U[h * B + j];
         for (uint32_t x = 0; x < nbin; ++x) {
             const uint32_t e = list[x];
             w.x -= sub[e * H + h].x;
             w.y -= sub[e * H + h].y;
         }
-        u[h].x = w.x;
-        u[h].y = w.y;
+        u[h] = w;
+    }
+}
+__device__ __forceinline__ void subtracted_bin(const float2* U, uint32_t B, uint32_t H, uint32_t j,
+                                               const uint32_t* list, uint32_t nbin, const double2* /*sub*/,
+                                               const float2* sub_f, float2* u) {
+    for (uint32_t h = 0; h < H; ++h) {
+        float2 w = U[h * B + j];
+        for (uint32_t x = 0; x < nbin; ++x) {
+            const uint32_t e = list[x];
+            w.x -= sub_f[e * H + h].x;
+            w.y -= sub_f[e * H + h].y;
+        }
+        u[h] = w;
     }
 }
 // u_0 of bin j after the subtraction, in FP64 (the first row of subtracted_bin, same order)
@@ -427,6 +435,65 @@ __device__ void gather_fold(const ExactArgs& a, const void* xrow, uint32_t xmask
     }
 }
 
+// Step 2 across chunks: U[h][brev(r)] = sum over chunks c, in order, of part[c][h][r].  Each thread
+// takes E elements of up to CM chunks with all their loads in flight at once (CM >= chunks), else
+// one element at a time in batches of 16.
+template <int E, int CM, typename C>
+__device__ __forceinline__ void sum_partials_batched(const C* part, uint32_t chunks, uint32_t H, uint32_t logB, C* U) {
+    const uint32_t B = 1u << logB, HB = H * B, shift_br = 32u - logB;
+    for (uint32_t i0 = threadIdx.x; i0 < HB; i0 += (uint32_t)kThreads * E) {
+        C v[E][CM];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const uint32_t i = i0 + (uint32_t)e * kThreads;
+            const uint32_t h = i >> logB, r = i & (B - 1);
+#pragma unroll
+            for (int c = 0; c < CM; ++c)
+                if (i < HB && (uint32_t)c < chunks) v[e][c] = __ldcg(part + ((size_t)c * H + h) * B + r);
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const uint32_t i = i0 + (uint32_t)e * kThreads;
+            if (i < HB) {
+                C sum;
+                sum.x = 0;
+                sum.y = 0;
+#pragma unroll
+                for (int c = 0; c < CM; ++c)
+                    if ((uint32_t)c < chunks) sum = cadd(sum, v[e][c]);
+                U[(i >> logB) * B + (__brev(i & (B - 1)) >> shift_br)] = sum;
+            }
+        }
+    }
+}
+template <typename C>
+__device__ void sum_partials(const C* part, uint32_t chunks, uint32_t H, uint32_t logB, C* U) {
+    constexpr bool f32 = sizeof(C) == sizeof(float2);  // FP64 bins: half the loads in flight (registers)
+    if (chunks <= 8) {
+        sum_partials_batched<f32 ? 2 : 1, 8>(part, chunks, H, logB, U);
+    } else if (chunks <= 16) {
+        sum_partials_batched<1, 16>(part, chunks, H, logB, U);
+    } else {
+        const uint32_t B = 1u << logB, shift_br = 32u - logB;
+        for (uint32_t i = threadIdx.x; i < H * B; i += kThreads) {
+            const uint32_t h = i >> logB, r = i & (B - 1);
+            C sum;
+            sum.x = 0;
+            sum.y = 0;
+            for (uint32_t c0 = 0; c0 < chunks; c0 += 16) {  // 16 loads in flight, summed in chunk order
+                C v[16];
+#pragma unroll
+                for (uint32_t q = 0; q < 16; ++q)
+                    if (c0 + q < chunks) v[q] = __ldcg(part + ((size_t)(c0 + q) * H + h) * B + r);
+#pragma unroll
+                for (uint32_t q = 0; q < 16; ++q)
+                    if (c0 + q < chunks) sum = cadd(sum, v[q]);
+            }
+            U[h * B + (__brev(r) >> shift_br)] = sum;
+        }
+    }
+}
+
 template <typename R>
 __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uint32_t b, unsigned char* smem) {
     using C = typename Cx<R>::T;
@@ -439,6 +506,7 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     double2* ent_val = reinterpret_cast<double2*>(smem + Ly.ent_val);
     double* ent_gain = reinterpret_cast<double*>(smem + Ly.ent_gain);
     double2* ent_sub = reinterpret_cast<double2*>(smem + Ly.ent_sub);
+    float2* ent_sub_f = reinterpret_cast<float2*>(smem + Ly.ent_sub_f);
     uint32_t* bin_cnt = reinterpret_cast<uint32_t*>(smem + Ly.bin_cnt);
     uint32_t* bin_start = reinterpret_cast<uint32_t*>(smem + Ly.bin_start);
     uint32_t* bin_list = reinterpret_cast<uint32_t*>(smem + Ly.bin_list);
@@ -457,6 +525,14 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     // zhat of this request and its per-entry subtraction terms (independent of the bins: done first,
     // in parallel, so that the bin threads below only add)
     // zhat is read through L2 only: in the one-launch path another CTA of this launch wrote it
+    // (the first entry of each thread is fetched together with the count)
+    const uint32_t zlim = a.bins_only ? a.e_nz : a.zcap;
+    uint32_t zi0 = 0;
+    double2 zv0 = make_double2(0.0, 0.0);
+    if (tid < zlim) {
+        zi0 = __ldcg(a.zidx + (size_t)s * a.zcap + tid);
+        zv0 = __ldcg(a.zval + (size_t)s * a.zcap + tid);
+    }
     const uint32_t nz = a.bins_only ? a.e_nz : min(__ldcg(a.zcount + s), a.zcap);
     DecodeCtx d;
     uint64_t ladder[kMaxHash];
@@ -464,31 +540,16 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     fill_ctx(d, a.n, a.nmask, B, a.logB, H, ladder, sigma, b, a.wtab, a.thr, a.iso_tol, a.gmin, a.ref_lo, a.ref_hi,
              a.ref_tol);
     for (uint32_t e = tid; e < nz; e += kThreads) {
-        const uint32_t i = __ldcg(a.zidx + (size_t)s * a.zcap + e);
+        const uint32_t i = e == tid ? zi0 : __ldcg(a.zidx + (size_t)s * a.zcap + e);
         ent_idx[e] = i;
-        ent_val[e] = __ldcg(a.zval + (size_t)s * a.zcap + e);
+        ent_val[e] = e == tid ? zv0 : __ldcg(a.zval + (size_t)s * a.zcap + e);
         uint32_t jb;
         const int32_t o = offset_of((sigma * (i - b)) & a.nmask, d, &jb);
         ent_bin[e] = jb;
         ent_gain[e] = a.wtab[o < 0 ? -o : o];
     }
     // step 2 (across chunks) and 3: partial folds summed in chunk order, bit-reversed, FFT
-    const C* part = reinterpret_cast<const C*>(a.part) + (size_t)s * a.part_stride;
-    const uint32_t shift_br = 32u - a.logB;
-    for (uint32_t i = tid; i < H * B; i += kThreads) {
-        const uint32_t h = i / B, r = i - h * B;
-        C sum = mkc((R)0, (R)0);
-        for (uint32_t c0 = 0; c0 < a.chunks; c0 += 16) {  // 16 loads in flight, summed in chunk order
-            C v[16];
-#pragma unroll
-            for (uint32_t q = 0; q < 16; ++q)
-                if (c0 + q < a.chunks) v[q] = __ldcg(part + ((size_t)(c0 + q) * H + h) * B + r);
-#pragma unroll
-            for (uint32_t q = 0; q < 16; ++q)
-                if (c0 + q < a.chunks) sum = cadd(sum, v[q]);
-        }
-        U[h * B + (__brev(r) >> shift_br)] = sum;
-    }
+    sum_partials(reinterpret_cast<const C*>(a.part) + (size_t)s * a.part_stride, a.chunks, H, a.logB, U);
     if (tid == 0) {
         s_nw = 0;
         s_above = 0;
@@ -501,7 +562,9 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         const uint32_t i = ent_idx[e];
         const double2 w = root_pow<R>(((a.a_base + a.a[h]) * sigma * i) & a.nmask, a.nmask);
         const double2 gz = make_double2(ent_gain[e] * ent_val[e].x, ent_gain[e] * ent_val[e].y);
-        ent_sub[q] = make_double2(gz.x * w.x - gz.y * w.y, gz.x * w.y + gz.y * w.x);
+        const double2 t = make_double2(gz.x * w.x - gz.y * w.y, gz.x * w.y + gz.y * w.x);
+        ent_sub[q] = t;
+        ent_sub_f[q] = make_float2((float)t.x, (float)t.y);
     }
     block_fft_rows<R>(U, H, a.logB);  // ends with a barrier
     bucket_entries(ent_bin, nz, B, bin_cnt, bin_start, bin_list, scan);
@@ -516,7 +579,7 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         C u[kMaxHash];
         const uint32_t* list = bin_list + bin_start[j];
         const uint32_t nbin = bin_start[j + 1] - bin_start[j];
-        subtracted_bin(U, B, H, j, list, nbin, ent_sub, u);
+        subtracted_bin(U, B, H, j, list, nbin, ent_sub, ent_sub_f, u);
         uint32_t oi = 0;
         double gain = 1.0;
         bool above;
