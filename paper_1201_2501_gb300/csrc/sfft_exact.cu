@@ -228,19 +228,25 @@ __device__ __forceinline__ float phase01_f(float2 z) {
 }
 __device__ __forceinline__ float pow2_f(int e) { return __int_as_float((127 + e) << 23); }  // 2^e, |e| < 127
 
-__device__ int decode_bin_fp32(const DecodeCtx& d, uint32_t j, const float2* u, const uint32_t* list, uint32_t nbin,
-                               const uint32_t* ent_idx, const double* ent_gain, uint32_t* oi, double* gout,
-                               bool* above) {
+// Every loop over hashings is unrolled to kMaxHash with compile-time indices, so u[] and the
+// phases stay in registers.
+__device__ __forceinline__ int decode_bin_fp32(const DecodeCtx& d, uint32_t j, const float2* u, const uint32_t* list,
+                                               uint32_t nbin, const uint32_t* ent_idx, const double* ent_gain,
+                                               uint32_t* oi, double* gout, bool* above) {
     const float mag0 = hypotf(u[0].x, u[0].y);
     const uint32_t L = d.H - 1;
     *above = false;
     if (!(mag0 > d.thr_f)) {
         // re-estimation of a known value: exactly one entry of the bin must explain the residual
         if (nbin == 0 || !(mag0 > d.ref_lo_f && mag0 <= d.ref_hi_f)) return 0;
-        float th[kMaxHash];
-        for (uint32_t l = 0; l < L; ++l) {
-            if (fabsf(hypotf(u[l + 1].x, u[l + 1].y) - mag0) > 0.25f * mag0) return 0;
-            th[l] = phase01_f(mul_conj_f(u[0], u[l + 1]));
+        float th[kMaxHash - 1];
+#pragma unroll
+        for (int l = 0; l < kMaxHash - 1; ++l) {
+            th[l] = 0.0f;
+            if ((uint32_t)l < L) {
+                if (fabsf(hypotf(u[l + 1].x, u[l + 1].y) - mag0) > 0.25f * mag0) return 0;
+                th[l] = phase01_f(mul_conj_f(u[0], u[l + 1]));
+            }
         }
         uint32_t matches = 0, who = 0;
         double gw = 1.0;
@@ -250,11 +256,14 @@ __device__ int decode_bin_fp32(const DecodeCtx& d, uint32_t j, const float2* u, 
             const double gain = ent_gain[e];
             if (!(gain >= d.gmin)) continue;
             bool ok = true;
-            for (uint32_t l = 0; l < L && ok; ++l) {
-                const uint32_t ph = (d.shift[l] * d.sigma * i) & d.nmask;
-                float dist = fabsf(th[l] - (float)ph * d.inv_n_f);
-                if (dist > 0.5f) dist = 1.0f - dist;
-                ok = dist * 6.28318530717958648f < d.ref_tol_f;
+#pragma unroll
+            for (int l = 0; l < kMaxHash - 1; ++l) {
+                if ((uint32_t)l < L && ok) {
+                    const uint32_t ph = (d.shift[l] * d.sigma * i) & d.nmask;
+                    float dist = fabsf(th[l] - (float)ph * d.inv_n_f);
+                    if (dist > 0.5f) dist = 1.0f - dist;
+                    ok = dist * 6.28318530717958648f < d.ref_tol_f;
+                }
             }
             if (ok) {
                 ++matches;
@@ -270,10 +279,20 @@ __device__ int decode_bin_fp32(const DecodeCtx& d, uint32_t j, const float2* u, 
     *above = true;
     // location ladder, coarsest shift first (as decode_bin_fp64).  Products with powers of two are
     // exact; c < 2^logM <= 2^30 stays an integer held in 64 bits.
-    uint32_t logM = d.logNp - d.logR[L - 1];
-    const float th = phase01_f(mul_conj_f(u[0], u[L]));
+    float2 uL = u[1];
+    uint32_t logRL = d.logR[0];
+#pragma unroll
+    for (int l = 2; l < kMaxHash; ++l)
+        if ((uint32_t)l == L) {
+            uL = u[l];
+            logRL = d.logR[l - 1];
+        }
+    uint32_t logM = d.logNp - logRL;
+    const float th = phase01_f(mul_conj_f(u[0], uL));
     uint64_t c = (uint64_t)(int64_t)floorf(th * pow2_f((int)logM) + 0.5f) & ((uint64_t(1) << logM) - 1);
-    for (int l = (int)L - 2; l >= 0; --l) {
+#pragma unroll
+    for (int l = kMaxHash - 3; l >= 0; --l) {
+        if (l > (int)L - 2) continue;
         const uint32_t logMp = d.logNp - d.logR[l];
         const uint32_t logRatio = logMp - logM;
         const float thl = phase01_f(mul_conj_f(u[0], u[l + 1]));
@@ -288,8 +307,9 @@ __device__ int decode_bin_fp32(const DecodeCtx& d, uint32_t j, const float2* u, 
     const uint32_t p = (j * d.Np + (uint32_t)o) & d.nmask;
     const uint32_t si = (p + d.sb) & d.nmask;
     const uint32_t i = (d.sigma_inv * si) & d.nmask;
-    for (uint32_t l = 0; l < L; ++l)
-        if (fabsf(hypotf(u[l + 1].x, u[l + 1].y) - mag0) > d.iso_tol_f * mag0) return 0;
+#pragma unroll
+    for (int l = 0; l < kMaxHash - 1; ++l)
+        if ((uint32_t)l < L && fabsf(hypotf(u[l + 1].x, u[l + 1].y) - mag0) > d.iso_tol_f * mag0) return 0;
     const double gain = d.wtab[o < 0 ? -o : o];
     if (!(gain >= d.gmin)) return 0;
     *oi = i;
@@ -328,14 +348,16 @@ __device__ __forceinline__ void subtracted_bin(const double2* U, uint32_t B, uin
 __device__ __forceinline__ void subtracted_bin(const float2* U, uint32_t B, uint32_t H, uint32_t j,
                                                const uint32_t* list, uint32_t nbin, const double2* /*sub*/,
                                                const float2* sub_f, float2* u) {
-    for (uint32_t h = 0; h < H; ++h) {
-        float2 w = U[h * B + j];
-        for (uint32_t x = 0; x < nbin; ++x) {
-            const uint32_t e = list[x];
-            w.x -= sub_f[e * H + h].x;
-            w.y -= sub_f[e * H + h].y;
-        }
-        u[h] = w;
+#pragma unroll
+    for (int h = 0; h < kMaxHash; ++h) u[h] = (uint32_t)h < H ? U[h * B + j] : make_float2(0.0f, 0.0f);
+    for (uint32_t x = 0; x < nbin; ++x) {
+        const float2* t = sub_f + list[x] * H;
+#pragma unroll
+        for (int h = 0; h < kMaxHash; ++h)
+            if ((uint32_t)h < H) {
+                u[h].x -= t[h].x;
+                u[h].y -= t[h].y;
+            }
     }
 }
 // u_0 of bin j after the subtraction, in FP64 (the first row of subtracted_bin, same order)
@@ -355,6 +377,23 @@ __device__ __forceinline__ double2 subtracted_u0(const C* U, uint32_t H, uint32_
 // ------------------------------------------------------------------------------------------------
 // The round kernel
 // ------------------------------------------------------------------------------------------------
+// Arrival of this CTA at a counter whose last arrival (the target-th) does the follow-up work.
+// Returns 1 in every thread of the last arriving CTA.  Only thread 0 fences: the barrier before its
+// fence orders every thread's stores before it (the fence is cumulative), and the barrier after it
+// orders its fence before every thread's loads (the same pattern as a grid-wide barrier).  Data
+// written by other CTAs of the same launch is then read through L2 (ld.global.cg).
+__device__ __forceinline__ uint32_t arrive(uint32_t* counter, uint32_t target) {
+    __shared__ uint32_t s_arrive_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t last = atomicAdd(counter, 1u) + 1u == target ? 1u : 0u;
+        if (last) __threadfence();
+        s_arrive_last = last;
+    }
+    __syncthreads();
+    return s_arrive_last;
+}
 template <typename R>
 __device__ void gather_fold(const ExactArgs& a, const void* xrow, uint32_t xmask, uint32_t s, uint32_t c,
                             uint32_t sigma, uint32_t b, unsigned char* smem) {
@@ -584,10 +623,19 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         double gain = 1.0;
         bool above;
         const int kind = decode_bin(d, j, u, list, nbin, ent_idx, ent_gain, &oi, &gain, &above);
-        if (above) atomicAdd(&s_above, 1u);
-        if (kind == 1) atomicAdd(&s_kept, 1u);
+        // counts and candidate slots, one shared-memory atomic per warp and counter
+        const unsigned m = __activemask();
+        const unsigned ma = __ballot_sync(m, above), mk = __ballot_sync(m, kind == 1), mw = __ballot_sync(m, kind != 0);
+        const uint32_t lane = tid & 31u, leader = (uint32_t)__ffs((int)m) - 1u;
+        uint32_t base = 0;
+        if (lane == leader) {
+            if (ma) atomicAdd(&s_above, (uint32_t)__popc((int)ma));
+            if (mk) atomicAdd(&s_kept, (uint32_t)__popc((int)mk));
+            if (mw) base = atomicAdd(&s_nw, (uint32_t)__popc((int)mw));
+        }
+        base = __shfl_sync(m, base, (int)leader);
         if (kind != 0) {
-            const uint32_t slot = atomicAdd(&s_nw, 1u);
+            const uint32_t slot = base + (uint32_t)__popc((int)(mw & ((1u << lane) - 1u)));
             cand_idx[slot] = oi;
             cand_bin[slot] = j;
             cand_gain[slot] = gain;
@@ -678,7 +726,6 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
 template <typename R>
 __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_round(const ExactArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ uint32_t s_last;
     const uint32_t s = a.req_base + blockIdx.y, c = blockIdx.x;
     const ReqView rq = req_view(a.reqs, a.x, a.n * sizeof(typename Cx<R>::T), a.seed, s, a.nmask);
     uint32_t sigma, b;
@@ -690,12 +737,7 @@ __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_round
     }
     gather_fold<R>(a, rq.x, rq.xmask, s, c, sigma, b, smem);
     // arrival: the last CTA of request s finishes the round (nobody waits)
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(a.counter + s, 1u) == a.chunks - 1) ? 1u : 0u;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    if (arrive(a.counter + s, a.chunks) == 0) return;
     finish_round<R>(a, s, sigma, b, a.fin_scratch ? a.fin_scratch + (size_t)s * a.fin_stride : smem);
     if (threadIdx.x == 0) a.counter[s] = 0;
 }
@@ -706,7 +748,6 @@ __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_round
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_step(const __grid_constant__ StepParams<NR> sp) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ uint32_t s_last;
     const uint32_t tid = threadIdx.x;
     uint32_t t = 0;
     while (t + 1 < sp.R && blockIdx.x >= sp.seg[t + 1]) ++t;
@@ -718,21 +759,15 @@ __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_step(
     uint32_t sigma, b;
     exact_hash(rq.seed, rq.id, t, a->nmask, &sigma, &b);
     gather_fold<R>(*a, rq.x, rq.xmask, s, c, sigma, b, smem);
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(a->counter + s, 1u) + 1u == a->chunks + (t > 0 ? 1u : 0u)) ? 1u : 0u;
-    __syncthreads();
-    while (s_last) {
-        __threadfence();
+    if (arrive(a->counter + s, a->chunks + (t > 0 ? 1u : 0u)) == 0) return;
+    for (;;) {
         finish_round<R>(*a, s, sigma, b, a->fin_scratch ? a->fin_scratch + (size_t)s * a->fin_stride : smem);
-        __threadfence();  // zhat of round t is visible before round t + 1 counts this arrival
-        __syncthreads();
         if (tid == 0) a->counter[s] = 0;  // every arrival of round t has happened
         if (t + 1 >= sp.R) break;
         a = &sp.r[++t];
-        if (tid == 0) s_last = (atomicAdd(a->counter + s, 1u) == a->chunks) ? 1u : 0u;
-        __syncthreads();
-        if (s_last) exact_hash(rq.seed, rq.id, t, a->nmask, &sigma, &b);
+        // zhat of round t is published by the arrival at round t + 1's counter
+        if (arrive(a->counter + s, a->chunks + 1u) == 0) break;
+        exact_hash(rq.seed, rq.id, t, a->nmask, &sigma, &b);
     }
 }
 
@@ -763,7 +798,6 @@ __global__ void __launch_bounds__(kThreads, SFFT_PERSIST_MIN_BLOCKS) k_exact_per
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) ExactArgs sa;
     __shared__ unsigned long long s_item;
-    __shared__ uint32_t s_last;
     const uint32_t tid = threadIdx.x;
     for (;;) {
         // take the next item and wait (bounded) until it is published
@@ -820,16 +854,11 @@ __global__ void __launch_bounds__(kThreads, SFFT_PERSIST_MIN_BLOCKS) k_exact_per
         uint32_t sigma, b;
         exact_hash(rq.seed, rq.id, a.round, a.nmask, &sigma, &b);
         gather_fold<R>(a, rq.x, rq.xmask, 0, c, sigma, b, smem);
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) s_last = (atomicAdd(a.counter, 1u) == a.chunks - 1) ? 1u : 0u;
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
+        if (arrive(a.counter, a.chunks)) {
             finish_round<R>(a, 0, sigma, b, a.fin_scratch ? a.fin_scratch : smem);
-            __threadfence();
-            __syncthreads();
+            __syncthreads();  // every thread's zhat and output stores precede thread 0's release
             if (tid == 0) {
+                __threadfence();
                 *a.counter = 0;
                 if (t + 1 < pa.req_rounds[r]) {  // publish the request's next round
                     const uint32_t nch = pa.rdesc[pa.req_rd0[r] + t + 1].chunks;
