@@ -171,7 +171,7 @@ def profiled_traffic():
 
 def launch_groups(batch, streams):
     """Stream groups sfft_execute splits an exact-mode batch into (one k_exact_step launch each per step)."""
-    g = streams if streams else 4
+    g = streams if streams else 1
     g = min(g, 8, batch)
     return 1 if batch < 8 else g
 
@@ -1018,8 +1018,9 @@ def main():
                     help="exact: the n=2^22, k=64 benchmark; general: the noisy n=2^22, k=256 case as the timed step")
     ap.add_argument("--mixed", action="store_true", help="also time the uneven mixed batch (1024 requests)")
     ap.add_argument("--mixed-requests", type=int, default=1024)
-    ap.add_argument("--path", default="rounds", choices=["rounds", "persistent"],
-                    help="per-round launches (one kernel per round and stream group) or one persistent launch")
+    ap.add_argument("--path", default="step", choices=["step", "persistent"],
+                    help="one k_exact_step launch per step and stream group (all rounds), or the persistent "
+                         "work-queue launch")
     ap.add_argument("--precision-table", action="store_true", help="print the precision-variant table instead")
     ap.add_argument("--precision-batch", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=2000)

@@ -409,7 +409,7 @@ void sfft_params_default(sfft_params* p, uint64_t n, uint32_t k, uint32_t mode) 
     p->R_est = 5;
     p->s = 0.25;
     p->est_gmin = 0.25;
-    p->streams = 4;
+    p->streams = mode == SFFT_GENERAL ? 4 : 1;  // exact: one launch per batch already overlaps its rounds
     p->gain = 0;
     p->chunk_taps = 2048;
 }
