@@ -274,6 +274,24 @@ __device__ inline void bucket_entries(const uint32_t* ent_bin, uint32_t nz, uint
         __syncthreads();
         return;
     }
+    if (nz <= (uint32_t)kThreads) {
+        // one entry per thread: its place in bin_list is the number of entries before it in (bin, id)
+        // order; scan_tmp receives the bins in that order, and bin_start[j] counts those below j
+        if (threadIdx.x < nz) {
+            const uint32_t e0 = threadIdx.x, b0 = ent_bin[e0];
+            uint32_t r = 0;
+            for (uint32_t e = 0; e < nz; ++e) {
+                const uint32_t be = ent_bin[e];
+                r += (be < b0 || (be == b0 && e < e0)) ? 1u : 0u;
+            }
+            bin_list[r] = e0;
+            scan_tmp[r] = b0;
+        }
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j <= B; j += kThreads) bin_start[j] = lower_bound_u32(scan_tmp, nz, j);
+        __syncthreads();
+        return;
+    }
     for (uint32_t j = threadIdx.x; j <= B; j += kThreads) bin_cnt[j] = 0;
     __syncthreads();
     for (uint32_t e = threadIdx.x; e < nz; e += kThreads) atomicAdd(&bin_cnt[ent_bin[e]], 1u);

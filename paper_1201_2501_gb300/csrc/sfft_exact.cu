@@ -278,7 +278,8 @@ __device__ __forceinline__ int decode_bin_fp32(const DecodeCtx& d, uint32_t j, c
     }
     *above = true;
     // location ladder, coarsest shift first (as decode_bin_fp64).  Products with powers of two are
-    // exact; c < 2^logM <= 2^30 stays an integer held in 64 bits.
+    // exact; c < 2^logM <= 2^30 and every rounded quantity fits 32 bits, so the conversions are the
+    // 32-bit ones.
     float2 uL = u[1];
     uint32_t logRL = d.logR[0];
 #pragma unroll
@@ -289,19 +290,19 @@ __device__ __forceinline__ int decode_bin_fp32(const DecodeCtx& d, uint32_t j, c
         }
     uint32_t logM = d.logNp - logRL;
     const float th = phase01_f(mul_conj_f(u[0], uL));
-    uint64_t c = (uint64_t)(int64_t)floorf(th * pow2_f((int)logM) + 0.5f) & ((uint64_t(1) << logM) - 1);
+    uint32_t c = (uint32_t)__float2int_rd(th * pow2_f((int)logM) + 0.5f) & ((1u << logM) - 1u);
 #pragma unroll
     for (int l = kMaxHash - 3; l >= 0; --l) {
         if (l > (int)L - 2) continue;
         const uint32_t logMp = d.logNp - d.logR[l];
         const uint32_t logRatio = logMp - logM;
         const float thl = phase01_f(mul_conj_f(u[0], u[l + 1]));
-        const float y = thl * pow2_f((int)logRatio) - (float)c * pow2_f(-(int)logM);
-        const int64_t h = (int64_t)floorf(y + 0.5f) & (int64_t)((uint64_t(1) << logRatio) - 1);
-        c += (uint64_t(1) << logM) * (uint64_t)h;
+        const float y = thl * pow2_f((int)logRatio) - __uint2float_rn(c) * pow2_f(-(int)logM);
+        const uint32_t h = (uint32_t)__float2int_rd(y + 0.5f) & ((1u << logRatio) - 1u);
+        c += h << logM;
         logM = logMp;
     }
-    const uint32_t q = (uint32_t)c;
+    const uint32_t q = c;
     const uint32_t dd = (q + d.Np - (d.sb & (d.Np - 1)) + (d.Np >> 1)) & (d.Np - 1);
     const int32_t o = (int32_t)dd - (int32_t)(d.Np >> 1);
     const uint32_t p = (j * d.Np + (uint32_t)o) & d.nmask;
@@ -573,11 +574,16 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         zv0 = __ldcg(a.zval + (size_t)s * a.zcap + tid);
     }
     const uint32_t nz = a.bins_only ? a.e_nz : min(__ldcg(a.zcount + s), a.zcap);
-    DecodeCtx d;
-    uint64_t ladder[kMaxHash];
-    for (int l = 0; l < kMaxHash; ++l) ladder[l] = l + 1 < kMaxHash ? a.shift64[l + 1] : 0;
-    fill_ctx(d, a.n, a.nmask, B, a.logB, H, ladder, sigma, b, a.wtab, a.thr, a.iso_tol, a.gmin, a.ref_lo, a.ref_hi,
-             a.ref_tol);
+    // the decode context is the same for every thread: one copy in shared memory (registers would
+    // hold it only by spilling it to local memory)
+    __shared__ DecodeCtx d;
+    if (tid == 0) {
+        uint64_t ladder[kMaxHash];
+        for (int l = 0; l < kMaxHash; ++l) ladder[l] = l + 1 < kMaxHash ? a.shift64[l + 1] : 0;
+        fill_ctx(d, a.n, a.nmask, B, a.logB, H, ladder, sigma, b, a.wtab, a.thr, a.iso_tol, a.gmin, a.ref_lo,
+                 a.ref_hi, a.ref_tol);
+    }
+    __syncthreads();
     for (uint32_t e = tid; e < nz; e += kThreads) {
         const uint32_t i = e == tid ? zi0 : __ldcg(a.zidx + (size_t)s * a.zcap + e);
         ent_idx[e] = i;
@@ -919,9 +925,11 @@ __global__ void __launch_bounds__(kThreads) k_exact_decode(const DecodeArgs a) {
     uint32_t* srt_idx = reinterpret_cast<uint32_t*>(smem + Ly.srt_idx);
     double2* srt_val = reinterpret_cast<double2*>(smem + Ly.srt_val);
     uint32_t* scan = reinterpret_cast<uint32_t*>(smem + Ly.scan);
-    DecodeCtx d;
-    fill_ctx(d, a.n, a.nmask, B, a.logB, a.H, a.shift64, a.sigma, a.b, a.wtab, a.thr, a.iso_tol, a.gmin, a.ref_lo,
-             a.ref_hi, a.ref_tol);
+    __shared__ DecodeCtx d;
+    if (tid == 0)
+        fill_ctx(d, a.n, a.nmask, B, a.logB, a.H, a.shift64, a.sigma, a.b, a.wtab, a.thr, a.iso_tol, a.gmin, a.ref_lo,
+                 a.ref_hi, a.ref_tol);
+    __syncthreads();
     for (uint32_t i = tid; i < a.H * B; i += kThreads) U[i] = a.u[i];
     for (uint32_t e = tid; e < a.nz; e += kThreads) {
         const uint32_t i = a.zidx[e];
