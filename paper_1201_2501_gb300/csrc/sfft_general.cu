@@ -10,8 +10,8 @@
 //   2. k_gen_finish   every (hashing group, request): partials summed in order, B-point FFT
 //                     (step 3), recovered coefficients subtracted in FP64 (step 4), bins stored;
 //                     for a LocateInner pair also c_j = phase(u_j / u'_j);
-//   3. k_gen_locate   every (bin, request), one thread per bin: LocateSignal's levels in order,
-//                     votes, regions, the bin's candidate for the list L;
+//   3. k_gen_locate   every (bin, request), t threads per bin (one per subregion): LocateSignal's
+//                     levels in order, votes, regions, the bin's candidate for the list L;
 //   4. k_gen_estimate every request: EstimateValues' medians, the top k', zhat += w_J.
 // Reductions run in a fixed order; results are bit-reproducible.
 #include <cuda_runtime.h>
@@ -310,43 +310,62 @@ __device__ __forceinline__ bool vote_hit(const VoteBounds& v, uint64_t e, uint64
 
 // Votes of bin j at one level, then its region update (the four consecutive subregions with the
 // most votes among those with a majority; bottom when no subregion has one).
-// phase(q) returns c_j of LocateInner round q; beta[q] its beta.
-template <typename PhaseFn>
-__device__ void locate_bin(uint32_t t, uint32_t nrep, const uint64_t* beta, PhaseFn phase, uint64_t sb_fp,
-                           uint64_t w_fp, uint32_t logM, double s, int64_t hw_fix, uint64_t& l_fp, uint8_t& valid,
-                           uint32_t* votes_out) {
-    uint8_t v[kMaxT];
-    for (uint32_t q = 0; q < t; ++q) v[q] = 0;
+// phase(q) returns c_j of LocateInner round q; beta[q] its beta.  T = t subregions, a compile-time
+// constant so that the vote counters live in registers.
+template <int T, typename PhaseFn>
+__device__ __forceinline__ void locate_bin_t(uint32_t nrep, const uint64_t* beta, PhaseFn phase, uint64_t sb_fp,
+                                             uint64_t w_fp, uint32_t logM, double s, int64_t hw_fix, uint64_t& l_fp,
+                                             uint8_t& valid, uint32_t* votes_out) {
+    uint32_t v[T];
+#pragma unroll
+    for (int q = 0; q < T; ++q) v[q] = 0;
     const uint64_t M = uint64_t(1) << logM;
     const uint64_t mask = M - 1;
-    const uint64_t half_step = w_fp / (2 * (uint64_t)t), step = w_fp / t;
+    const uint64_t half_step = w_fp / (2 * (uint64_t)T), step = w_fp / T;
     for (uint32_t r = 0; r < nrep; ++r) {
         const VoteBounds vb = vote_bounds(phase(r), hw_fix, logM);
         // e_q = beta (m_q + sigma b) mod M, m_q = l + (2q - 1) w / 2t, advanced by beta w / t
         uint64_t e = (beta[r] * ((l_fp + half_step + sb_fp) & mask)) & mask;
         const uint64_t de = (beta[r] * step) & mask;
-        for (uint32_t q = 0; q < t; ++q) {
+#pragma unroll
+        for (int q = 0; q < T; ++q) {
             if (vote_hit(vb, e, M, s)) v[q] += 1;
             e = (e + de) & mask;
         }
     }
-    if (votes_out)
-        for (uint32_t q = 0; q < t; ++q) votes_out[q] = v[q];
+    if (votes_out) {
+#pragma unroll
+        for (int q = 0; q < T; ++q) votes_out[q] = v[q];
+    }
     bool any = false;
-    for (uint32_t q = 0; q < t; ++q) any = any || 2u * v[q] > nrep;
+#pragma unroll
+    for (int q = 0; q < T; ++q) any = any || 2u * v[q] > nrep;
     if (!any) {
         valid = 0;
         return;
     }
     uint32_t best = 0, best_sum = 0;
-    for (uint32_t q0 = 0; q0 + 4 <= t; ++q0) {
-        const uint32_t sum = (uint32_t)v[q0] + v[q0 + 1] + v[q0 + 2] + v[q0 + 3];
+#pragma unroll
+    for (int q0 = 0; q0 + 4 <= T; ++q0) {
+        const uint32_t sum = v[q0] + v[q0 + 1] + v[q0 + 2] + v[q0 + 3];
         if (q0 == 0 || sum > best_sum) {
-            best = q0;
+            best = (uint32_t)q0;
             best_sum = sum;
         }
     }
     l_fp = (l_fp + (uint64_t)best * step) & mask;
+}
+template <typename PhaseFn>
+__device__ void locate_bin(uint32_t t, uint32_t nrep, const uint64_t* beta, PhaseFn phase, uint64_t sb_fp,
+                           uint64_t w_fp, uint32_t logM, double s, int64_t hw_fix, uint64_t& l_fp, uint8_t& valid,
+                           uint32_t* votes_out) {
+    // the schedule admits t in {8, 16, 32} (a power of two in [8, kMaxT])
+    if (t == 8)
+        locate_bin_t<8>(nrep, beta, phase, sb_fp, w_fp, logM, s, hw_fix, l_fp, valid, votes_out);
+    else if (t == 16)
+        locate_bin_t<16>(nrep, beta, phase, sb_fp, w_fp, logM, s, hw_fix, l_fp, valid, votes_out);
+    else
+        locate_bin_t<32>(nrep, beta, phase, sb_fp, w_fp, logM, s, hw_fix, l_fp, valid, votes_out);
 }
 
 size_t general_locate_smem(uint32_t B) {
@@ -375,25 +394,38 @@ __device__ uint32_t sort_unique_u32(uint32_t* key, uint32_t m, uint32_t* tmp, ui
     return total;
 }
 
-// LocateSignal for one bin per thread: the bins of a request are independent until L is formed, so
-// a request spreads over ceil(B / kThreads) CTAs.  The candidate of bin j (pi^{-1} of the integer
-// nearest the centre of its last region, or ~0 for bottom) goes to L[s B + j]; EstimateValues sorts
-// and de-duplicates them.
+// LocateSignal with t threads per bin, thread q owning subregion q: a CTA holds kThreads / t bins of
+// one request (the bins are independent until L is formed).  Per level, the vote arcs of the R_loc
+// rounds are formed once per bin (by threads q < R_loc, in shared memory), every thread counts the
+// votes of its subregion over the rounds, and thread 0 of the bin takes the level's decision from
+// the t counts (the decision of locate_bin_t, on the same integers).  The candidate of bin j
+// (pi^{-1} of the integer nearest the centre of its last region, or ~0 for bottom) goes to
+// L[s B + j]; EstimateValues sorts and de-duplicates them.
+constexpr int kLocBins = kThreads / 8;  // bins per CTA at the smallest t
 __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
     __shared__ uint64_t s_beta[kMaxRloc];
+    __shared__ VoteBounds s_vb[kLocBins][kMaxRloc];
+    __shared__ uint64_t s_l[kLocBins];
+    __shared__ uint32_t s_valid[kLocBins];
+    __shared__ uint32_t s_votes[kThreads];
     const uint32_t s = a.req_base + blockIdx.y, tid = threadIdx.x;
-    const uint32_t j = blockIdx.x * kThreads + tid;
+    const uint32_t t = a.t;  // 8, 16 or 32 (the schedule checks it)
+    const uint32_t q = tid & (t - 1), lb = tid / t, nb = kThreads / t;
     const uint32_t B = a.B;
+    const uint32_t j = blockIdx.x * nb + lb;
     const ReqView rq = gen_req(a, s);
     uint32_t sigma, b;
     locate_sigma_b(rq.seed, rq.id, a.round, a.nmask, &sigma, &b);
     const uint64_t n = a.n, Np = n >> a.logB;
     const uint32_t logM = (uint32_t)(63 - __clzll((long long)n)) + kFracBits;
+    const uint64_t M = uint64_t(1) << logM, mask = M - 1;
     const int64_t hw_fix = vote_halfwidth(a.s, logM);
     const uint64_t sb_fp = ((uint64_t)((sigma * b) & a.nmask)) << kFracBits;
-    // the region of bin j starts centred on the bin: [j n/B - n/2B, + n/B)
-    uint64_t l_fp = ((((uint64_t)j * Np) + n - Np / 2) & (n - 1)) << kFracBits;
-    uint8_t valid = j < B ? 1 : 0;
+    if (q == 0) {
+        // the region of bin j starts centred on the bin: [j n/B - n/2B, + n/B)
+        s_l[lb] = ((((uint64_t)j * Np) + n - Np / 2) & (n - 1)) << kFracBits;
+        s_valid[lb] = j < B ? 1u : 0u;
+    }
     const double* phase = a.phase + (size_t)s * a.phase_stride;
     for (uint32_t D = 0; D < a.dmax; ++D) {
         __syncthreads();
@@ -403,18 +435,50 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
             inner_a_beta(rq.seed, rq.id, a.round, D * a.R_loc + tid, a.nmask, a.beta_lo[D], a.beta_hi[D], &aa, &be);
             s_beta[tid] = be;
         }
-        __syncthreads();
-        if (!valid) continue;
-        const uint64_t w_fp = (Np << kFracBits) >> ((uint64_t)D * a.logtp);
+        const bool valid = s_valid[lb] != 0;
         const double* ph = phase + (size_t)D * a.R_loc * B;
-        locate_bin(a.t, a.R_loc, s_beta, [&](uint32_t r) { return ph[(size_t)r * B + j]; }, sb_fp, w_fp, logM, a.s,
-                   hw_fix, l_fp, valid, nullptr);
+        if (valid)
+            for (uint32_t r = q; r < a.R_loc; r += t) s_vb[lb][r] = vote_bounds(ph[(size_t)r * B + j], hw_fix, logM);
+        __syncthreads();
+        const uint64_t w_fp = (Np << kFracBits) >> ((uint64_t)D * a.logtp);
+        const uint64_t half_step = w_fp / (2 * (uint64_t)t), step = w_fp / t;
+        uint32_t v = 0;
+        if (valid) {
+            const uint64_t l_fp = s_l[lb];
+            for (uint32_t r = 0; r < a.R_loc; ++r) {
+                // e_q = beta (m_q + sigma b) mod M, m_q = l + (2q - 1) w / 2t
+                const uint64_t e0 = (s_beta[r] * ((l_fp + half_step + sb_fp) & mask)) & mask;
+                const uint64_t de = (s_beta[r] * step) & mask;
+                if (vote_hit(s_vb[lb][r], (e0 + (uint64_t)q * de) & mask, M, a.s)) ++v;
+            }
+        }
+        s_votes[tid] = v;
+        __syncthreads();
+        if (q == 0 && valid) {
+            const uint32_t* vv = s_votes + lb * t;
+            bool any = false;
+            for (uint32_t qq = 0; qq < t; ++qq) any = any || 2u * vv[qq] > a.R_loc;
+            if (!any) {
+                s_valid[lb] = 0;
+            } else {
+                uint32_t best = 0, best_sum = 0;
+                for (uint32_t q0 = 0; q0 + 4 <= t; ++q0) {
+                    const uint32_t sum = vv[q0] + vv[q0 + 1] + vv[q0 + 2] + vv[q0 + 3];
+                    if (q0 == 0 || sum > best_sum) {
+                        best = q0;
+                        best_sum = sum;
+                    }
+                }
+                s_l[lb] = (s_l[lb] + (uint64_t)best * step) & mask;
+            }
+        }
     }
-    if (j >= B) return;
+    __syncthreads();
+    if (q != 0 || j >= B) return;
     uint32_t cand = 0xFFFFFFFFu;
-    if (valid) {
+    if (s_valid[lb]) {
         const uint64_t wlast = (Np << kFracBits) >> ((uint64_t)a.dmax * a.logtp);
-        const uint32_t tau = (uint32_t)(((l_fp + wlast / 2 + (1ull << (kFracBits - 1))) >> kFracBits) & (n - 1));
+        const uint32_t tau = (uint32_t)(((s_l[lb] + wlast / 2 + (1ull << (kFracBits - 1))) >> kFracBits) & (n - 1));
         cand = ((inverse_odd(sigma) & a.nmask) * tau + b) & a.nmask;
     }
     a.L[(size_t)s * B + j] = cand;
@@ -729,7 +793,7 @@ cudaError_t launch_general_round(const GenArgs& a, uint32_t batch, const General
     if (e != cudaSuccess) return e;
     k_gen_finish<<<dim3(r.ngroups, batch), kThreads, r.fin_global ? 0 : r.smem_finish, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_gen_locate<<<dim3((r.B + kThreads - 1) / kThreads, batch), kThreads, 0, st>>>(a);
+    k_gen_locate<<<dim3((r.B * r.t + kThreads - 1) / kThreads, batch), kThreads, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_gen_estimate<<<batch, kThreads, r.est_global ? 0 : r.smem_estimate, st>>>(a);
     return cudaGetLastError();
