@@ -51,6 +51,7 @@ void free_plan(sfft_plan_s* pl) {
     cudaFree(pl->d_taps32);
     cudaFree(pl->d_taps64);
     cudaFree(pl->d_wtab);
+    cudaFree(pl->d_tw);
     cudaFree(pl->d_part);
     cudaFree(pl->d_counter);
     cudaFree(pl->d_zidx);
@@ -256,6 +257,8 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         SFFT_ALLOC(pl->d_bins, pl->bins_stride * max_batch * sizeof(double2));
         SFFT_ALLOC(pl->d_phase, pl->phase_stride * max_batch * sizeof(double));
         SFFT_ALLOC(pl->d_L, (size_t)maxB * max_batch * sizeof(uint32_t));
+        pl->tw_shift = (ilog2_host(p->n) + 1) / 2;
+        SFFT_ALLOC(pl->d_tw, ((size_t(1) << pl->tw_shift) + (p->n >> pl->tw_shift)) * sizeof(double2));
         SFFT_ALLOC(pl->d_nL, (size_t)max_batch * sizeof(uint32_t));
     }
 #undef SFFT_ALLOC
@@ -269,6 +272,12 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     if ((e = cudaMemcpy(pl->d_taps64, pl->taps_host.data(), ntaps * sizeof(double), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return fail(e, "upload taps");
+    if (general) {  // twiddle factor tables of the FP64 estimates
+        std::vector<double2> tw;
+        twiddle_tables_host(p->n, pl->tw_shift, &tw);
+        if ((e = cudaMemcpy(pl->d_tw, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e, "upload twiddle tables");
+    }
     if ((e = cudaMemcpy(pl->d_wtab, pl->wtab_host.data(), pl->wtab_len * sizeof(double), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return fail(e, "upload window table");
@@ -423,6 +432,8 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
             a.est_gmin = p.est_gmin;
             a.taps = plan->d_taps32 + gr.taps_off;
             a.wtab = plan->d_wtab + gr.wtab_off;
+            a.tw = plan->d_tw;
+            a.tw_shift = plan->tw_shift;
             a.part = reinterpret_cast<float2*>(plan->d_part);
             a.part_stride = plan->part_stride;
             a.fin_scratch = gr.fin_global ? plan->d_gfin : nullptr;
@@ -786,6 +797,8 @@ sfft_status sfft_estimate_from_bins(sfft_plan plan, uint32_t r, uint32_t nrep, c
     a.u = reinterpret_cast<const double2*>(d_u);
     a.L = d_L;
     a.wtab = plan->d_wtab + g.wtab_off;
+    a.tw = plan->d_tw;
+    a.tw_shift = plan->tw_shift;
     a.est_gmin = plan->p.est_gmin;
     a.widx = d_widx;
     a.wval = reinterpret_cast<double2*>(d_wval);

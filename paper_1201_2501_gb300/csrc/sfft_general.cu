@@ -373,22 +373,69 @@ size_t general_locate_smem(uint32_t B) {
     return 0;
 }
 
-// Sorts the m keys of key[] ascending and removes duplicates: the distinct keys end up in
-// key[0..returned count).  tmp and keep hold m words each.
-__device__ uint32_t sort_unique_u32(uint32_t* key, uint32_t m, uint32_t* tmp, uint32_t* keep, uint32_t* scan) {
-    for (uint32_t c = threadIdx.x; c < m; c += kThreads) {  // rank, ties broken by position
-        const uint32_t k = key[c];
-        uint32_t r = 0;
-        for (uint32_t q = 0; q < m; ++q) r += (key[q] < k || (key[q] == k && q < c)) ? 1u : 0u;
-        tmp[r] = k;
+// Ascending bitonic sort of the P keys of k[] (P a power of two), one CTA; ends with a barrier.
+__device__ void block_bitonic_sort_u32(uint32_t* k, uint32_t P) {
+    for (uint32_t size = 2; size <= P; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P; i += kThreads) {
+                const uint32_t j = i ^ stride;
+                if (j > i) {
+                    const uint32_t x = k[i], y = k[j];
+                    if ((i & size) == 0 ? x > y : x < y) {
+                        k[i] = y;
+                        k[j] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
     }
-    __syncthreads();
-    for (uint32_t p = threadIdx.x; p < m; p += kThreads) keep[p] = (p == 0 || tmp[p - 1] != tmp[p]) ? 1u : 0u;
+}
+
+// Sorts the m keys of key[0..m) ascending (key holds P >= m words, P a power of two; keys < 2^32 - 1)
+// and writes the distinct ones to out[0..returned count).  keep holds m words.  Up to kThreads keys
+// are ranked directly (one key per thread, ties by position); more are sorted by a bitonic network
+// over the smallest power of two >= m.
+__device__ uint32_t sort_unique_u32(uint32_t* key, uint32_t m, uint32_t P, uint32_t* out, uint32_t* keep,
+                                    uint32_t* scan) {
+    const uint32_t* sorted = key;
+    if (m <= (uint32_t)kThreads) {
+        if (threadIdx.x < m) {
+            const uint32_t c = threadIdx.x, k = key[c];
+            uint32_t r = 0;
+            for (uint32_t q = 0; q < m; ++q) r += (key[q] < k || (key[q] == k && q < c)) ? 1u : 0u;
+            out[r] = k;
+        }
+        __syncthreads();
+        sorted = out;
+    } else {
+        uint32_t Pm = 1;
+        while (Pm < m && Pm < P) Pm <<= 1;  // key holds P words and m <= P
+        for (uint32_t p = m + threadIdx.x; p < Pm; p += kThreads) key[p] = 0xFFFFFFFFu;  // sort last
+        __syncthreads();
+        block_bitonic_sort_u32(key, Pm);
+    }
+    for (uint32_t p = threadIdx.x; p < m; p += kThreads) keep[p] = (p == 0 || sorted[p - 1] != sorted[p]) ? 1u : 0u;
     __syncthreads();
     const uint32_t total = block_exclusive_scan(keep, m, scan);  // keep[p]: output slot of a kept key
-    for (uint32_t p = threadIdx.x; p < m; p += kThreads) {
-        const uint32_t nxt = p + 1 < m ? keep[p + 1] : total;
-        if (nxt != keep[p]) key[keep[p]] = tmp[p];
+    // compaction: into out from key, or within out (then every kept key is read before any write)
+    if (sorted == out) {
+        uint32_t mine = 0, slot = 0;
+        bool kept = false;
+        if (threadIdx.x < m) {
+            const uint32_t p = threadIdx.x;
+            const uint32_t nxt = p + 1 < m ? keep[p + 1] : total;
+            kept = nxt != keep[p];
+            mine = out[p];
+            slot = keep[p];
+        }
+        __syncthreads();
+        if (kept) out[slot] = mine;
+    } else {
+        for (uint32_t p = threadIdx.x; p < m; p += kThreads) {
+            const uint32_t nxt = p + 1 < m ? keep[p + 1] : total;
+            if (nxt != keep[p]) out[keep[p]] = key[p];
+        }
     }
     __syncthreads();
     return total;
@@ -516,9 +563,18 @@ size_t general_estimate_smem(uint32_t B, uint32_t kprime, uint32_t zcap) { retur
 
 // w_i = median_q Re e_q + i median_q Im e_q over the hashings q whose window gain at i is >= est_gmin,
 // e_q = u^{(q)}_{h_q(i)} w^{-a_q sigma_q i} / W(-o_q(i)); lower median; 0 when no hashing qualifies.
+// w^e = exp(-2 pi i e / n) for an exact exponent e in [0, n) from two tables of FP64 factors,
+// exp(-2 pi i (e mod 2^sh) / n) and exp(-2 pi i 2^sh (e >> sh) / n): one complex product (a few ulp
+// from a direct evaluation) instead of an FP64 sincospi, which GB300 runs at 1/64 of the FP32 rate
+__device__ __forceinline__ double2 root_pow_tab(uint32_t e, const double2* tw, uint32_t sh) {
+    const double2 lo = tw[e & ((1u << sh) - 1u)], hi = tw[(1u << sh) + (e >> sh)];
+    return make_double2(hi.x * lo.x - hi.y * lo.y, hi.x * lo.y + hi.y * lo.x);
+}
+
 template <typename BinFn>
 __device__ double2 estimate_one(uint32_t i, uint32_t nrep, const uint64_t* sig, const uint64_t* bb, const uint64_t* aa,
-                                BinFn bin, uint32_t n, uint32_t nmask, uint32_t logNp, const double* wtab, double gmin) {
+                                BinFn bin, uint32_t n, uint32_t nmask, uint32_t logNp, const double* wtab, double gmin,
+                                const double2* tw, uint32_t tw_shift) {
     double re[kMaxRest], im[kMaxRest];
     uint32_t m = 0;
     for (uint32_t q = 0; q < nrep; ++q) {
@@ -529,7 +585,7 @@ __device__ double2 estimate_one(uint32_t i, uint32_t nrep, const uint64_t* sig, 
         const double gain = wtab[o < 0 ? -o : o];
         if (!(gain >= gmin)) continue;
         const uint32_t e = ((uint32_t)aa[q] * sq * i) & nmask;
-        const double2 w = root_pow<double>(e, nmask);
+        const double2 w = root_pow_tab(e, tw, tw_shift);
         const double2 u = bin(q, j);
         const double2 v = mul_conj_rn(u, w);
         const double x = __ddiv_rn(v.x, gain), y = __ddiv_rn(v.y, gain);
@@ -551,19 +607,25 @@ __device__ double2 estimate_one(uint32_t i, uint32_t nrep, const uint64_t* sig, 
     return make_double2(re[(m - 1) / 2], im[(m - 1) / 2]);
 }
 
-// (mag2 descending, index ascending) order of candidates via a bitonic sort of a permutation
+// (mag2 descending, index ascending) order of candidates via a bitonic sort of a permutation over the
+// smallest power of two >= m (<= P).  mag2 >= 0 is finite, so its IEEE bit pattern orders like its
+// value and the comparisons run on the integer units (GB300's FP64 pipe runs at 1/64 rate).
 __device__ void sort_by_magnitude(const double* mag, const uint32_t* idx, uint32_t m, uint32_t P, uint32_t* perm) {
-    for (uint32_t p = threadIdx.x; p < P; p += kThreads) perm[p] = p;
+    uint32_t Pm = 1;
+    while (Pm < m && Pm < P) Pm <<= 1;
+    for (uint32_t p = threadIdx.x; p < Pm; p += kThreads) perm[p] = p;
     __syncthreads();
+    const unsigned long long* mb = reinterpret_cast<const unsigned long long*>(mag);
     auto before = [&](uint32_t a, uint32_t b) -> bool {  // a ranks before b
         if (a >= m) return false;
         if (b >= m) return true;
-        if (mag[a] != mag[b]) return mag[a] > mag[b];
+        const unsigned long long x = mb[a], y = mb[b];
+        if (x != y) return x > y;
         return idx[a] < idx[b];
     };
-    for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t k = 2; k <= Pm; k <<= 1) {
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P; i += kThreads) {
+            for (uint32_t i = threadIdx.x; i < Pm; i += kThreads) {
                 const uint32_t ixj = i ^ j;
                 if (ixj > i) {
                     const bool up = (i & k) == 0;
@@ -615,15 +677,15 @@ __global__ void __launch_bounds__(kThreads) k_gen_estimate(const GenArgs a) {
         if (c != 0xFFFFFFFFu) Lk[atomicAdd(&s_m, 1u)] = c;
     }
     __syncthreads();
-    const uint32_t nL = sort_unique_u32(Lk, s_m, Lt, keep, scan);
-    const uint32_t* L = Lk;
+    const uint32_t nL = sort_unique_u32(Lk, s_m, Ly.P, Lt, keep, scan);
+    const uint32_t* L = Lt;
     if (tid == 0) a.nL[s] = nL;
     const double2* bins = a.bins + (size_t)s * a.bins_stride + (size_t)2 * a.npairs * B;
     const uint32_t logNp = (uint32_t)(63 - __clzll((long long)a.n)) - a.logB;
     for (uint32_t c = tid; c < nL; c += kThreads) {
         const double2 w = estimate_one(L[c], a.R_est, dr, dr + kMaxRest, dr + 2 * kMaxRest,
                                        [&](uint32_t q, uint32_t j) { return bins[(size_t)q * B + j]; }, (uint32_t)a.n,
-                                       a.nmask, logNp, a.wtab, a.est_gmin);
+                                       a.nmask, logNp, a.wtab, a.est_gmin, a.tw, a.tw_shift);
         wv[c] = w;
         mag[c] = __dadd_rn(__dmul_rn(w.x, w.x), __dmul_rn(w.y, w.y));
     }
@@ -736,7 +798,7 @@ __global__ void __launch_bounds__(kThreads) k_estimate_from_bins(const EstArgs a
     for (uint32_t c = tid; c < a.nL; c += kThreads) {
         const double2 w = estimate_one(a.L[c], a.nrep, a.sig, a.bb, a.aa,
                                        [&](uint32_t q, uint32_t j) { return a.u[(size_t)q * a.B + j]; }, (uint32_t)a.n,
-                                       a.nmask, logNp, a.wtab, a.est_gmin);
+                                       a.nmask, logNp, a.wtab, a.est_gmin, a.tw, a.tw_shift);
         wv[c] = w;
         mag[c] = __dadd_rn(__dmul_rn(w.x, w.x), __dmul_rn(w.y, w.y));
     }

@@ -191,6 +191,35 @@ void window_table_chirp(uint64_t n, const double* g, int64_t T, uint64_t len, do
 // The paper's closed-form gain Ghat'(o) for o = 0..len-1 (Sec. 7): 1 for |o| <= (1 - alpha) n / 2B,
 // 0 for |o| >= n / 2B, and Phi((s + C) / sig_f) - Phi((s - C) / sig_f), s = o / n, in between, with
 // the window's C = (1 - alpha/2) / 2B and sig_f = alpha / (4 B z), z = sqrt(2 ln(1/delta)).
+// exp(-2 pi i m / n) for an integer m in [0, n), n a power of two: the angle is reduced to the first
+// octant exactly (m / n is an exact binary fraction) before one cos and one sin are taken
+static double2 root_of_unity(uint64_t m, uint64_t n) {
+    const uint64_t q = n / 8;  // n >= 64
+    const uint64_t oct = m / q, r = m % q;
+    // angle = 2 pi (oct q + r) / n = oct pi / 4 + 2 pi r / n; fold into [0, pi/4] with a sign/swap table
+    const double th = 2.0 * M_PI * (double)r / (double)n;  // in [0, pi/4)
+    const double c = std::cos(th), s = std::sin(th), h = std::sqrt(0.5);
+    double re = 0, im = 0;  // cos and sin of the full angle
+    switch (oct) {
+        case 0: re = c; im = s; break;
+        case 1: re = h * (c - s); im = h * (c + s); break;
+        case 2: re = -s; im = c; break;
+        case 3: re = -h * (c + s); im = h * (c - s); break;
+        case 4: re = -c; im = -s; break;
+        case 5: re = -h * (c - s); im = -h * (c + s); break;
+        case 6: re = s; im = -c; break;
+        default: re = h * (c + s); im = -h * (c - s); break;
+    }
+    return make_double2(re, -im);
+}
+
+void twiddle_tables_host(uint64_t n, uint32_t sh, std::vector<double2>* out) {
+    const uint64_t lo = uint64_t(1) << sh, hi = n >> sh;
+    out->resize(lo + hi);
+    for (uint64_t b = 0; b < lo; ++b) (*out)[b] = root_of_unity(b, n);
+    for (uint64_t a = 0; a < hi; ++a) (*out)[lo + a] = root_of_unity(a << sh, n);
+}
+
 void window_gprime_host(uint64_t n, uint32_t B, double alpha, double delta, uint64_t len, double* W) {
     const double nn = (double)n, z = std::sqrt(2.0 * std::log(1.0 / delta));
     const double C = (1.0 - alpha / 2.0) / (2.0 * (double)B), sf = alpha / (4.0 * (double)B * z);

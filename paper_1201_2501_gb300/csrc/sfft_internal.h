@@ -199,6 +199,8 @@ struct GenArgs {
     double s, est_gmin;
     const float* taps;
     const double* wtab;
+    const double2* tw;     // FP64 twiddles w^e = tw[e mod 2^tw_shift] tw[2^tw_shift + (e >> tw_shift)]
+    uint32_t tw_shift;
     float2* part;          // [batch][ngroups][ctas][2][B]
     size_t part_stride;    // elements per request
     unsigned char* fin_scratch;  // k_gen_finish arrays in device memory: [batch][ngroups][fin_stride], or null
@@ -248,6 +250,8 @@ struct EstArgs {
     const double2* u;      // nrep x B
     const uint32_t* L;     // nL, ascending
     const double* wtab;
+    const double2* tw;     // as GenArgs::tw
+    uint32_t tw_shift;
     double est_gmin;
     uint32_t* widx;
     double2* wval;
@@ -265,6 +269,8 @@ struct sfft_plan_s {
     double2* d_bins = nullptr;
     double* d_phase = nullptr;
     uint32_t* d_L = nullptr;
+    double2* d_tw = nullptr;  // general mode: FP64 twiddle factor tables (2^tw_shift + n / 2^tw_shift)
+    uint32_t tw_shift = 0;
     uint32_t* d_nL = nullptr;
     size_t bins_stride = 0, phase_stride = 0;
     std::vector<double> taps_host;  // every round's taps, FP64
@@ -330,6 +336,14 @@ sfft_status execute_batch(sfft_plan_s* plan, const void* d_x, const ReqDesc* d_r
                           cudaStream_t st, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
                           int32_t* d_flag);
 void window_taps_host(uint64_t n, uint32_t B, double alpha, double delta, int64_t T, double* g);
+inline uint32_t ilog2_host(uint64_t v) {  // v a power of two
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < v) ++l;
+    return l;
+}
+// FP64 twiddle factor tables for n = 2^L and split sh: out[b] = exp(-2 pi i b / n), b < 2^sh, then
+// out[2^sh + a] = exp(-2 pi i a 2^sh / n), a < n / 2^sh
+void twiddle_tables_host(uint64_t n, uint32_t sh, std::vector<double2>* out);
 void window_table_host(uint64_t n, const double* g, int64_t T, uint64_t len, double* W);
 int64_t window_halfwidth(uint32_t B, double alpha, double delta);
 void draw_exact_host(uint64_t seed, uint32_t request, uint32_t round, uint64_t n, uint64_t* sigma, uint64_t* b);

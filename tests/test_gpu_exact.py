@@ -239,6 +239,24 @@ def test_sfft_exact_fp32_matches_oracle(sf, m, k, batch):
     plan.close()
 
 
+@pytest.mark.parametrize("extra", [4, 13])
+def test_sfft_exact_many_rounds_matches_oracle(sf, extra):
+    """Rounds after t = ceil(log2 k) (k_t = 1, B_t = B_min): 9 and 18 rounds, so the one-launch kernel
+    carries its round blocks in both of its larger parameter sizes (up to 16 and up to 32 rounds)."""
+    n, k, batch = 1 << 16, 16, 3
+    f = exact_fields(n, k, extra_rounds=extra)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f, 0), batch)
+    assert plan.rounds == 5 + extra
+    sigs = [workloads.exact_sparse(n, k, workloads.seed_for(2, 500 + i), dtype=np.complex64) for i in range(batch)]
+    seed = 31
+    got = _run_gpu(sf, plan, [s.x for s in sigs], seed, f["z_cap"])
+    for r, s in enumerate(sigs):
+        want = oracle.sfft_exact(P, s.x.astype(np.complex128), seed, r)
+        _compare(got[r], want, 1e-5)
+    plan.close()
+
+
 @pytest.mark.parametrize("m,k,prec,batch", [(18, 512, 0, 3), (20, 1024, 0, 2), (16, 512, 1, 2)])
 def test_sfft_exact_large_k_matches_oracle(sf, m, k, prec, batch):
     """B = 2048 and 4096 with zhat capacities of 2048 and 4096: the end-of-round arrays no longer fit
