@@ -112,21 +112,25 @@ __global__ void __launch_bounds__(kThreads) k_gen_gather(const GenArgs a) {
     for (uint32_t ch = c0; ch < c1; ++ch) {
         const int64_t t_lo = -a.T + (int64_t)ch * kChunkTaps;
         const uint32_t ntap = (uint32_t)(min(t_lo + (int64_t)kChunkTaps, a.T + 1) - t_lo);
-        // step 1a: x_{sigma (t - a_h)} for the chunk's taps, 12 loads in flight per thread
-        for (uint32_t hh = 0; hh < h.H; ++hh) {
-            const int32_t base = (int32_t)(t_lo - (int64_t)h.a[hh]);
-            for (uint32_t i0 = tid; i0 < ntap; i0 += kThreads * 12) {
-                float2 v[12];
+        // step 1a: x_{sigma (t - a_h)} for the chunk's taps of every hashing of the group, 16 loads in
+        // flight per thread (a pair's whole chunk in one batch)
+        const uint32_t total = h.H * ntap;
+        for (uint32_t f0 = tid; f0 < total; f0 += kThreads * 16) {
+            float2 v[16];
 #pragma unroll
-                for (int q = 0; q < 12; ++q) {
-                    const uint32_t i = i0 + (uint32_t)q * kThreads;
-                    if (i < ntap) v[q] = __ldcg(x + ((h.sigma * (uint32_t)(base + (int32_t)i)) & rq.xmask));
+            for (int q = 0; q < 16; ++q) {
+                const uint32_t f = f0 + (uint32_t)q * kThreads;
+                if (f < total) {
+                    const bool second = f >= ntap;
+                    const uint32_t i = second ? f - ntap : f;
+                    const int32_t base = (int32_t)(t_lo - (int64_t)(second ? h.a[1] : h.a[0]));
+                    v[q] = __ldcg(x + ((h.sigma * (uint32_t)(base + (int32_t)i)) & rq.xmask));
                 }
+            }
 #pragma unroll
-                for (int q = 0; q < 12; ++q) {
-                    const uint32_t i = i0 + (uint32_t)q * kThreads;
-                    if (i < ntap) stage[hh * kChunkTaps + i] = v[q];
-                }
+            for (int q = 0; q < 16; ++q) {
+                const uint32_t f = f0 + (uint32_t)q * kThreads;
+                if (f < total) stage[f < ntap ? f : kChunkTaps + (f - ntap)] = v[q];
             }
         }
         __syncthreads();
