@@ -260,7 +260,9 @@ __global__ void __launch_bounds__(kThreads) k_gen_finish(const GenArgs a) {
             }
         }
         for (uint32_t hh = 0; hh < h.H; ++hh) bins[(size_t)hash_index(a, g, hh) * B + j] = u[hh];
-        if (h.H == 2) a.phase[(size_t)s * a.phase_stride + (size_t)g * B + j] = phase01<double>(mul_conj_rn(u[0], u[1]));
+        // LocateInner's c_j: an FP32 arctangent of the FP64 product (the vote arcs are s pi wide and
+        // the FP32 bins carry ~1e-6 of phase noise; GB300 runs FP64 at 1/64 of the FP32 rate)
+        if (h.H == 2) a.phase[(size_t)s * a.phase_stride + (size_t)g * B + j] = phase01<float>(mul_conj_rn(u[0], u[1]));
     }
 }
 
