@@ -144,8 +144,11 @@ sfft_status sfft_plan_taps(sfft_plan plan, uint32_t t, double* h_taps, uint64_t 
  *   d_val[...]                    their values X_f as (re, im) doubles
  *   d_count[r]                    number of entries written (<= cap)
  *   d_flag[r]                     sfft_status of the request: OK, NOT_CONVERGED or CAPACITY
- * Exact mode follows Algorithm 1; general mode Algorithms 2 and 3.
- * Errors: INVALID_ARG (null pointer, batch out of range, cap == 0), CUDA (launch failure).
+ * Exact mode follows Algorithm 1: one kernel launch per stream group covers every round, since the
+ * samples of all rounds are known before any is decoded; general mode follows Algorithms 2 and 3 with
+ * four launches per round.  Asynchronous on `stream`; the plan may run one call at a time.
+ * Errors: INVALID_ARG (null pointer, batch out of range, cap == 0), CUDA (launch failure, including a
+ * batch whose chunks would exceed 2^31 - 1 CTAs).
  */
 sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, void* stream,
                          uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag);
