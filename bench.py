@@ -581,6 +581,12 @@ def run_ours(args):
             "cpu_baseline": cpu,
         }
         line.update(extra)
+        ceil = extra.get("random_gather_ceiling")
+        if ceil:  # the same step against the random 32-byte-sector rate measured in this run
+            sectors = achieved * 1e9 / 32.0
+            line["roofline"]["random_sector_rate"] = {"achieved_sectors_per_s": sectors,
+                                                      "ceiling_sectors_per_s": ceil["sectors_per_s"],
+                                                      "frac": sectors / ceil["sectors_per_s"]}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
