@@ -231,7 +231,7 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     SFFT_ALLOC(pl->d_taps64, ntaps * sizeof(double));
     SFFT_ALLOC(pl->d_wtab, pl->wtab_len * sizeof(double));
     SFFT_ALLOC(pl->d_part, pl->part_bytes);
-    const size_t ncounters = (size_t)max_batch * (general ? 1 : pl->rounds.size());
+    const size_t ncounters = (size_t)max_batch * (general ? 1 : 2 * pl->rounds.size());
     SFFT_ALLOC(pl->d_counter, ncounters * sizeof(uint32_t));
 
     SFFT_ALLOC(pl->d_zidx, (size_t)max_batch * p->z_cap * sizeof(uint32_t));
@@ -289,6 +289,7 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
             ExactArgs a = base_args(pl, pl->rounds[t], t);
             a.part = static_cast<unsigned char*>(pl->d_part) + part_off[t] * csize;
             a.counter = pl->d_counter + (size_t)t * max_batch;
+            a.counter2 = pl->d_counter + (size_t)(pl->rounds.size() + t) * max_batch;
             a.first_round = t == 0;
             a.last_round = t + 1 == pl->rounds.size();
             pl->rdesc.push_back(a);

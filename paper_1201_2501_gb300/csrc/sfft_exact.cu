@@ -534,8 +534,14 @@ __device__ void sum_partials(const C* part, uint32_t chunks, uint32_t H, uint32_
     }
 }
 
+// Parts of a round's finisher: the bins (partial folds summed in chunk order, bit-reversed, B-point
+// FFT) and the decode (zhat subtraction, location, estimation, merge).  kFinBins leaves the bins in
+// the first H B entries of the request's partial-fold area of the round; kFinDecode starts from there.
+enum FinPart { kFinBins = 1, kFinDecode = 2, kFinAll = 3 };
+
 template <typename R>
-__device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uint32_t b, unsigned char* smem) {
+__device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uint32_t b, unsigned char* smem,
+                             int part = kFinAll) {
     using C = typename Cx<R>::T;
     const uint32_t tid = threadIdx.x;
     const uint32_t B = a.B, H = a.H;
@@ -561,9 +567,21 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     uint32_t* keep = reinterpret_cast<uint32_t*>(smem + Ly.keep);
     uint32_t* scan = reinterpret_cast<uint32_t*>(smem + Ly.scan);
     __shared__ uint32_t s_nw, s_above, s_kept;
+    C* area = reinterpret_cast<C*>(a.part) + (size_t)s * a.part_stride;  // the round's partial folds
 
-    // zhat of this request and its per-entry subtraction terms (independent of the bins: done first,
-    // in parallel, so that the bin threads below only add)
+    // steps 2 (across chunks) and 3: partial folds summed in chunk order, bit-reversed, FFT
+    if (part & kFinBins) {
+        sum_partials(area, a.chunks, H, a.logB, U);
+        block_fft_rows<R>(U, H, a.logB);  // starts and ends with a barrier
+        if (!(part & kFinDecode)) {  // every partial fold has been read: the area takes the bins
+            for (uint32_t i = tid; i < H * B; i += kThreads) area[i] = U[i];
+            return;
+        }
+    } else {
+        for (uint32_t i = tid; i < H * B; i += kThreads) U[i] = __ldcg(area + i);
+    }
+
+    // zhat of this request and its per-entry subtraction terms
     // zhat is read through L2 only: in the one-launch path another CTA of this launch wrote it
     // (the first entry of each thread is fetched together with the count)
     const uint32_t zlim = a.bins_only ? a.e_nz : a.zcap;
@@ -593,8 +611,6 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         ent_bin[e] = jb;
         ent_gain[e] = a.wtab[o < 0 ? -o : o];
     }
-    // step 2 (across chunks) and 3: partial folds summed in chunk order, bit-reversed, FFT
-    sum_partials(reinterpret_cast<const C*>(a.part) + (size_t)s * a.part_stride, a.chunks, H, a.logB, U);
     if (tid == 0) {
         s_nw = 0;
         s_above = 0;
@@ -611,7 +627,7 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         ent_sub[q] = t;
         ent_sub_f[q] = make_float2((float)t.x, (float)t.y);
     }
-    block_fft_rows<R>(U, H, a.logB);  // ends with a barrier
+    __syncthreads();
     bucket_entries(ent_bin, nz, B, bin_cnt, bin_start, bin_list, scan);
 
     if (a.bins_only) {  // single-hashing mode: the subtracted bins u_0 in FP64, no decode
@@ -765,14 +781,19 @@ __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_step(
     uint32_t sigma, b;
     exact_hash(rq.seed, rq.id, t, a->nmask, &sigma, &b);
     gather_fold<R>(*a, rq.x, rq.xmask, s, c, sigma, b, smem);
-    if (arrive(a->counter + s, a->chunks + (t > 0 ? 1u : 0u)) == 0) return;
+    if (arrive(a->counter + s, a->chunks) == 0) return;
+    // the round's bins, in this CTA's shared memory (the gather's staging area holds H B values)
+    finish_round<R>(*a, s, sigma, b, smem, kFinBins);
+    if (tid == 0) a->counter[s] = 0;  // every chunk of round t has arrived
+    if (arrive(a->counter2 + s, t > 0 ? 2u : 1u) == 0) return;
     for (;;) {
-        finish_round<R>(*a, s, sigma, b, a->fin_scratch ? a->fin_scratch + (size_t)s * a->fin_stride : smem);
-        if (tid == 0) a->counter[s] = 0;  // every arrival of round t has happened
+        finish_round<R>(*a, s, sigma, b, a->fin_scratch ? a->fin_scratch + (size_t)s * a->fin_stride : smem,
+                        kFinDecode);
+        if (tid == 0) a->counter2[s] = 0;  // both arrivals of round t have happened
         if (t + 1 >= sp.R) break;
         a = &sp.r[++t];
-        // zhat of round t is published by the arrival at round t + 1's counter
-        if (arrive(a->counter + s, a->chunks + 1u) == 0) break;
+        // zhat of round t is published by the arrival at round t + 1's second counter
+        if (arrive(a->counter2 + s, 2u) == 0) break;
         exact_hash(rq.seed, rq.id, t, a->nmask, &sigma, &b);
     }
 }

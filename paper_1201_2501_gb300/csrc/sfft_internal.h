@@ -72,6 +72,8 @@ struct ExactArgs {
                                // laid out [chunks][H][B] complex R (requests may be in different rounds)
     size_t part_stride;
     uint32_t* counter;         // [batch] arrival counters (zero between launches)
+    uint32_t* counter2;        // [batch] the one-launch path's second counters: round t's decode starts
+                               // once its bins are ready and round t - 1's decode is done
     uint32_t* zidx;            // [batch][zcap]
     double2* zval;             // [batch][zcap]
     uint32_t* zcount;          // [batch]
@@ -97,9 +99,11 @@ struct ExactArgs {
 
 // One launch of the exact algorithm over a batch: every round's gather chunks at once, grouped by
 // round (segment t = chunks_t x batch CTAs, request-major, chunk fastest), since no sample position
-// depends on zhat.  Round t of request s is finished by whichever arrives last: its t-th round's final
-// chunk or round t - 1's finisher (arrival counter t of s, target chunks_t + [t > 0]).  That CTA then
-// arrives on round t + 1 and, if last there too, finishes it as well.  Nobody waits.  The round
+// depends on zhat.  A round's finisher comes in two parts.  Its bins (partial sums, B-point FFT) need
+// only the round's chunks: the last chunk to arrive computes them (counter) and leaves them in the
+// request's partial-fold area.  Its decode (subtraction of zhat, location, estimation, merge) also
+// needs round t - 1's zhat: whichever arrives last at counter2 -- the bins part, or round t - 1's
+// decode -- runs it, then arrives at round t + 1's counter2.  Nobody waits.  The round
 // blocks (tables, workspace and this launch's signal and outputs) travel in the kernel parameters,
 // NR of them (8, 16 or 32: the smallest that holds the plan's rounds).
 template <int NR>
@@ -282,7 +286,7 @@ struct sfft_plan_s {
     void* d_part = nullptr;
     size_t part_bytes = 0;
     size_t part_stride = 0;  // elements of the partial-fold buffer owned by one request
-    uint32_t* d_counter = nullptr;  // [R][max_batch] arrival counters (zero between launches)
+    uint32_t* d_counter = nullptr;  // [2 R][max_batch] arrival counters (zero between launches)
     std::vector<sfft::ExactArgs> rdesc;  // [R] round blocks of the one-launch exact path
     size_t step_smem = 0;                // its dynamic shared memory (largest round)
     uint32_t* d_zidx = nullptr;
