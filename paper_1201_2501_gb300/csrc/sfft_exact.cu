@@ -674,6 +674,26 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     }
     __syncthreads();
 
+    const bool last = a.last_round != 0;
+    if (nw == 0) {
+        // nothing decoded: zhat stays as it is (its entries passed the same prune test when merged)
+        if (last) {
+            for (uint32_t e = tid; e < nz && e < a.out_cap; e += kThreads) {
+                a.out_idx[(size_t)s * a.out_cap + e] = ent_idx[e];
+                a.out_val[(size_t)s * a.out_cap + e] = ent_val[e];
+            }
+            if (tid == 0) {
+                a.out_count[s] = nz < a.out_cap ? nz : a.out_cap;
+                int32_t flag = SFFT_OK;
+                if (__ldcg(a.zflag + s) || nz > a.out_cap)
+                    flag = SFFT_ERR_CAPACITY;
+                else if (s_above > s_kept)
+                    flag = SFFT_ERR_NOT_CONVERGED;
+                a.out_flag[s] = flag;
+            }
+        }
+        return;
+    }
     // merge what into zhat (NoiselessSparseFFT: zhat <- zhat + what), zhat first on equal indices,
     // then drop entries below prune * thr
     const uint32_t tot = nz + nw;
@@ -708,7 +728,6 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     const uint32_t newcount = block_exclusive_scan(keep, tot, scan);
     uint32_t* zi = a.zidx + (size_t)s * a.zcap;
     double2* zv = a.zval + (size_t)s * a.zcap;
-    const bool last = a.last_round != 0;
     for (uint32_t p = tid; p < tot; p += kThreads) {
         const uint32_t pos = keep[p];  // exclusive prefix of the keep flags: kept iff the next differs
         const uint32_t nxt = p + 1 < tot ? keep[p + 1] : newcount;
