@@ -491,6 +491,16 @@ sfft_status sfft_window_taps(uint64_t n, uint32_t B, double alpha, double delta,
 sfft_status sfft_window_gains(uint64_t n, uint32_t B, double alpha, double delta, uint64_t len, double* h_W);
 
 /*
+ * Host only: the twiddle factor tables general-mode plans use for EstimateValues' FP64 terms
+ * w^{a sigma i} (Algorithm 2), with w = exp(-2 pi i / n).  For n = 2^L (64 <= n <= 2^30) and
+ * sh = ceil(L / 2), h_tw (2^sh + n / 2^sh complex values, (re, im) doubles) receives
+ * exp(-2 pi i b / n) for b < 2^sh, then exp(-2 pi i a 2^sh / n) for a < n / 2^sh; then
+ * w^e = h_tw[e mod 2^sh] h_tw[2^sh + (e >> sh)].  *len receives the entry count (h_tw may be NULL to
+ * query it).  Each entry is within a few ulp of the exact value.
+ */
+sfft_status sfft_twiddle_tables(uint64_t n, uint64_t* len, double* h_tw, uint64_t cap);
+
+/*
  * Philox4x32-10 as the device computes it (Salmon et al., SC 2011): for i < count, the four output
  * words for key (key0, key1) and counter (ctr[0], ctr[1], ctr[2], ctr[3] + i), written to d_out[4 i..].
  */

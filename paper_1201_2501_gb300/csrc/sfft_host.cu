@@ -472,6 +472,22 @@ sfft_status sfft_window_taps(uint64_t n, uint32_t B, double alpha, double delta,
     return SFFT_OK;
 }
 
+sfft_status sfft_twiddle_tables(uint64_t n, uint64_t* len, double* h_tw, uint64_t cap) {
+    if (!len || n < 64 || n > (uint64_t(1) << 30) || (n & (n - 1))) return SFFT_ERR_INVALID_ARG;
+    const uint32_t sh = (sfft::ilog2_host(n) + 1) / 2;
+    const uint64_t m = (uint64_t(1) << sh) + (n >> sh);
+    *len = m;
+    if (!h_tw) return SFFT_OK;
+    if (cap < m) return SFFT_ERR_INVALID_ARG;
+    std::vector<double2> tw;
+    sfft::twiddle_tables_host(n, sh, &tw);
+    for (uint64_t i = 0; i < m; ++i) {
+        h_tw[2 * i] = tw[i].x;
+        h_tw[2 * i + 1] = tw[i].y;
+    }
+    return SFFT_OK;
+}
+
 sfft_status sfft_window_gains(uint64_t n, uint32_t B, double alpha, double delta, uint64_t len, double* h_W) {
     int64_t T = 0;
     const sfft_status st = sfft_window_taps(n, B, alpha, delta, &T, nullptr, 0);

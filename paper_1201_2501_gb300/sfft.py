@@ -148,6 +148,7 @@ _SIGS = {
                                                _vp]),
     "sfft_window_taps": (ctypes.c_int, [_u64, _u32, _dbl, _dbl, _i64p, _dblp, _u64]),
     "sfft_window_gains": (ctypes.c_int, [_u64, _u32, _dbl, _dbl, _u64, _dblp]),
+    "sfft_twiddle_tables": (ctypes.c_int, [_u64, ctypes.POINTER(ctypes.c_uint64), _dblp, _u64]),
     "sfft_execute_requests": (ctypes.c_int, [_vp, ctypes.POINTER(SfftRequest), _u32, _vp, _vp, _vp, _u32, _vp, _vp]),
     "sfft_autotune": (ctypes.c_int, [_P, _u32, _dbl, _u64, _u32, _P, ctypes.POINTER(SfftTuneEntry), _u32, _u32p]),
     "sfft_graph_create": (ctypes.c_int, [_vp, _vp, _u32, _u64, _vp, _vp, _u32, _vp, _vp, ctypes.POINTER(_vp)]),
@@ -319,6 +320,17 @@ def sfft_window_taps(n: int, B: int, alpha: float, delta: float):
     _check(lib().sfft_window_taps(n, B, alpha, delta, ctypes.byref(T), g.ctypes.data_as(_dblp), g.size),
            "sfft_window_taps")
     return g
+
+
+def sfft_twiddle_tables(n: int):
+    """Host-only: the general mode's FP64 twiddle factor tables for n (numpy complex128)."""
+    import numpy as np
+
+    m = ctypes.c_uint64()
+    _check(lib().sfft_twiddle_tables(n, ctypes.byref(m), None, 0), "sfft_twiddle_tables")
+    tw = np.empty(2 * m.value, dtype=np.float64)
+    _check(lib().sfft_twiddle_tables(n, ctypes.byref(m), tw.ctypes.data_as(_dblp), m.value), "sfft_twiddle_tables")
+    return tw[0::2] + 1j * tw[1::2]
 
 
 def sfft_window_gains(n: int, B: int, alpha: float, delta: float, length: int):

@@ -44,3 +44,19 @@ def test_window_functions_reject_bad_arguments(sf):
     assert sf.lib().sfft_window_taps(1000, 16, 0.5, 1e-6, ctypes.byref(T), None, 0) == sf.SFFT_ERR_INVALID_ARG
     assert sf.lib().sfft_window_taps(1 << 10, 24, 0.5, 1e-6, ctypes.byref(T), None, 0) == sf.SFFT_ERR_INVALID_ARG
     assert sf.lib().sfft_window_gains(1 << 10, 16, 0.5, 1e-6, (1 << 9) + 2, None) == sf.SFFT_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("m", [6, 11, 16, 22, 26])
+def test_twiddle_tables_give_the_roots_of_unity(sf, m):
+    """The general mode's FP64 twiddles: w^e = T[e mod 2^sh] T[2^sh + (e >> sh)], w = exp(-2 pi i / n),
+    against numpy's exp of the exact angle (e / n is an exact binary fraction) at sampled exponents."""
+    n = 1 << m
+    tw = sf.sfft_twiddle_tables(n)
+    sh = (m + 1) // 2
+    assert len(tw) == (1 << sh) + (n >> sh)
+    rng = np.random.default_rng(m)
+    e = np.unique(np.concatenate([[0, 1, n // 8, n // 4, n // 2, n - 1], rng.integers(0, n, 500)]))
+    got = tw[e & ((1 << sh) - 1)] * tw[(1 << sh) + (e >> sh)]
+    want = np.exp(-2j * np.pi * (e.astype(np.float64) / n))
+    assert np.max(np.abs(got - want)) <= 4e-15  # two roundings of the factors and four of the product
+    assert np.max(np.abs(np.abs(tw) - 1.0)) <= 1e-15  # each factor a unit complex number to a few ulp
