@@ -42,7 +42,7 @@ def _rows(outs, nreq):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_mixed_batch_equals_per_round_launches(sf, prec):
+def test_mixed_batch_equals_each_plans_own_execution(sf, prec):
     sizes = [(14, 8), (16, 16), (18, 64), (16, 512)] if prec == 0 else [(12, 4), (14, 8), (14, 32)]
     fields = [exact_fields(1 << m, k) for m, k in sizes]
     plans = [sf.Plan(gpu_params(sf, f, prec), 16) for f in fields]
