@@ -1,6 +1,6 @@
 """Mixed exact-mode batches in one persistent launch (sfft_batch_*): requests of several plans
 (different n and k, one with its end-of-round arrays in device memory) in a shuffled order give bit
-for bit the results of the per-round launches of each request's own plan, and the oracle's."""
+for bit the results of each request's own plan run through sfft_execute, and the oracle's."""
 import random
 
 import numpy as np
@@ -81,7 +81,7 @@ def test_mixed_batch_equals_each_plans_own_execution(sf, prec):
 
 def test_persistent_headline_shape(sf):
     """The benchmark's workload shape (n = 2^22, k = 64) through one persistent launch of 32 requests,
-    against the per-round launches of the same plan."""
+    against sfft_execute of the same plan."""
     n, k, nreq = 1 << 22, 64, 32
     f = exact_fields(n, k)
     p = gpu_params(sf, f)
