@@ -278,6 +278,15 @@ sfft_status sfft_batch_execute(sfft_batch_plan bp, const uint32_t* h_plan_of, co
                                uint32_t nreq, void* stream, uint32_t* d_idx, double* d_val, uint32_t cap,
                                uint32_t* d_count, int32_t* d_flag);
 
+/*
+ * Check of the persistent launch's bounded wait: one CTA of the batch kernel takes a queue item that
+ * nothing ever publishes.  Its wait gives up after about a second, it sets the launch's error flag and
+ * returns; the call synchronises `stream` and returns SFFT_ERR_TIMEOUT when the flag was set (the
+ * expected outcome) or SFFT_OK if the wait did not give up.  The device stays usable either way.
+ * Errors: OOM, CUDA.
+ */
+sfft_status sfft_persistent_wait_check(void* stream);
+
 /* ---------------------------------------------------------------------------------------------- */
 /* Serving: continuous batching of independent transforms                                         */
 /* ---------------------------------------------------------------------------------------------- */

@@ -973,6 +973,35 @@ sfft_status sfft_batch_plan_create(const sfft_plan* plans, uint32_t nplans, uint
     return SFFT_OK;
 }
 
+sfft_status sfft_persistent_wait_check(void* stream) {
+    // control block: items[1] (never published), head, tail, error
+    unsigned char* d = nullptr;
+    if (cudaMalloc((void**)&d, 64) != cudaSuccess) {
+        cudaGetLastError();
+        return SFFT_ERR_OOM;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    PersistArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.items = reinterpret_cast<unsigned long long*>(d);
+    a.head = reinterpret_cast<uint32_t*>(d + 16);
+    a.tail = a.head + 1;
+    a.error = reinterpret_cast<int32_t*>(a.head + 2);
+    a.total = 1;
+    int32_t err = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, 64, st);
+    if (e == cudaSuccess) e = launch_exact_persistent(a, 1, 0, st, false);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, a.error, sizeof(err), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("wait check: ") + cudaGetErrorString(e));
+        cudaGetLastError();
+        return SFFT_ERR_CUDA;
+    }
+    return err ? SFFT_ERR_TIMEOUT : SFFT_OK;
+}
+
 sfft_status sfft_batch_plan_destroy(sfft_batch_plan bp) {
     if (!bp) return SFFT_OK;
     cudaDeviceSynchronize();

@@ -157,6 +157,7 @@ _SIGS = {
     "sfft_plan_set_requests": (ctypes.c_int, [_vp, ctypes.POINTER(SfftRequest), _u32, _vp]),
     "sfft_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _u32, ctypes.POINTER(_vp)]),
     "sfft_batch_plan_destroy": (ctypes.c_int, [_vp]),
+    "sfft_persistent_wait_check": (ctypes.c_int, [_vp]),
     "sfft_batch_execute": (ctypes.c_int, [_vp, _u32p, ctypes.POINTER(SfftRequest), _u32, _vp, _vp, _vp, _u32, _vp,
                                           _vp]),
     "sfft_server_create": (ctypes.c_int, [ctypes.POINTER(SfftServerConfig), ctypes.POINTER(_vp)]),

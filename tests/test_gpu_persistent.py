@@ -98,3 +98,21 @@ def test_persistent_headline_shape(sf):
         assert np.array_equal(got[r][0], sup[r])
     bp.close()
     plan.close()
+
+
+def test_a_wait_that_nothing_ends_gives_up_with_a_status(sf):
+    """The persistent kernel's bounded wait: a CTA waiting for a queue item that is never published
+    gives up after about a second, flags the launch and returns; the host reads SFFT_ERR_TIMEOUT and the
+    device keeps working (a transform afterwards matches the oracle)."""
+    import time
+
+    t0 = time.perf_counter()
+    assert sf.lib().sfft_persistent_wait_check(None) == sf.SFFT_ERR_TIMEOUT
+    assert 0.2 < time.perf_counter() - t0 < 30.0
+    n, k = 1 << 14, 8
+    f = exact_fields(n, k)
+    plan = sf.Plan(gpu_params(sf, f, 0), 1)
+    s = workloads.exact_sparse(n, k, workloads.seed_for(2, 900), dtype=np.complex64)
+    got = _rows(sf.sfft_execute(plan, torch.as_tensor(s.x[None]).cuda(), 5, f["z_cap"]), 1)[0]
+    assert np.array_equal(got[0], s.support)
+    plan.close()
