@@ -558,7 +558,17 @@ def run_ours(args):
                "sample": f"{cnt_o} transforms of the same workload (n=2^22, k=64, distinct signals), "
                          f"{per_core} per process on {cores} processes (one pre-generated signal each, fresh "
                          f"hashings per transform), {wall:.1f} s wall, {busy:.1f} s oracle CPU time, "
-                         f"{ok}/{cnt_o} exact supports"}
+                         f"{ok}/{cnt_o} exact supports",
+               "ms_per_transform_one_core": 1000.0 * busy / max(1, cnt_o)}
+        # context: a dense FFT of the same n on one host core (numpy, complex128)
+        sig = np.exp(2j * np.pi * np.random.default_rng(1).random(n))
+        np.fft.fft(sig)
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            np.fft.fft(sig)
+        cpu["dense_fft_one_core"] = {"ms_per_transform": 1000.0 * (time.perf_counter() - t0) / reps,
+                                     "what": "numpy.fft.fft of n=2^22 complex128 on one host core"}
 
     if rank == 0:
         line = {
