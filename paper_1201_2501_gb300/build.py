@@ -3,7 +3,7 @@
     python -m paper_1201_2501_gb300.build [--force]
 
 Objects go to ``paper_1201_2501_gb300/_build/``; the library to ``paper_1201_2501_gb300/libsfft.so``.
-Only nvcc and the host compiler are needed (no GPU): the same command builds here and on the GPU machine.
+Only nvcc and the host compiler are needed (no GPU): the same command builds on x86-64 and Arm hosts.
 """
 from __future__ import annotations
 
