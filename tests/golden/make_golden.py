@@ -34,7 +34,7 @@ def main():
     g["philox"] = [{"ctr": c, "key": k, "out": [int(w) for w in oracle.philox4x32_10(c, k)]}
                    for c, k in (([0, 0, 0, 0], [0, 0]), ([1, 2, 3, 4], [5, 6]),
                                 ([0xFFFFFFFF, 0, 7, 0x12345678], [0xDEADBEEF, 0xCAFEF00D]))]
-    # flat window of Sec. 7 (this build's reading): T, a few taps, and the exact response W(o)
+    # flat window of Sec. 7 (the library's reading of its construction): T, a few taps, and the exact response W(o)
     n, B, a, d = 1 << 14, 32, 0.5, 1e-8
     taps = oracle.window_taps(n, B, a, d)
     offs = [0, 1, 64, 128, 192, 255, 256]
