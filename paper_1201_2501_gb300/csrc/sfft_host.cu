@@ -361,7 +361,7 @@ sfft_status build_general_schedule(sfft_plan_s* pl) {
         r.logB = ceil_log2(B);
         r.T = window_halfwidth(r.B, p.alpha0, p.delta);
         r.chunks = (uint32_t)((2 * (uint64_t)r.T + 1 + kChunkTaps - 1) / kChunkTaps);
-        r.cpb = r.chunks < 8 ? r.chunks : 8;
+        r.cpb = r.chunks < 4 ? r.chunks : 4;  // chunks per gather CTA: 4 beat 2 and 8 at n = 2^22, k = 256
         r.ctas = (r.chunks + r.cpb - 1) / r.cpb;
         r.t = t;
         r.logtp = logtp;
