@@ -180,7 +180,7 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     std::vector<float> t32(ntaps);
     for (size_t i = 0; i < ntaps; ++i) t32[i] = (float)pl->taps_host[i];
     size_t part_elems = 0, max_smem = 0, gs_max = 0, fs_max = 0, ls_max = 0, es_max = 0;
-    uint32_t maxB = 0;
+    uint32_t maxB = 0, max_groups = 0;
     // exact mode: every round's partial folds live at once (the one-launch path gathers all rounds
     // before their finishers), round t at part_off[t] of a request's region
     std::vector<size_t> part_off;
@@ -203,6 +203,7 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         if ((size_t)r.nhash * r.B > pl->bins_stride) pl->bins_stride = (size_t)r.nhash * r.B;
         if ((size_t)r.npairs * r.B > pl->phase_stride) pl->phase_stride = (size_t)r.npairs * r.B;
         if (r.B > maxB) maxB = r.B;
+        if (r.ngroups > max_groups) max_groups = r.ngroups;
         gs_max = r.smem_gather > gs_max ? r.smem_gather : gs_max;
         if (r.fin_global) {
             pl->gfin_stride = std::max(pl->gfin_stride, (r.smem_finish + 255) & ~size_t(255));
@@ -231,7 +232,9 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     SFFT_ALLOC(pl->d_taps64, ntaps * sizeof(double));
     SFFT_ALLOC(pl->d_wtab, pl->wtab_len * sizeof(double));
     SFFT_ALLOC(pl->d_part, pl->part_bytes);
-    const size_t ncounters = (size_t)max_batch * (general ? 1 : 2 * pl->rounds.size());
+    // arrival counters: per (round, request) twice in exact mode, per (request, hashing group) in
+    // general mode
+    const size_t ncounters = (size_t)max_batch * (general ? max_groups : 2 * pl->rounds.size());
     SFFT_ALLOC(pl->d_counter, ncounters * sizeof(uint32_t));
 
     SFFT_ALLOC(pl->d_zidx, (size_t)max_batch * p->z_cap * sizeof(uint32_t));
@@ -437,6 +440,7 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
             a.tw_shift = plan->tw_shift;
             a.part = reinterpret_cast<float2*>(plan->d_part);
             a.part_stride = plan->part_stride;
+            a.gcount = plan->d_counter;
             a.fin_scratch = gr.fin_global ? plan->d_gfin : nullptr;
             a.fin_stride = plan->gfin_stride;
             a.est_scratch = gr.est_global ? plan->d_gest : nullptr;

@@ -378,23 +378,6 @@ __device__ __forceinline__ double2 subtracted_u0(const C* U, uint32_t H, uint32_
 // ------------------------------------------------------------------------------------------------
 // The round kernel
 // ------------------------------------------------------------------------------------------------
-// Arrival of this CTA at a counter whose last arrival (the target-th) does the follow-up work.
-// Returns 1 in every thread of the last arriving CTA.  Only thread 0 fences: the barrier before its
-// fence orders every thread's stores before it (the fence is cumulative), and the barrier after it
-// orders its fence before every thread's loads (the same pattern as a grid-wide barrier).  Data
-// written by other CTAs of the same launch is then read through L2 (ld.global.cg).
-__device__ __forceinline__ uint32_t arrive(uint32_t* counter, uint32_t target) {
-    __shared__ uint32_t s_arrive_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const uint32_t last = atomicAdd(counter, 1u) + 1u == target ? 1u : 0u;
-        if (last) __threadfence();
-        s_arrive_last = last;
-    }
-    __syncthreads();
-    return s_arrive_last;
-}
 template <typename R>
 __device__ void gather_fold(const ExactArgs& a, const void* xrow, uint32_t xmask, uint32_t s, uint32_t c,
                             uint32_t sigma, uint32_t b, unsigned char* smem) {

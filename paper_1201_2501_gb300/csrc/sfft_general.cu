@@ -6,8 +6,9 @@
 // (a, a + beta) of every level and every EstimateValues hashing is known before any vote is counted.
 // So a round is four launches for the whole batch:
 //   1. k_gen_gather   every (chunk range, hashing group, request): permuted gather, window,
-//                     modulation, fold mod B (HashToBins steps 1-2) into partial sums;
-//   2. k_gen_finish   every (hashing group, request): partials summed in order, B-point FFT
+//                     modulation, fold mod B (HashToBins steps 1-2) into partial sums; the group's
+//                     last CTA to arrive sums them in chunk order;
+//   2. k_gen_finish   every (hashing group, request): the fold's B-point FFT
 //                     (step 3), recovered coefficients subtracted in FP64 (step 4), bins stored;
 //                     for a LocateInner pair also c_j = phase(u_j / u'_j);
 //   3. k_gen_locate   every (bin, request), t threads per bin (one per subregion): LocateSignal's
@@ -170,6 +171,26 @@ __global__ void __launch_bounds__(kThreads) k_gen_gather(const GenArgs a) {
     } else {
         for (uint32_t i = tid; i < h.H * a.B; i += kThreads) part[i] = red[i];
     }
+    // step 2 across CTAs: the last CTA of this (request, group) to arrive sums the partial folds in
+    // chunk order into slot 0, so the finish reads one fold per hashing
+    if (a.ctas == 1 || arrive(a.gcount + (size_t)s * a.ngroups + g, a.ctas) == 0) return;
+    float2* part0 = a.part + (size_t)s * a.part_stride + (size_t)g * a.ctas * 2 * a.B;
+    for (uint32_t i = tid; i < h.H * a.B; i += kThreads) {
+        const uint32_t hh = i / a.B, r = i - hh * a.B;
+        const float2* src = part0 + (size_t)hh * a.B + r;
+        float2 sum = make_float2(0.f, 0.f);
+        uint32_t c0 = 0;
+        for (; c0 + 8 <= a.ctas; c0 += 8) {  // 8 loads in flight, added in order
+            float2 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = __ldcg(src + (size_t)(c0 + q) * 2 * a.B);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sum = cadd(sum, v[q]);
+        }
+        for (; c0 < a.ctas; ++c0) sum = cadd(sum, __ldcg(src + (size_t)c0 * 2 * a.B));
+        part0[(size_t)hh * a.B + r] = sum;
+    }
+    if (tid == 0) a.gcount[(size_t)s * a.ngroups + g] = 0;  // every CTA of the group has arrived
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -217,14 +238,13 @@ __global__ void __launch_bounds__(kThreads) k_gen_finish(const GenArgs a) {
     uint32_t* bin_list = reinterpret_cast<uint32_t*>(fb + Ly.bin_list);
     uint32_t* scan = reinterpret_cast<uint32_t*>(fb + Ly.scan);
     const uint32_t logNp = (uint32_t)(63 - __clzll((long long)a.n)) - a.logB;
-    // steps 2-3: partial folds summed in chunk order, bit-reversed, B-point FFT per hashing
+    // step 3: the fold (summed over chunks by the gather's last CTA), bit-reversed, B-point FFT per
+    // hashing
     const float2* part = a.part + (size_t)s * a.part_stride + (size_t)g * a.ctas * 2 * B;
     const uint32_t shift_br = 32u - a.logB;
     for (uint32_t i = tid; i < h.H * B; i += kThreads) {
         const uint32_t hh = i / B, r = i - hh * B;
-        float2 sum = make_float2(0.f, 0.f);
-        for (uint32_t c = 0; c < a.ctas; ++c) sum = cadd(sum, __ldcg(part + ((size_t)c * 2 + hh) * B + r));
-        U[hh * B + (__brev(r) >> shift_br)] = sum;
+        U[hh * B + (__brev(r) >> shift_br)] = __ldcg(part + (size_t)hh * B + r);
     }
     // step 4 terms of the recovered coefficients: W(-o(i)) zhat_i w^{a_h sigma i}
     const uint32_t nz = min(a.zcount[s], a.zcap);

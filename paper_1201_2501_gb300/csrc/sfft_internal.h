@@ -205,8 +205,9 @@ struct GenArgs {
     const double* wtab;
     const double2* tw;     // FP64 twiddles w^e = tw[e mod 2^tw_shift] tw[2^tw_shift + (e >> tw_shift)]
     uint32_t tw_shift;
-    float2* part;          // [batch][ngroups][ctas][2][B]
+    float2* part;          // [batch][ngroups][ctas][2][B]; after the gather, ctas slot 0 holds the sum
     size_t part_stride;    // elements per request
+    uint32_t* gcount;      // [batch][ngroups] arrival counters of the gather CTAs (zero between launches)
     unsigned char* fin_scratch;  // k_gen_finish arrays in device memory: [batch][ngroups][fin_stride], or null
     size_t fin_stride;
     unsigned char* est_scratch;  // k_gen_estimate arrays in device memory: [batch][est_stride], or null
@@ -286,7 +287,8 @@ struct sfft_plan_s {
     void* d_part = nullptr;
     size_t part_bytes = 0;
     size_t part_stride = 0;  // elements of the partial-fold buffer owned by one request
-    uint32_t* d_counter = nullptr;  // [2 R][max_batch] arrival counters (zero between launches)
+    // arrival counters, zero between launches: exact [2 R][max_batch], general [max_batch][max ngroups]
+    uint32_t* d_counter = nullptr;
     std::vector<sfft::ExactArgs> rdesc;  // [R] round blocks of the one-launch exact path
     size_t step_smem = 0;                // its dynamic shared memory (largest round)
     uint32_t* d_zidx = nullptr;
