@@ -77,6 +77,7 @@ void free_plan(sfft_plan_s* pl) {
     cudaFree(pl->d_phase);
     cudaFree(pl->d_L);
     cudaFree(pl->d_nL);
+    cudaFree(pl->d_estw);
     for (int i = 0; i < sfft_plan_s::kMaxStreams; ++i) {
         if (pl->aux[i]) cudaStreamDestroy(pl->aux[i]);
         if (pl->ev_join[i]) cudaEventDestroy(pl->ev_join[i]);
@@ -216,6 +217,8 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         if (!r.est_global) es_max = r.smem_estimate > es_max ? r.smem_estimate : es_max;
     }
     pl->part_stride = part_elems;
+    pl->max_B = maxB;
+    pl->max_groups = max_groups;
     pl->part_bytes = part_elems * (size_t)max_batch * (fp64 ? 16 : 8);
     cudaError_t e = cudaSuccess;
 #define SFFT_ALLOC(ptr, bytes)                                        \
@@ -232,9 +235,9 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     SFFT_ALLOC(pl->d_taps64, ntaps * sizeof(double));
     SFFT_ALLOC(pl->d_wtab, pl->wtab_len * sizeof(double));
     SFFT_ALLOC(pl->d_part, pl->part_bytes);
-    // arrival counters: per (round, request) twice in exact mode, per (request, hashing group) in
-    // general mode
-    const size_t ncounters = (size_t)max_batch * (general ? max_groups : 2 * pl->rounds.size());
+    // arrival counters: per (round, request) twice in exact mode; per (request, hashing group) and
+    // per request in general mode
+    const size_t ncounters = (size_t)max_batch * (general ? max_groups + 1 : 2 * pl->rounds.size());
     SFFT_ALLOC(pl->d_counter, ncounters * sizeof(uint32_t));
 
     SFFT_ALLOC(pl->d_zidx, (size_t)max_batch * p->z_cap * sizeof(uint32_t));
@@ -263,6 +266,7 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         pl->tw_shift = (ilog2_host(p->n) + 1) / 2;
         SFFT_ALLOC(pl->d_tw, ((size_t(1) << pl->tw_shift) + (p->n >> pl->tw_shift)) * sizeof(double2));
         SFFT_ALLOC(pl->d_nL, (size_t)max_batch * sizeof(uint32_t));
+        SFFT_ALLOC(pl->d_estw, (size_t)max_batch * maxB * (sizeof(double2) + sizeof(double)));
     }
 #undef SFFT_ALLOC
     auto fail = [&](cudaError_t err, const char* what) {
@@ -441,6 +445,9 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
             a.part = reinterpret_cast<float2*>(plan->d_part);
             a.part_stride = plan->part_stride;
             a.gcount = plan->d_counter;
+            a.ecount = plan->d_counter + (size_t)plan->max_batch * plan->max_groups;
+            a.est_w = plan->d_estw;
+            a.est_mag = reinterpret_cast<double*>(plan->d_estw + (size_t)plan->max_batch * plan->max_B);
             a.fin_scratch = gr.fin_global ? plan->d_gfin : nullptr;
             a.fin_stride = plan->gfin_stride;
             a.est_scratch = gr.est_global ? plan->d_gest : nullptr;

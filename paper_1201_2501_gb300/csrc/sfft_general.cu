@@ -13,7 +13,8 @@
 //                     for a LocateInner pair also c_j = phase(u_j / u'_j);
 //   3. k_gen_locate   every (bin, request), t threads per bin (one per subregion): LocateSignal's
 //                     levels in order, votes, regions, the bin's candidate for the list L;
-//   4. k_gen_estimate every request: EstimateValues' medians, the top k', zhat += w_J.
+//   4. k_gen_estimate every (candidate share, request): EstimateValues' medians; the request's last
+//                     CTA takes the top k' and zhat += w_J.
 // Reductions run in a fixed order; results are bit-reproducible.
 #include <cuda_runtime.h>
 
@@ -668,9 +669,12 @@ __device__ void sort_by_magnitude(const double* mag, const uint32_t* idx, uint32
     }
 }
 
+// Grid (E, batch): the E CTAs of a request each form L and estimate their share of its candidates;
+// with E > 1 the shares go through est_w / est_mag and the last CTA to arrive takes the top k' and
+// the merge.  E = 1 when the arrays live in est_scratch (one slice per request).
 __global__ void __launch_bounds__(kThreads) k_gen_estimate(const GenArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const uint32_t s = a.req_base + blockIdx.x, tid = threadIdx.x, B = a.B;
+    const uint32_t s = a.req_base + blockIdx.y, tid = threadIdx.x, B = a.B, E = gridDim.x;
     const EstLayout Ly = est_layout(B, a.kprime, a.zcap);
     // the arrays live in shared memory, or in this request's slice of est_scratch when large
     unsigned char* eb = a.est_scratch ? a.est_scratch + (size_t)s * a.est_stride : smem;
@@ -705,15 +709,31 @@ __global__ void __launch_bounds__(kThreads) k_gen_estimate(const GenArgs a) {
     __syncthreads();
     const uint32_t nL = sort_unique_u32(Lk, s_m, Ly.P, Lt, keep, scan);
     const uint32_t* L = Lt;
-    if (tid == 0) a.nL[s] = nL;
+    if (tid == 0 && blockIdx.x == 0) a.nL[s] = nL;
     const double2* bins = a.bins + (size_t)s * a.bins_stride + (size_t)2 * a.npairs * B;
     const uint32_t logNp = (uint32_t)(63 - __clzll((long long)a.n)) - a.logB;
-    for (uint32_t c = tid; c < nL; c += kThreads) {
+    double2* gw = a.est_w + (size_t)s * B;
+    double* gmag = a.est_mag + (size_t)s * B;
+    for (uint32_t c = blockIdx.x * kThreads + tid; c < nL; c += E * kThreads) {
         const double2 w = estimate_one(L[c], a.R_est, dr, dr + kMaxRest, dr + 2 * kMaxRest,
                                        [&](uint32_t q, uint32_t j) { return bins[(size_t)q * B + j]; }, (uint32_t)a.n,
                                        a.nmask, logNp, a.wtab, a.est_gmin, a.tw, a.tw_shift);
-        wv[c] = w;
-        mag[c] = __dadd_rn(__dmul_rn(w.x, w.x), __dmul_rn(w.y, w.y));
+        const double m2 = __dadd_rn(__dmul_rn(w.x, w.x), __dmul_rn(w.y, w.y));
+        if (E == 1) {
+            wv[c] = w;
+            mag[c] = m2;
+        } else {
+            gw[c] = w;
+            gmag[c] = m2;
+        }
+    }
+    if (E > 1) {
+        if (arrive(a.ecount + s, E) == 0) return;
+        for (uint32_t c = tid; c < nL; c += kThreads) {
+            wv[c] = __ldcg(gw + c);
+            mag[c] = __ldcg(gmag + c);
+        }
+        if (tid == 0) a.ecount[s] = 0;  // every CTA of the request has arrived
     }
     __syncthreads();
     sort_by_magnitude(mag, L, nL, Ly.P, perm);
@@ -883,7 +903,8 @@ cudaError_t launch_general_round(const GenArgs& a, uint32_t batch, const General
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_gen_locate<<<dim3((r.B * r.t + kThreads - 1) / kThreads, batch), kThreads, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_gen_estimate<<<batch, kThreads, r.est_global ? 0 : r.smem_estimate, st>>>(a);
+    const uint32_t E = r.est_global ? 1u : (r.B + kThreads - 1) / kThreads;
+    k_gen_estimate<<<dim3(E, batch), kThreads, r.est_global ? 0 : r.smem_estimate, st>>>(a);
     return cudaGetLastError();
 }
 

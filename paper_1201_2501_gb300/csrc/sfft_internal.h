@@ -208,6 +208,9 @@ struct GenArgs {
     float2* part;          // [batch][ngroups][ctas][2][B]; after the gather, ctas slot 0 holds the sum
     size_t part_stride;    // elements per request
     uint32_t* gcount;      // [batch][ngroups] arrival counters of the gather CTAs (zero between launches)
+    uint32_t* ecount;      // [batch] arrival counters of the estimate CTAs (zero between launches)
+    double2* est_w;        // [batch][B] candidates' estimates shared by a request's estimate CTAs
+    double* est_mag;       // [batch][B] their squared magnitudes
     unsigned char* fin_scratch;  // k_gen_finish arrays in device memory: [batch][ngroups][fin_stride], or null
     size_t fin_stride;
     unsigned char* est_scratch;  // k_gen_estimate arrays in device memory: [batch][est_stride], or null
@@ -268,6 +271,7 @@ struct EstArgs {
 struct sfft_plan_s {
     sfft_params p{};
     uint32_t max_batch = 0;
+    uint32_t max_B = 0, max_groups = 0;  // largest B and number of hashing groups over the rounds
     int device = 0;
     std::vector<sfft::ExactRound> rounds;
     std::vector<sfft::GeneralRound> grounds;  // general mode
@@ -277,6 +281,7 @@ struct sfft_plan_s {
     double2* d_tw = nullptr;  // general mode: FP64 twiddle factor tables (2^tw_shift + n / 2^tw_shift)
     uint32_t tw_shift = 0;
     uint32_t* d_nL = nullptr;
+    double2* d_estw = nullptr;  // general mode: [max_batch][max B] estimates, then [max_batch][max B] magnitudes
     size_t bins_stride = 0, phase_stride = 0;
     std::vector<double> taps_host;  // every round's taps, FP64
     std::vector<double> wtab_host;  // every round's W(o), o = 0..n/2B
@@ -287,7 +292,8 @@ struct sfft_plan_s {
     void* d_part = nullptr;
     size_t part_bytes = 0;
     size_t part_stride = 0;  // elements of the partial-fold buffer owned by one request
-    // arrival counters, zero between launches: exact [2 R][max_batch], general [max_batch][max ngroups]
+    // arrival counters, zero between launches: exact [2 R][max_batch]; general [max_batch][max ngroups]
+    // for the gather, then [max_batch] for the estimate
     uint32_t* d_counter = nullptr;
     std::vector<sfft::ExactArgs> rdesc;  // [R] round blocks of the one-launch exact path
     size_t step_smem = 0;                // its dynamic shared memory (largest round)
