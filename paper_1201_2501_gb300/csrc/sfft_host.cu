@@ -386,7 +386,8 @@ sfft_status build_general_schedule(sfft_plan_s* pl) {
         r.smem_finish = general_finish_smem(r.B, p.z_cap);
         r.smem_locate = general_locate_smem(r.B);
         r.smem_estimate = general_estimate_smem(r.B, r.kprime, p.z_cap);
-        // arrays beyond kFinSmemMax go to device memory (one CTA per request and group uses them)
+        // arrays beyond kFinSmemMax go to device memory, one slice per CTA: the finish's per (request,
+        // group), the estimate's per request (its launch then gives each request a single CTA)
         r.fin_global = r.smem_finish > kFinSmemMax;
         r.est_global = r.smem_estimate > kFinSmemMax;
         if (r.smem_gather > 200 * 1024 || r.smem_locate > 200 * 1024) return SFFT_ERR_K_RANGE;
