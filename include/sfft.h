@@ -88,6 +88,11 @@ typedef struct sfft_params {
     uint32_t chunk_taps;   /* exact mode: window taps gathered per CTA (a power of two in [256, 8192];
                               0 -> 2048); fewer taps spread one request over more CTAs (lower latency),
                               more taps cut partial sums (batch throughput) */
+    uint32_t permuted_copy; /* general mode: 0 -> a round whose LocateInner hashings (all under the
+                              round's sigma) gather at least 2n samples first writes x_{sigma m} for
+                              every m in [n] once per request, and those hashings read it in order
+                              instead of at random (the same samples, so the same results; n complex64
+                              of device memory per request of max_batch); 1 -> never */
 } sfft_params;
 
 /* Fill *p with the library defaults for (n, k, mode); precision SFFT_FP32. */

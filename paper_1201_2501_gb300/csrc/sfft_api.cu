@@ -78,6 +78,7 @@ void free_plan(sfft_plan_s* pl) {
     cudaFree(pl->d_L);
     cudaFree(pl->d_nL);
     cudaFree(pl->d_estw);
+    cudaFree(pl->d_xperm);
     for (int i = 0; i < sfft_plan_s::kMaxStreams; ++i) {
         if (pl->aux[i]) cudaStreamDestroy(pl->aux[i]);
         if (pl->ev_join[i]) cudaEventDestroy(pl->ev_join[i]);
@@ -267,6 +268,9 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         SFFT_ALLOC(pl->d_tw, ((size_t(1) << pl->tw_shift) + (p->n >> pl->tw_shift)) * sizeof(double2));
         SFFT_ALLOC(pl->d_nL, (size_t)max_batch * sizeof(uint32_t));
         SFFT_ALLOC(pl->d_estw, (size_t)max_batch * maxB * (sizeof(double2) + sizeof(double)));
+        bool perm = false;
+        for (const GeneralRound& r : pl->grounds) perm = perm || r.perm;
+        if (perm) SFFT_ALLOC(pl->d_xperm, (size_t)max_batch * p->n * sizeof(float2));
     }
 #undef SFFT_ALLOC
     auto fail = [&](cudaError_t err, const char* what) {
@@ -411,6 +415,7 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
             GenArgs a;
             std::memset(&a, 0, sizeof(a));
             a.x = reinterpret_cast<const float2*>(d_x);
+            a.xperm = gr.perm ? plan->d_xperm : nullptr;
             a.reqs = d_reqs;
             a.n = p.n;
             a.nmask = (uint32_t)(p.n - 1);

@@ -4,7 +4,9 @@
 //
 // The hashings of one round are non-adaptive (the intuition of Sec. 4.1): every LocateInner pair
 // (a, a + beta) of every level and every EstimateValues hashing is known before any vote is counted.
-// So a round is four launches for the whole batch:
+// So a round is four launches for the whole batch (five with the permuted copy):
+//   0. k_gen_permute  (rounds whose LocateInner pairs gather >= 2n samples) every request: x_{sigma m}
+//                     for all m under the round's sigma, so that the pairs read it in order;
 //   1. k_gen_gather   every (chunk range, hashing group, request): permuted gather, window,
 //                     modulation, fold mod B (HashToBins steps 1-2) into partial sums; the group's
 //                     last CTA to arrive sums them in chunk order;
@@ -93,16 +95,47 @@ __device__ __forceinline__ int32_t gen_offset(uint32_t p, uint32_t n, uint32_t n
 }
 
 // ------------------------------------------------------------------------------------------------
+// 0. permuted copy (rounds whose LocateInner pairs gather >= 2n samples)
+// ------------------------------------------------------------------------------------------------
+// xperm[m] = x_{sigma m} for every m in [n], sigma the round's LocateInner sigma: the pairs then read
+// x_{sigma (t - a)} = xperm[(t - a) mod n] in order.  Grid (CTAs, batch); 8 loads in flight per thread.
+__global__ void __launch_bounds__(kThreads) k_gen_permute(const GenArgs a) {
+    const uint32_t s = a.req_base + blockIdx.y;
+    const ReqView rq = gen_req(a, s);
+    uint32_t sigma, b;
+    locate_sigma_b(rq.seed, rq.id, a.round, a.nmask, &sigma, &b);
+    const float2* __restrict__ x = static_cast<const float2*>(rq.x);
+    float2* __restrict__ xp = a.xperm + (size_t)s * a.n;
+    constexpr uint32_t kPer = kThreads * 8;
+    for (uint64_t m0 = (uint64_t)blockIdx.x * kPer; m0 < a.n; m0 += (uint64_t)gridDim.x * kPer) {
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint64_t m = m0 + (uint64_t)q * kThreads + threadIdx.x;
+            if (m < a.n) v[q] = __ldcg(x + ((sigma * (uint32_t)m) & rq.xmask));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint64_t m = m0 + (uint64_t)q * kThreads + threadIdx.x;
+            if (m < a.n) xp[m] = v[q];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // 1. gather and fold
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_gen_gather(const GenArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_gen_gather(const GenArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t s = a.req_base + blockIdx.z, g = blockIdx.y, c = blockIdx.x, tid = threadIdx.x;
     const ReqView rq = gen_req(a, s);
     const HashDesc h = group_desc(a, rq.seed, rq.id, g);
     float2* stage = reinterpret_cast<float2*>(smem);   // [2][kChunkTaps]
     float2* red = stage + 2 * kChunkTaps;               // [H][max(B, kThreads)]
-    const float2* __restrict__ x = static_cast<const float2*>(rq.x);
+    // a pair of a round with a permuted copy reads xperm[(t - a) mod n] = x_{sigma (t - a)} in order
+    const bool perm = a.xperm != nullptr && g < a.npairs;
+    const float2* __restrict__ x = perm ? a.xperm + (size_t)s * a.n : static_cast<const float2*>(rq.x);
+    const uint32_t xmul = perm ? 1u : h.sigma, xmask = perm ? a.nmask : rq.xmask;
     const bool big = a.B > (uint32_t)kThreads;
     if (big)
         for (uint32_t i = tid; i < h.H * a.B; i += kThreads) red[i] = make_float2(0.f, 0.f);
@@ -126,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) k_gen_gather(const GenArgs a) {
                     const bool second = f >= ntap;
                     const uint32_t i = second ? f - ntap : f;
                     const int32_t base = (int32_t)(t_lo - (int64_t)(second ? h.a[1] : h.a[0]));
-                    v[q] = __ldcg(x + ((h.sigma * (uint32_t)(base + (int32_t)i)) & rq.xmask));
+                    v[q] = __ldcg(x + ((xmul * (uint32_t)(base + (int32_t)i)) & xmask));
                 }
             }
 #pragma unroll
@@ -896,6 +929,12 @@ cudaError_t general_set_smem(size_t gather, size_t finish, size_t locate, size_t
 }
 
 cudaError_t launch_general_round(const GenArgs& a, uint32_t batch, const GeneralRound& r, cudaStream_t st) {
+    if (r.perm) {
+        const uint64_t per = (uint64_t)kThreads * 8, blocks = (a.n + per - 1) / per;
+        k_gen_permute<<<dim3((uint32_t)(blocks < 65535 ? blocks : 65535), batch), kThreads, 0, st>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     k_gen_gather<<<dim3(r.ctas, r.ngroups, batch), kThreads, r.smem_gather, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

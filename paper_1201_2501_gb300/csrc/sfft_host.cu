@@ -378,6 +378,9 @@ sfft_status build_general_schedule(sfft_plan_s* pl) {
             r.beta_hi[D - 1] = hi;
         }
         r.npairs = r.dmax * p.R_loc;
+        // the pairs share the round's sigma: when they gather >= 2n samples, one in-order pass that
+        // writes x_{sigma m} costs less than the random reads it replaces
+        r.perm = p.permuted_copy == 0 && 2 * (uint64_t)r.npairs * (2 * (uint64_t)r.T + 1) >= 2 * p.n;
         r.ngroups = r.npairs + p.R_est;
         r.nhash = 2 * r.npairs + p.R_est;
         r.taps_off = taps_off;

@@ -184,11 +184,13 @@ struct GeneralRound {
     size_t taps_off = 0, wtab_off = 0;
     size_t smem_gather = 0, smem_finish = 0, smem_locate = 0, smem_estimate = 0;
     bool fin_global = false, est_global = false;  // arrays too large for shared memory: in d_gfin / d_gest
+    bool perm = false;             // the pairs read the permuted copy x_{sigma m} (written first)
 };
 
 // Kernel argument block of the general-mode kernels of one round (passed by value).
 struct GenArgs {
     const float2* x;
+    float2* xperm;         // [batch][n] x_{sigma m} under the round's LocateInner sigma, or null
     uint64_t n;
     uint32_t nmask, logn;
     uint64_t seed;
@@ -281,6 +283,7 @@ struct sfft_plan_s {
     double2* d_tw = nullptr;  // general mode: FP64 twiddle factor tables (2^tw_shift + n / 2^tw_shift)
     uint32_t tw_shift = 0;
     uint32_t* d_nL = nullptr;
+    float2* d_xperm = nullptr;  // general mode, rounds with perm: [max_batch][n] permuted signals
     double2* d_estw = nullptr;  // general mode: [max_batch][max B] estimates, then [max_batch][max B] magnitudes
     size_t bins_stride = 0, phase_stride = 0;
     std::vector<double> taps_host;  // every round's taps, FP64

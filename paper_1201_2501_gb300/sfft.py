@@ -61,6 +61,7 @@ class SfftParams(ctypes.Structure):
         ("streams", ctypes.c_uint32),
         ("gain", ctypes.c_uint32),
         ("chunk_taps", ctypes.c_uint32),
+        ("permuted_copy", ctypes.c_uint32),
     ]
 
 

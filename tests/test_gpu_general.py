@@ -276,3 +276,28 @@ def test_general_edge_cases(sf):
         assert (s.support[0] in got[r][0].tolist()) == (s.support[0] in oi.astype(np.int64).tolist())
         assert abs(_l2l2(X, got[r][0], got[r][1], k) / _l2l2(X, oi, ov, k) - 1.0) <= 0.05
     plan.close()
+
+
+@pytest.mark.parametrize("n,k,batch", [(1 << 16, 32, 3), (1 << 22, 256, 2)])
+def test_permuted_copy_gives_the_same_results(sf, n, k, batch):
+    """A round whose LocateInner pairs gather >= 2n samples first writes x_{sigma m} (all pairs of a
+    round share sigma) and the pairs read it in order; the samples are the same, so the results are
+    bit-identical to the random gather's (permuted_copy = 1)."""
+    f = general_fields(n, k)
+    sigs = [workloads.general_noisy(n, k, workloads.seed_for(3, 60 + i)) for i in range(batch)]
+    out, used = [], []
+    for pc in (0, 1):
+        p = gpu_params(sf, f)
+        p.permuted_copy = pc
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        plan = sf.Plan(p, batch)
+        used.append(free0 - torch.cuda.mem_get_info()[0])
+        out.append(_run_gpu(sf, plan, [s.x for s in sigs], 777, f["z_cap"]))
+        plan.close()
+    if n >= 1 << 20:  # the copy (batch x n complex64) is visible in the device memory the plan holds
+        assert used[0] - used[1] >= 0.9 * batch * n * 8
+    for (ia, va, fa), (ib, vb, fb) in zip(*out):
+        assert fa == fb == 0
+        assert np.array_equal(ia, ib)
+        assert np.array_equal(va, vb)
