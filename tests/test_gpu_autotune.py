@@ -51,7 +51,7 @@ def test_autotune_picks_a_fast_accurate_setting(sf, mode):
         x = torch.as_tensor(np.stack([s.x for s in sigs])).cuda()
         idx, val, cnt, flag = (t.cpu().numpy() for t in sf.sfft_execute(plan, x, 3, best.z_cap))
         fields = {f: getattr(best, f) for f, _ in sf.SfftParams._fields_
-                  if f not in ("precision", "streams", "gain", "chunk_taps")}
+                  if f not in ("precision", "streams", "gain", "chunk_taps", "permuted_copy")}
         P = oracle_params(fields)
         for r, s in enumerate(sigs):
             gi = idx[r, :cnt[r]].view(np.uint32).astype(np.int64)
