@@ -151,7 +151,8 @@ sfft_status sfft_plan_taps(sfft_plan plan, uint32_t t, double* h_taps, uint64_t 
  *   d_flag[r]                     sfft_status of the request: OK, NOT_CONVERGED or CAPACITY
  * Exact mode follows Algorithm 1: one kernel launch per stream group covers every round, since the
  * samples of all rounds are known before any is decoded; general mode follows Algorithms 2 and 3 with
- * four launches per round.  Asynchronous on `stream`; the plan may run one call at a time.
+ * four launches per round (five in a round that writes the permuted copy; see permuted_copy).
+ * Asynchronous on `stream`; the plan may run one call at a time.
  * Errors: INVALID_ARG (null pointer, batch out of range, cap == 0), CUDA (launch failure, including a
  * batch whose chunks would exceed 2^31 - 1 CTAs).
  */
