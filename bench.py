@@ -150,14 +150,25 @@ KERNEL_SOURCES = ("sfft_exact.cu", "sfft_device.cuh", "sfft_internal.h", "philox
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_exact_step_n22_k64_b256_launches.md")
 
 
+def code_only(text):
+    """A C/CUDA source without its comments, trailing blanks and empty lines (the sources hold no
+    string literal with a comment marker in it)."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def kernel_fingerprint():
-    """First 16 hex digits of sha256 over the sha256 hex digests of the exact kernel's sources."""
+    """First 16 hex digits of sha256 over the sha256 hex digests of the exact kernel's sources, taken
+    on their code only, so that an edit of a comment keeps the committed counters valid."""
     import hashlib
 
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1201_2501_gb300", "csrc", f), "rb") as fh:
-            h.update(hashlib.sha256(fh.read()).hexdigest().encode())
+        with open(os.path.join(ROOT, "paper_1201_2501_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(hashlib.sha256(code_only(fh.read()).encode()).hexdigest().encode())
     return h.hexdigest()[:16]
 
 

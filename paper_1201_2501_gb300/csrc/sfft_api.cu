@@ -183,6 +183,7 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     for (size_t i = 0; i < ntaps; ++i) t32[i] = (float)pl->taps_host[i];
     size_t part_elems = 0, max_smem = 0, gs_max = 0, fs_max = 0, ls_max = 0, es_max = 0;
     uint32_t maxB = 0, max_groups = 0;
+    size_t sum_groups = 0, sum_B = 0;  // general: hashing groups and bins over all rounds
     // exact mode: every round's partial folds live at once (the one-launch path gathers all rounds
     // before their finishers), round t at part_off[t] of a request's region
     std::vector<size_t> part_off;
@@ -206,6 +207,8 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         if ((size_t)r.npairs * r.B > pl->phase_stride) pl->phase_stride = (size_t)r.npairs * r.B;
         if (r.B > maxB) maxB = r.B;
         if (r.ngroups > max_groups) max_groups = r.ngroups;
+        sum_groups += r.ngroups;
+        sum_B += r.B;
         gs_max = r.smem_gather > gs_max ? r.smem_gather : gs_max;
         if (r.fin_global) {
             pl->gfin_stride = std::max(pl->gfin_stride, (r.smem_finish + 255) & ~size_t(255));
@@ -236,9 +239,10 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     SFFT_ALLOC(pl->d_taps64, ntaps * sizeof(double));
     SFFT_ALLOC(pl->d_wtab, pl->wtab_len * sizeof(double));
     SFFT_ALLOC(pl->d_part, pl->part_bytes);
-    // arrival counters: per (round, request) twice in exact mode; per (request, hashing group) and
-    // per request in general mode
-    const size_t ncounters = (size_t)max_batch * (general ? max_groups + 1 : 2 * pl->rounds.size());
+    // arrival counters: per (round, request) twice in exact mode; in general mode per (round, request,
+    // hashing group), each round in its own region because stream groups may run different rounds at
+    // once, then per request
+    const size_t ncounters = (size_t)max_batch * (general ? sum_groups + 1 : 2 * pl->rounds.size());
     SFFT_ALLOC(pl->d_counter, ncounters * sizeof(uint32_t));
 
     SFFT_ALLOC(pl->d_zidx, (size_t)max_batch * p->z_cap * sizeof(uint32_t));
@@ -267,7 +271,7 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         pl->tw_shift = (ilog2_host(p->n) + 1) / 2;
         SFFT_ALLOC(pl->d_tw, ((size_t(1) << pl->tw_shift) + (p->n >> pl->tw_shift)) * sizeof(double2));
         SFFT_ALLOC(pl->d_nL, (size_t)max_batch * sizeof(uint32_t));
-        SFFT_ALLOC(pl->d_estw, (size_t)max_batch * maxB * (sizeof(double2) + sizeof(double)));
+        SFFT_ALLOC(pl->d_estw, (size_t)max_batch * sum_B * (sizeof(double2) + sizeof(double)));
         bool perm = false;
         for (const GeneralRound& r : pl->grounds) perm = perm || r.perm;
         if (perm) SFFT_ALLOC(pl->d_xperm, (size_t)max_batch * p->n * sizeof(float2));
@@ -400,6 +404,14 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
     SFFT_CUDA(cudaMemsetAsync(plan->d_zcount, 0, batch * sizeof(uint32_t), st), "clear zhat");
     SFFT_CUDA(cudaMemsetAsync(plan->d_zflag, 0, batch * sizeof(int32_t), st), "clear flags");
     const uint32_t R = (uint32_t)plan->grounds.size();
+    // stream groups may run different rounds at once, so every round has its own regions: gather
+    // counters from max_batch goff[r] (the estimate's counters at max_batch goff[R]), estimates and
+    // magnitudes from max_batch boff[r]
+    std::vector<size_t> goff(R + 1, 0), boff(R + 1, 0);
+    for (uint32_t r = 0; r < R; ++r) {
+        goff[r + 1] = goff[r] + plan->grounds[r].ngroups;
+        boff[r + 1] = boff[r] + plan->grounds[r].B;
+    }
     uint32_t groups = plan->nstreams;
     if (groups > batch) groups = batch;
     if (groups > 1) {
@@ -449,10 +461,11 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
             a.tw_shift = plan->tw_shift;
             a.part = reinterpret_cast<float2*>(plan->d_part);
             a.part_stride = plan->part_stride;
-            a.gcount = plan->d_counter;
-            a.ecount = plan->d_counter + (size_t)plan->max_batch * plan->max_groups;
-            a.est_w = plan->d_estw;
-            a.est_mag = reinterpret_cast<double*>(plan->d_estw + (size_t)plan->max_batch * plan->max_B);
+            a.gcount = plan->d_counter + (size_t)plan->max_batch * goff[r];
+            a.ecount = plan->d_counter + (size_t)plan->max_batch * goff[R];
+            a.est_w = plan->d_estw + (size_t)plan->max_batch * boff[r];
+            a.est_mag = reinterpret_cast<double*>(plan->d_estw + (size_t)plan->max_batch * boff[R]) +
+                        (size_t)plan->max_batch * boff[r];
             a.fin_scratch = gr.fin_global ? plan->d_gfin : nullptr;
             a.fin_stride = plan->gfin_stride;
             a.est_scratch = gr.est_global ? plan->d_gest : nullptr;

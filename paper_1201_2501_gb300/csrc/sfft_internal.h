@@ -284,7 +284,8 @@ struct sfft_plan_s {
     uint32_t tw_shift = 0;
     uint32_t* d_nL = nullptr;
     float2* d_xperm = nullptr;  // general mode, rounds with perm: [max_batch][n] permuted signals
-    double2* d_estw = nullptr;  // general mode: [max_batch][max B] estimates, then [max_batch][max B] magnitudes
+    // general mode: per round r, [max_batch][B_r] estimates; then per round [max_batch][B_r] magnitudes
+    double2* d_estw = nullptr;
     size_t bins_stride = 0, phase_stride = 0;
     std::vector<double> taps_host;  // every round's taps, FP64
     std::vector<double> wtab_host;  // every round's W(o), o = 0..n/2B
@@ -295,8 +296,8 @@ struct sfft_plan_s {
     void* d_part = nullptr;
     size_t part_bytes = 0;
     size_t part_stride = 0;  // elements of the partial-fold buffer owned by one request
-    // arrival counters, zero between launches: exact [2 R][max_batch]; general [max_batch][max ngroups]
-    // for the gather, then [max_batch] for the estimate
+    // arrival counters, zero between launches: exact [2 R][max_batch]; general, per round r,
+    // [max_batch][ngroups_r] for the gather, then [max_batch] for the estimate
     uint32_t* d_counter = nullptr;
     std::vector<sfft::ExactArgs> rdesc;  // [R] round blocks of the one-launch exact path
     size_t step_smem = 0;                // its dynamic shared memory (largest round)
