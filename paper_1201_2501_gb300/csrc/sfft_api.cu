@@ -212,7 +212,7 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         gs_max = r.smem_gather > gs_max ? r.smem_gather : gs_max;
         if (r.fin_global) {
             pl->gfin_stride = std::max(pl->gfin_stride, (r.smem_finish + 255) & ~size_t(255));
-            pl->gfin_groups = std::max(pl->gfin_groups, (size_t)r.ngroups);
+            pl->gfin_groups += r.ngroups;  // each such round has its own region
         } else {
             fs_max = r.smem_finish > fs_max ? r.smem_finish : fs_max;
         }
@@ -267,7 +267,7 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     if (general) {
         SFFT_ALLOC(pl->d_bins, pl->bins_stride * max_batch * sizeof(double2));
         SFFT_ALLOC(pl->d_phase, pl->phase_stride * max_batch * sizeof(double));
-        SFFT_ALLOC(pl->d_L, (size_t)maxB * max_batch * sizeof(uint32_t));
+        SFFT_ALLOC(pl->d_L, sum_B * max_batch * sizeof(uint32_t));
         pl->tw_shift = (ilog2_host(p->n) + 1) / 2;
         SFFT_ALLOC(pl->d_tw, ((size_t(1) << pl->tw_shift) + (p->n >> pl->tw_shift)) * sizeof(double2));
         SFFT_ALLOC(pl->d_nL, (size_t)max_batch * sizeof(uint32_t));
@@ -405,12 +405,14 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
     SFFT_CUDA(cudaMemsetAsync(plan->d_zflag, 0, batch * sizeof(int32_t), st), "clear flags");
     const uint32_t R = (uint32_t)plan->grounds.size();
     // stream groups may run different rounds at once, so every round has its own regions: gather
-    // counters from max_batch goff[r] (the estimate's counters at max_batch goff[R]), estimates and
-    // magnitudes from max_batch boff[r]
-    std::vector<size_t> goff(R + 1, 0), boff(R + 1, 0);
+    // counters from max_batch goff[r] (the estimate's counters at max_batch goff[R]), candidates,
+    // estimates and magnitudes from max_batch boff[r], device-memory finish arrays from
+    // max_batch foff[r] slices
+    std::vector<size_t> goff(R + 1, 0), boff(R + 1, 0), foff(R + 1, 0);
     for (uint32_t r = 0; r < R; ++r) {
         goff[r + 1] = goff[r] + plan->grounds[r].ngroups;
         boff[r + 1] = boff[r] + plan->grounds[r].B;
+        foff[r + 1] = foff[r] + (plan->grounds[r].fin_global ? plan->grounds[r].ngroups : 0);
     }
     uint32_t groups = plan->nstreams;
     if (groups > batch) groups = batch;
@@ -466,7 +468,8 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
             a.est_w = plan->d_estw + (size_t)plan->max_batch * boff[r];
             a.est_mag = reinterpret_cast<double*>(plan->d_estw + (size_t)plan->max_batch * boff[R]) +
                         (size_t)plan->max_batch * boff[r];
-            a.fin_scratch = gr.fin_global ? plan->d_gfin : nullptr;
+            a.fin_scratch =
+                gr.fin_global ? plan->d_gfin + (size_t)plan->max_batch * foff[r] * plan->gfin_stride : nullptr;
             a.fin_stride = plan->gfin_stride;
             a.est_scratch = gr.est_global ? plan->d_gest : nullptr;
             a.est_stride = plan->gest_stride;
@@ -474,7 +477,7 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
             a.phase = plan->d_phase;
             a.bins_stride = plan->bins_stride;
             a.phase_stride = plan->phase_stride;
-            a.L = plan->d_L;
+            a.L = plan->d_L + (size_t)plan->max_batch * boff[r];
             a.nL = plan->d_nL;
             a.zidx = plan->d_zidx;
             a.zval = plan->d_zval;

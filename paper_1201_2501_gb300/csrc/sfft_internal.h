@@ -279,7 +279,7 @@ struct sfft_plan_s {
     std::vector<sfft::GeneralRound> grounds;  // general mode
     double2* d_bins = nullptr;
     double* d_phase = nullptr;
-    uint32_t* d_L = nullptr;
+    uint32_t* d_L = nullptr;  // general mode: per round r, [max_batch][B_r] candidates
     double2* d_tw = nullptr;  // general mode: FP64 twiddle factor tables (2^tw_shift + n / 2^tw_shift)
     uint32_t tw_shift = 0;
     uint32_t* d_nL = nullptr;
@@ -316,8 +316,9 @@ struct sfft_plan_s {
     int reqs_cur = 0;
     unsigned char* d_fin = nullptr;   // [max_batch][fin_stride] finisher arrays of rounds with fin_global
     size_t fin_stride = 0;
-    unsigned char* d_gfin = nullptr;  // general mode: [max_batch][ngroups][gfin_stride]
-    size_t gfin_stride = 0, gfin_groups = 0;
+    // general mode, per round r with fin_global: [max_batch][ngroups_r][gfin_stride]
+    unsigned char* d_gfin = nullptr;
+    size_t gfin_stride = 0, gfin_groups = 0;  // gfin_groups: ngroups summed over those rounds
     unsigned char* d_gest = nullptr;  // general mode: [max_batch][gest_stride]
     size_t gest_stride = 0;
     size_t dev_bytes = 0;          // device memory allocated at plan creation
