@@ -314,7 +314,8 @@ struct sfft_plan_s {
     sfft::ReqDesc* h_reqs[2] = {nullptr, nullptr};
     cudaEvent_t ev_reqs[2] = {nullptr, nullptr};
     int reqs_cur = 0;
-    unsigned char* d_fin = nullptr;   // [max_batch][fin_stride] finisher arrays of rounds with fin_global
+    // finisher arrays of the exact rounds with fin_global: per such round, [max_batch][fin_stride]
+    unsigned char* d_fin = nullptr;
     size_t fin_stride = 0;
     // general mode, per round r with fin_global: [max_batch][ngroups_r][gfin_stride]
     unsigned char* d_gfin = nullptr;
