@@ -118,6 +118,15 @@ def _declare(lib):
         "or_estimate_values": (u32, [_P, _dblp, u64, u32, u32, u32, u32, _u64p, _dblp, u32, _u64p, u32, _u64p, _dblp]),
         "or_sfft_general": (i32, [_P, _dblp, u64, u32, _u64p, _dblp, _u32p]),
         "or_samples_per_hashing": (i64, [u64, u32, dbl, dbl]),
+        "or_paper_exact_decode": (u32, [_P, u32, u64, _dblp, _dblp, _u64p, _dblp, _u32p, _u32p]),
+        "or_paper_exact_inner": (u32, [_P, _dblp, u64, u32, u32, u32, _u64p, _dblp, _u64p, _dblp, _u32p, _u32p,
+                                       _dblp]),
+        "or_sfft_exact_paper": (i64, [_P, _dblp, u64, u32, _u64p, _dblp, u64]),
+        "or_locate_inner_votes_ex": (None, [_P, u32, u64, u64, u32, u64, u32, _u64p, _dblp, _dblp, i32, _u64p, _u8p,
+                                            _u32p]),
+        "or_locate_replay": (None, [_P, u32, u64, u64, u32, _u64p, _dblp, _dblp, i32, _u64p, _u8p, _u64p]),
+        "or_locate_signal_ex": (u32, [_P, _dblp, u64, u32, u32, u32, u32, _u64p, _dblp, i32, _u64p, _u64p]),
+        "or_sfft_general_ex": (i32, [_P, _dblp, u64, u32, i32, _u64p, _dblp, _u32p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -312,8 +321,10 @@ def estimate_draws(P, seed, stream, r, q):
 FRAC_BITS = 16
 
 
-def locate_inner_votes(P, B, sigma, b, t, w_fp, betas, u, up, l_fp, valid):
-    """One LocateInner level on given bins; returns updated (l_fp, valid, votes)."""
+def locate_inner_votes(P, B, sigma, b, t, w_fp, betas, u, up, l_fp, valid, paper=False):
+    """One LocateInner level on given bins; returns updated (l_fp, valid, votes).
+
+    ``paper=True`` moves each region by the listing's min Q* instead of the four best subregions."""
     betas = np.ascontiguousarray(np.asarray(betas, dtype=np.uint64))
     nrep = len(betas)
     u = _c128(u).reshape(nrep, B)
@@ -321,17 +332,47 @@ def locate_inner_votes(P, B, sigma, b, t, w_fp, betas, u, up, l_fp, valid):
     l_fp = np.ascontiguousarray(np.asarray(l_fp, dtype=np.uint64)).copy()
     valid = np.ascontiguousarray(np.asarray(valid, dtype=np.uint8)).copy()
     votes = np.zeros(B * t, dtype=np.uint32)
-    lib().or_locate_inner_votes(ctypes.byref(P), B, sigma, b, t, w_fp, nrep, _u64(betas), _dp(u), _dp(up),
-                                _u64(l_fp), valid.ctypes.data_as(_u8p), votes.ctypes.data_as(_u32p))
+    lib().or_locate_inner_votes_ex(ctypes.byref(P), B, sigma, b, t, w_fp, nrep, _u64(betas), _dp(u), _dp(up),
+                                   1 if paper else 0, _u64(l_fp), valid.ctypes.data_as(_u8p),
+                                   votes.ctypes.data_as(_u32p))
     return l_fp, valid, votes.reshape(B, t)
 
 
-def locate_signal(P, x, seed, stream, r, B, z_idx=None, z_val=None):
+def locate_signal(P, x, seed, stream, r, B, z_idx=None, z_val=None, paper=False, with_candidates=False):
+    """LocateSignal: the sorted, de-duplicated list L (and, with ``with_candidates``, each bin's
+    candidate, ``BOTTOM`` for a bin without a region)."""
     x = _c128(x)
     zi, zv = _z_arrays(z_idx, z_val)
     L = np.zeros(B, dtype=np.uint64)
-    c = lib().or_locate_signal(ctypes.byref(P), _dp(x), seed, stream, r, B, len(zi), _u64(zi), _dp(zv), _u64(L))
+    cand = np.zeros(B, dtype=np.uint64)
+    c = lib().or_locate_signal_ex(ctypes.byref(P), _dp(x), seed, stream, r, B, len(zi), _u64(zi), _dp(zv),
+                                  1 if paper else 0, _u64(L), _u64(cand))
+    if with_candidates:
+        return L[:c].copy(), cand
     return L[:c].copy()
+
+
+BOTTOM = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def locate_replay(P, B, sigma, b, betas, u, up, paper=False):
+    """LocateSignal's level loop on given bins (the replay of a run's own bins).
+
+    ``u`` / ``up``: (dmax * nrep, B) bins at a_q and a_q + beta_q, level-major; ``betas`` the matching
+    shifts.  Returns (regions (dmax, B) fixed point, valid (dmax, B), candidates (B), BOTTOM for none)."""
+    betas = np.ascontiguousarray(np.asarray(betas, dtype=np.uint64))
+    _, _, dmax = locate_geometry(P, B)
+    if len(betas) % dmax:
+        raise ValueError("betas must hold dmax x nrep shifts")
+    nrep = len(betas) // dmax
+    u = _c128(u).reshape(dmax * nrep, B)
+    up = _c128(up).reshape(dmax * nrep, B)
+    lfp = np.zeros((dmax, B), dtype=np.uint64)
+    valid = np.zeros((dmax, B), dtype=np.uint8)
+    cand = np.zeros(B, dtype=np.uint64)
+    lib().or_locate_replay(ctypes.byref(P), B, sigma, b, nrep, _u64(betas), _dp(u), _dp(up), 1 if paper else 0,
+                           _u64(lfp), valid.ctypes.data_as(_u8p), _u64(cand))
+    return lfp, valid, cand
 
 
 def estimate_from_bins(P, B, alpha, sigmas, bs, as_, u, L, kprime):
@@ -359,13 +400,15 @@ def estimate_values(P, x, seed, stream, r, B, L, kprime, z_idx=None, z_val=None)
     return wi[:c].copy(), wv[:c].copy()
 
 
-def sfft_general(P, x, seed, stream=0):
+def sfft_general(P, x, seed, stream=0, paper=False):
+    """SparseFFT (Algorithm 2); ``paper=True`` uses LocateInner's min Q* as printed."""
     x = _c128(x)
     cap = P.z_cap
     oi = np.zeros(cap, dtype=np.uint64)
     ov = np.zeros(cap, dtype=np.complex128)
     cnt = ctypes.c_uint32()
-    flag = lib().or_sfft_general(ctypes.byref(P), _dp(x), seed, stream, _u64(oi), _dp(ov), ctypes.byref(cnt))
+    flag = lib().or_sfft_general_ex(ctypes.byref(P), _dp(x), seed, stream, 1 if paper else 0, _u64(oi), _dp(ov),
+                                    ctypes.byref(cnt))
     c = cnt.value
     return oi[:c].copy(), ov[:c].copy(), int(flag)
 
@@ -376,3 +419,49 @@ def sfft(P, x, seed, stream=0):
 
 def samples_per_hashing(n, B, alpha, delta):
     return int(lib().or_samples_per_hashing(n, B, alpha, delta))
+
+
+# ---------------------------------------------------------------------------------------------
+# Paper mode of Algorithm 1 (the literal decode, integer coefficients)
+# ---------------------------------------------------------------------------------------------
+def paper_exact_decode(P, B, sigma, u, up):
+    """Algorithm 1's decode on given bins at a = 0 (``u``) and a = 1 (``up``).
+
+    Returns (indices, values, bins they came from, |J|), sorted by index."""
+    u = _c128(u)
+    up = _c128(up)
+    wi = np.zeros(B, dtype=np.uint64)
+    wv = np.zeros(B, dtype=np.complex128)
+    wj = np.zeros(B, dtype=np.uint32)
+    above = ctypes.c_uint32()
+    c = lib().or_paper_exact_decode(ctypes.byref(P), B, sigma, _dp(u), _dp(up), _u64(wi), _dp(wv),
+                                    wj.ctypes.data_as(_u32p), ctypes.byref(above))
+    return wi[:c].copy(), wv[:c].copy(), wj[:c].copy(), int(above.value)
+
+
+def paper_exact_inner(P, x, seed, stream, t, z_idx=None, z_val=None):
+    """One literal NoiselessSparseFFTInner round (hashings at a = 0 and a = 1, Ghat' subtraction)."""
+    x = _c128(x)
+    zi, zv = _z_arrays(z_idx, z_val)
+    rp = exact_round_params(P, seed, stream, t)
+    B = rp["B"]
+    wi = np.zeros(B, dtype=np.uint64)
+    wv = np.zeros(B, dtype=np.complex128)
+    wj = np.zeros(B, dtype=np.uint32)
+    above = ctypes.c_uint32()
+    u = np.zeros(2 * B, dtype=np.complex128)
+    c = lib().or_paper_exact_inner(ctypes.byref(P), _dp(x), seed, stream, t, len(zi), _u64(zi), _dp(zv), _u64(wi),
+                                   _dp(wv), wj.ctypes.data_as(_u32p), ctypes.byref(above), _dp(u))
+    return dict(idx=wi[:c].copy(), val=wv[:c].copy(), bin=wj[:c].copy(), n_above=int(above.value),
+                bins=u.reshape(2, B), **rp)
+
+
+def sfft_exact_paper(P, x, seed, stream=0, cap=1 << 16):
+    """NoiselessSparseFFT as printed: the non-zero entries of zhat (indices ascending)."""
+    x = _c128(x)
+    oi = np.zeros(cap, dtype=np.uint64)
+    ov = np.zeros(cap, dtype=np.complex128)
+    c = lib().or_sfft_exact_paper(ctypes.byref(P), _dp(x), seed, stream, _u64(oi), _dp(ov), cap)
+    if c < 0:
+        raise ValueError("zhat outgrew cap")
+    return oi[:c].copy(), ov[:c].copy()

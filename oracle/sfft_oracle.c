@@ -664,6 +664,135 @@ int or_sfft_exact(const or_params* P, const double* x, uint64_t seed, uint32_t s
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Paper mode of Algorithm 1: the literal decode, for the paper's own input model              */
+/* ------------------------------------------------------------------------------------------ */
+/*
+ * Algorithm 1 as printed, for spectra whose coefficients are integers (the assumption of Sec. 3:
+ * every X_i lies in {-L, ..., L}; with this oracle's unnormalised scale the integers are the X_i
+ * themselves).  Per round t, with the round's sigma and b (the same Philox draws as the build
+ * readings, so both modes see the same hashings):
+ *   u  = HashToBins(x, zhat, P_{sigma,0,b}),  u' = HashToBins(x, zhat, P_{sigma,1,b}), both
+ *        subtracting zhat with the closed-form gain Ghat' of Sec. 7;
+ *   J  = {j : |u_j| > thr};
+ *   for j in J, ascending:  i = sigma^{-1} round(phase(u_j / u'_j) n / 2 pi) mod n,
+ *                          v = round(u_j) (real and imaginary parts rounded to integers),
+ *                          w_i <- v (a later j that decodes the same i overwrites it);
+ *   zhat <- zhat + w.
+ * round() is round-half-up.  zhat keeps every non-zero entry (the paper bounds neither its size nor
+ * prunes it); an entry that cancels to exactly zero leaves the support.
+ */
+static double round_half_up(double v) { return floor(v + 0.5); }
+
+/* The decode of one round on given bins u (row a = 0) and up (row a = 1): returns |w|; (wi, wv)
+ * sorted by index; wj (may be NULL) receives the bin each entry was decoded from. */
+uint32_t or_paper_exact_decode(const or_params* P, uint32_t B, uint64_t sigma, const double* u_re_im,
+                               const double* up_re_im, uint64_t* wi, double* wv_re_im, uint32_t* wj, uint32_t* n_above) {
+    const uint64_t n = P->n;
+    const uint64_t sigma_inv = or_inverse_mod_pow2(sigma, n);
+    const cplx* u = (const cplx*)u_re_im;
+    const cplx* up = (const cplx*)up_re_im;
+    cplx* wv = (cplx*)wv_re_im;
+    uint32_t cnt = 0, above = 0;
+    for (uint32_t j = 0; j < B; ++j) {
+        if (!(cabs(u[j]) > P->thr)) continue;
+        ++above;
+        const double ph = phase01(u[j] / up[j]);
+        const uint64_t si = (uint64_t)round_half_up(ph * (double)n) & (n - 1);
+        const uint64_t i = mulmod(sigma_inv, si, n);
+        const cplx v = round_half_up(creal(u[j])) + I * round_half_up(cimag(u[j]));
+        uint32_t e = 0;
+        while (e < cnt && wi[e] != i) ++e;
+        wi[e] = i;
+        wv[e] = v;
+        if (wj) wj[e] = j;
+        if (e == cnt) ++cnt;
+    }
+    /* ascending index order (insertion sort: cnt <= B) */
+    for (uint32_t a = 1; a < cnt; ++a) {
+        const uint64_t ki = wi[a];
+        const cplx kv = wv[a];
+        const uint32_t kj = wj ? wj[a] : 0;
+        uint32_t b = a;
+        while (b > 0 && wi[b - 1] > ki) {
+            wi[b] = wi[b - 1];
+            wv[b] = wv[b - 1];
+            if (wj) wj[b] = wj[b - 1];
+            --b;
+        }
+        wi[b] = ki;
+        wv[b] = kv;
+        if (wj) wj[b] = kj;
+    }
+    if (n_above) *n_above = above;
+    return cnt;
+}
+
+/* One round of the literal NoiselessSparseFFTInner; u_out (may be NULL) receives the 2 x B bins. */
+uint32_t or_paper_exact_inner(const or_params* P, const double* x, uint64_t seed, uint32_t stream, uint32_t t,
+                              uint32_t nz, const uint64_t* zi, const double* zv, uint64_t* wi, double* wv,
+                              uint32_t* wj, uint32_t* n_above, double* u_out) {
+    uint32_t B, nshift;
+    double alpha;
+    int64_t T;
+    uint64_t shifts[4], sigma, sigma_inv, b;
+    or_exact_round_params(P, seed, stream, t, &B, &alpha, &T, &nshift, shifts, &sigma, &sigma_inv, &b);
+    or_window W;
+    window_init(&W, P->n, B, alpha, P->delta);
+    cplx* u = (cplx*)malloc(sizeof(cplx) * (size_t)B * 2);
+    hash_to_bins(P->n, (const cplx*)x, nz, zi, (const cplx*)zv, sigma, 0, b, &W, 1, u);
+    hash_to_bins(P->n, (const cplx*)x, nz, zi, (const cplx*)zv, sigma, 1, b, &W, 1, u + B);
+    const uint32_t c = or_paper_exact_decode(P, B, sigma, (const double*)u, (const double*)(u + B), wi, wv, wj, n_above);
+    if (u_out) memcpy(u_out, u, sizeof(cplx) * (size_t)B * 2);
+    free(u);
+    window_free(&W);
+    return c;
+}
+
+/* NoiselessSparseFFT, literal: rounds t = 0 .. ceil(log2 k) (+ extra_rounds), as or_sfft_exact.
+ * Returns the number of non-zero entries of zhat written to (out_i, out_v), at most cap; -1 when zhat
+ * holds more than cap entries (nothing written). */
+int64_t or_sfft_exact_paper(const or_params* P, const double* x, uint64_t seed, uint32_t stream, uint64_t* out_i,
+                            double* out_v, uint64_t cap) {
+    const uint32_t rounds = or_exact_rounds(P);
+    uint64_t total = 0; /* zhat gains at most B_t entries per round */
+    for (uint32_t t = 0; t < rounds; ++t) total += exact_B(P, t);
+    uint64_t* zi = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)total);
+    cplx* zv = (cplx*)malloc(sizeof(cplx) * (size_t)total);
+    const uint64_t maxB = P->n / 2;
+    uint64_t* wi = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)maxB);
+    cplx* wv = (cplx*)malloc(sizeof(cplx) * (size_t)maxB);
+    uint32_t nz = 0;
+    int overflow = 0;
+    for (uint32_t t = 0; t < rounds; ++t) {
+        const uint32_t nw = or_paper_exact_inner(P, x, seed, stream, t, nz, zi, (const double*)zv, wi, (double*)wv,
+                                                 NULL, NULL, NULL);
+        /* zhat + w; an entry equal to zero is not in the support (drop_below 0 keeps everything with
+         * |v| >= 0, so exact zeros are removed here) */
+        nz = z_merge(nz, zi, zv, nw, wi, wv, 0.0, (uint32_t)total, &overflow);
+        uint32_t m = 0;
+        for (uint32_t e = 0; e < nz; ++e)
+            if (zv[e] != 0) {
+                zi[m] = zi[e];
+                zv[m] = zv[e];
+                ++m;
+            }
+        nz = m;
+    }
+    int64_t ret = nz;
+    if ((uint64_t)nz > cap) {
+        ret = -1;
+    } else {
+        memcpy(out_i, zi, sizeof(uint64_t) * nz);
+        memcpy(out_v, zv, sizeof(cplx) * nz);
+    }
+    free(zi);
+    free(zv);
+    free(wi);
+    free(wv);
+    return ret;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* General case: SparseFFT, LocateSignal, LocateInner, EstimateValues (Algorithms 2 and 3)     */
 /* ------------------------------------------------------------------------------------------ */
 #define OR_FRAC_BITS 16 /* fixed-point fraction bits for region positions (Alg. 3: m_{j,q}) */
@@ -750,10 +879,11 @@ void or_estimate_draws(const or_params* P, uint64_t seed, uint32_t stream, uint3
  * then jumps to it; the window of four subregions with the most votes keeps the Lemma's conclusion
  * (pi(i) in [l'_j, l'_j + 4w/t]) and ignores an isolated false majority.
  * Integer arithmetic is exact: beta (m + sigma b) mod n is formed in fixed point modulo n 2^F.
+ * paper = 1 takes the listing's own choice instead: l'_j = l_j + (min Q* - 1) w / t.
  */
-void or_locate_inner_votes(const or_params* P, uint32_t B, uint64_t sigma, uint64_t b, uint32_t t, uint64_t w_fp,
-                           uint32_t nrep, const uint64_t* beta, const double* u_re_im, const double* up_re_im,
-                           uint64_t* l_fp, uint8_t* valid, uint32_t* votes_out) {
+void or_locate_inner_votes_ex(const or_params* P, uint32_t B, uint64_t sigma, uint64_t b, uint32_t t, uint64_t w_fp,
+                              uint32_t nrep, const uint64_t* beta, const double* u_re_im, const double* up_re_im,
+                              int paper, uint64_t* l_fp, uint8_t* valid, uint32_t* votes_out) {
     const uint64_t n = P->n;
     const uint64_t modmask = (n << OR_FRAC_BITS) - 1;
     const uint64_t sb_fp = mulmod(sigma, b, n) << OR_FRAC_BITS;
@@ -784,13 +914,19 @@ void or_locate_inner_votes(const or_params* P, uint32_t B, uint64_t sigma, uint6
             valid[j] = 0;
             continue;
         }
-        /* the four consecutive subregions with the most votes (ties to the smallest start) */
-        uint32_t best = 0, best_sum = 0;
-        for (uint32_t q0 = 0; q0 + 4 <= t; ++q0) {
-            const uint32_t sum = vj[q0] + vj[q0 + 1] + vj[q0 + 2] + vj[q0 + 3];
-            if (q0 == 0 || sum > best_sum) {
-                best = q0;
-                best_sum = sum;
+        uint32_t best = 0;
+        if (paper) {
+            /* Algorithm 3 as printed: l' = l + (min Q* - 1) w / t (0-based: the first majority q) */
+            while (!(2 * vj[best] > nrep)) ++best;
+        } else {
+            /* the four consecutive subregions with the most votes (ties to the smallest start) */
+            uint32_t best_sum = 0;
+            for (uint32_t q0 = 0; q0 + 4 <= t; ++q0) {
+                const uint32_t sum = vj[q0] + vj[q0 + 1] + vj[q0 + 2] + vj[q0 + 3];
+                if (q0 == 0 || sum > best_sum) {
+                    best = q0;
+                    best_sum = sum;
+                }
             }
         }
         l_fp[j] = (l_fp[j] + (uint64_t)best * (w_fp / t)) & modmask;
@@ -798,63 +934,114 @@ void or_locate_inner_votes(const or_params* P, uint32_t B, uint64_t sigma, uint6
     if (votes_out) memcpy(votes_out, v, sizeof(uint32_t) * (size_t)B * t);
     free(v);
 }
+/* The build reading (four consecutive subregions) */
+void or_locate_inner_votes(const or_params* P, uint32_t B, uint64_t sigma, uint64_t b, uint32_t t, uint64_t w_fp,
+                           uint32_t nrep, const uint64_t* beta, const double* u_re_im, const double* up_re_im,
+                           uint64_t* l_fp, uint8_t* valid, uint32_t* votes_out) {
+    or_locate_inner_votes_ex(P, B, sigma, b, t, w_fp, nrep, beta, u_re_im, up_re_im, 0, l_fp, valid, votes_out);
+}
 
 static int cmp_u64(const void* a, const void* b) {
     const uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
     return x < y ? -1 : (x > y ? 1 : 0);
 }
 
-/* LocateSignal (Algorithm 3): returns |L|; L sorted ascending and de-duplicated. */
-uint32_t or_locate_signal(const or_params* P, const double* x, uint64_t seed, uint32_t stream, uint32_t r, uint32_t B,
-                          uint32_t nz, const uint64_t* zi, const double* zv, uint64_t* Lout) {
+/* Region start of bin j before the first level: [j n/B - n/2B, + n/B) (reading of Algorithm 3's
+ * initial l^(1), centred on the bins like h) */
+static uint64_t first_region_fp(uint64_t n, uint32_t B, uint32_t j) {
+    const uint64_t Np = n / B;
+    return ((((uint64_t)j * Np) + n - Np / 2) & (n - 1)) << OR_FRAC_BITS;
+}
+
+/* A bin's candidate after the last level: sigma^{-1}(tau) + b with tau the integer nearest the centre
+ * of its last region (pi^{-1} of Algorithm 3's final l), or all ones for a bottom bin. */
+static uint64_t region_candidate(uint64_t n, uint64_t Np, uint32_t tp, uint32_t dmax, uint64_t sigma, uint64_t b,
+                                 uint64_t l_fp, uint8_t valid) {
+    if (!valid) return ~(uint64_t)0;
+    const uint64_t wlast_fp = (Np << OR_FRAC_BITS) >> ((uint64_t)dmax * (uint64_t)ilog2(tp));
+    const uint64_t tau = ((l_fp + wlast_fp / 2 + ((uint64_t)1 << (OR_FRAC_BITS - 1))) >> OR_FRAC_BITS) & (n - 1);
+    return (mulmod(or_inverse_mod_pow2(sigma, n), tau, n) + b) & (n - 1);
+}
+
+/*
+ * LocateSignal's level loop on given bins (Algorithm 3 after its hashings): the replay entry.
+ * u / up hold dmax x nrep rows of B bins, row D nrep + q being LocateInner round q of level D + 1
+ * (hashings at a_q and a_q + beta_q under the call's sigma, b); beta the matching dmax x nrep shifts.
+ * Outputs (each may be NULL): lfp_levels / valid_levels (dmax x B) the regions and bottom flags after
+ * every level, cand (B) each bin's candidate (all ones for bottom), as the hashing driver forms them.
+ */
+void or_locate_replay(const or_params* P, uint32_t B, uint64_t sigma, uint64_t b, uint32_t nrep, const uint64_t* beta,
+                      const double* u_re_im, const double* up_re_im, int paper, uint64_t* lfp_levels,
+                      uint8_t* valid_levels, uint64_t* cand) {
     const uint64_t n = P->n;
     const uint64_t Np = n / B;
     uint32_t t, tp, dmax;
     or_locate_geometry(P, B, &t, &tp, &dmax);
-    or_window W;
-    window_init(&W, n, B, P->alpha0, P->delta);
     uint64_t* l_fp = (uint64_t*)malloc(sizeof(uint64_t) * B);
     uint8_t* valid = (uint8_t*)malloc(B);
-    for (uint32_t j = 0; j < B; ++j) { /* initial regions centred on the bins: [j n/B - n/2B, +n/B) */
-        l_fp[j] = ((((uint64_t)j * Np) + n - Np / 2) & (n - 1)) << OR_FRAC_BITS;
+    for (uint32_t j = 0; j < B; ++j) {
+        l_fp[j] = first_region_fp(n, B, j);
         valid[j] = 1;
     }
-    const uint32_t R = P->R_loc;
-    cplx* u = (cplx*)malloc(sizeof(cplx) * (size_t)B * R);
-    cplx* up = (cplx*)malloc(sizeof(cplx) * (size_t)B * R);
-    uint64_t* beta = (uint64_t*)malloc(sizeof(uint64_t) * R);
-    uint64_t sigma = 0, b = 0;
     for (uint32_t D = 1; D <= dmax; ++D) {
         const uint64_t w_fp = (Np << OR_FRAC_BITS) >> ((uint64_t)(D - 1) * (uint64_t)ilog2(tp));
+        const size_t row = (size_t)(D - 1) * nrep;
+        or_locate_inner_votes_ex(P, B, sigma, b, t, w_fp, nrep, beta + row, u_re_im + 2 * row * B,
+                                 up_re_im + 2 * row * B, paper, l_fp, valid, NULL);
+        if (lfp_levels) memcpy(lfp_levels + (size_t)(D - 1) * B, l_fp, sizeof(uint64_t) * B);
+        if (valid_levels) memcpy(valid_levels + (size_t)(D - 1) * B, valid, B);
+    }
+    if (cand)
+        for (uint32_t j = 0; j < B; ++j) cand[j] = region_candidate(n, Np, tp, dmax, sigma, b, l_fp[j], valid[j]);
+    free(l_fp);
+    free(valid);
+}
+
+/* LocateSignal (Algorithm 3): the hashings of every level, then the level loop; returns |L| with L
+ * sorted ascending and de-duplicated.  cand_out (may be NULL) receives the B per-bin candidates. */
+uint32_t or_locate_signal_ex(const or_params* P, const double* x, uint64_t seed, uint32_t stream, uint32_t r, uint32_t B,
+                             uint32_t nz, const uint64_t* zi, const double* zv, int paper, uint64_t* Lout,
+                             uint64_t* cand_out) {
+    const uint64_t n = P->n;
+    uint32_t t, tp, dmax;
+    or_locate_geometry(P, B, &t, &tp, &dmax);
+    or_window W;
+    window_init(&W, n, B, P->alpha0, P->delta);
+    const uint32_t R = P->R_loc;
+    cplx* u = (cplx*)malloc(sizeof(cplx) * (size_t)B * R * dmax);
+    cplx* up = (cplx*)malloc(sizeof(cplx) * (size_t)B * R * dmax);
+    uint64_t* beta = (uint64_t*)malloc(sizeof(uint64_t) * R * dmax);
+    uint64_t sigma = 0, b = 0;
+    for (uint32_t D = 1; D <= dmax; ++D) {
         for (uint32_t q = 0; q < R; ++q) {
+            const size_t row = (size_t)(D - 1) * R + q;
             uint64_t a;
-            or_locate_draws(P, seed, stream, r, B, D, q, &sigma, &b, &a, &beta[q]);
-            hash_to_bins(n, (const cplx*)x, nz, zi, (const cplx*)zv, sigma, a, b, &W, 0, u + (size_t)q * B);
-            hash_to_bins(n, (const cplx*)x, nz, zi, (const cplx*)zv, sigma, (a + beta[q]) & (n - 1), b, &W, 0,
-                         up + (size_t)q * B);
+            or_locate_draws(P, seed, stream, r, B, D, q, &sigma, &b, &a, &beta[row]);
+            hash_to_bins(n, (const cplx*)x, nz, zi, (const cplx*)zv, sigma, a, b, &W, 0, u + row * B);
+            hash_to_bins(n, (const cplx*)x, nz, zi, (const cplx*)zv, sigma, (a + beta[row]) & (n - 1), b, &W, 0,
+                         up + row * B);
         }
-        or_locate_inner_votes(P, B, sigma, b, t, w_fp, R, beta, (const double*)u, (const double*)up, l_fp, valid, NULL);
     }
-    /* final positions: the integer nearest the centre of the last region */
-    const uint64_t wlast_fp = (Np << OR_FRAC_BITS) >> ((uint64_t)dmax * (uint64_t)ilog2(tp));
-    const uint64_t sigma_inv = or_inverse_mod_pow2(sigma, n);
+    uint64_t* cand = (uint64_t*)malloc(sizeof(uint64_t) * B);
+    or_locate_replay(P, B, sigma, b, R, beta, (const double*)u, (const double*)up, paper, NULL, NULL, cand);
+    if (cand_out) memcpy(cand_out, cand, sizeof(uint64_t) * B);
     uint32_t cnt = 0;
-    for (uint32_t j = 0; j < B; ++j) {
-        if (!valid[j]) continue;
-        const uint64_t tau = ((l_fp[j] + wlast_fp / 2 + ((uint64_t)1 << (OR_FRAC_BITS - 1))) >> OR_FRAC_BITS) & (n - 1);
-        Lout[cnt++] = (mulmod(sigma_inv, tau, n) + b) & (n - 1);
-    }
+    for (uint32_t j = 0; j < B; ++j)
+        if (cand[j] != ~(uint64_t)0) Lout[cnt++] = cand[j];
     qsort(Lout, cnt, sizeof(uint64_t), cmp_u64);
     uint32_t uniq = 0;
     for (uint32_t e = 0; e < cnt; ++e)
         if (uniq == 0 || Lout[uniq - 1] != Lout[e]) Lout[uniq++] = Lout[e];
-    free(l_fp);
-    free(valid);
+    free(cand);
     free(u);
     free(up);
     free(beta);
     window_free(&W);
     return uniq;
+}
+uint32_t or_locate_signal(const or_params* P, const double* x, uint64_t seed, uint32_t stream, uint32_t r, uint32_t B,
+                          uint32_t nz, const uint64_t* zi, const double* zv, uint64_t* Lout) {
+    return or_locate_signal_ex(P, x, seed, stream, r, B, nz, zi, zv, 0, Lout, NULL);
 }
 
 static int cmp_double(const void* a, const void* b) {
@@ -968,9 +1155,10 @@ uint32_t or_estimate_values(const or_params* P, const double* x, uint64_t seed, 
     return nJ;
 }
 
-/* SparseFFT (Algorithm 2): returns 0, or 2 when zhat overflowed z_cap. */
-int or_sfft_general(const or_params* P, const double* x, uint64_t seed, uint32_t stream, uint64_t* out_i, double* out_v,
-                    uint32_t* out_count) {
+/* SparseFFT (Algorithm 2): returns 0, or 2 when zhat overflowed z_cap.  paper = 1 runs LocateInner
+ * with the listing's min Q* (or_locate_inner_votes_ex). */
+int or_sfft_general_ex(const or_params* P, const double* x, uint64_t seed, uint32_t stream, int paper, uint64_t* out_i,
+                       double* out_v, uint32_t* out_count) {
     const uint32_t cap = P->z_cap;
     uint64_t* zi = (uint64_t*)malloc(sizeof(uint64_t) * cap);
     cplx* zv = (cplx*)malloc(sizeof(cplx) * cap);
@@ -984,7 +1172,7 @@ int or_sfft_general(const or_params* P, const double* x, uint64_t seed, uint32_t
     cplx* wv = (cplx*)malloc(sizeof(cplx) * maxB);
     for (uint32_t r = 0; r < R; ++r) {
         const uint32_t B = Bs[r];
-        const uint32_t nL = or_locate_signal(P, x, seed, stream, r, B, nz, zi, (const double*)zv, L);
+        const uint32_t nL = or_locate_signal_ex(P, x, seed, stream, r, B, nz, zi, (const double*)zv, paper, L, NULL);
         const uint32_t nJ = or_estimate_values(P, x, seed, stream, r, B, nz, zi, (const double*)zv, nL, L, 3 * krs[r], wi,
                                                (double*)wv);
         nz = z_merge(nz, zi, zv, nJ, wi, wv, 0.0, cap, &overflow);
@@ -998,6 +1186,11 @@ int or_sfft_general(const or_params* P, const double* x, uint64_t seed, uint32_t
     free(wi);
     free(wv);
     return overflow ? 2 : 0;
+}
+
+int or_sfft_general(const or_params* P, const double* x, uint64_t seed, uint32_t stream, uint64_t* out_i, double* out_v,
+                    uint32_t* out_count) {
+    return or_sfft_general_ex(P, x, seed, stream, 0, out_i, out_v, out_count);
 }
 
 /* Number of distinct samples of x one HashToBins reads: 2T+1. */

@@ -81,6 +81,23 @@ def general_noisy(n: int, k: int, seed: int, snr_db: float = 20.0, dtype=np.comp
     return SparseSignal(x=x.astype(dtype), support=support, values=values, noise_power=noise_var)
 
 
+def integer_sparse(n: int, k: int, L: int, seed: int, noise_std: float = 0.0, dtype=np.complex128) -> SparseSignal:
+    """Exactly k-sparse spectrum with integer coefficients, the input model of Sec. 3 (X_f uniform on
+    {-L, ..., L} without 0, support uniform without replacement); x = IDFT(X) in FP64, plus, when
+    noise_std > 0, circular complex Gaussian noise of that standard deviation per time sample."""
+    rng = _rng(seed)
+    support = draw_support(rng, n, k)
+    mag = rng.integers(1, L + 1, size=k)
+    sign = np.where(rng.integers(0, 2, size=k) == 1, 1, -1)
+    values = (mag * sign).astype(np.complex128)
+    X = np.zeros(n, dtype=np.complex128)
+    X[support] = values
+    x = np.fft.ifft(X)
+    if noise_std > 0.0:
+        x = x + (rng.standard_normal(n) + 1j * rng.standard_normal(n)) * (noise_std / np.sqrt(2.0))
+    return SparseSignal(x=x.astype(dtype), support=support, values=values, noise_power=noise_std ** 2)
+
+
 def periodic_extension(n: int, kdim: int, seed: int, dtype=np.complex128):
     """Sec. 5 reduction input: s in C^kdim with unit-magnitude DFT, y_t = s_{t mod kdim}.
 
