@@ -146,7 +146,9 @@ def replica_value(units_per_rank, world, steps, ms_local):
     return units_per_rank * world * steps / (ms_max / 1000.0), ms_max
 
 
-KERNEL_SOURCES = ("sfft_exact.cu", "sfft_device.cuh", "sfft_internal.h", "philox.cuh")
+# the step's kernel and the host code that sets its launch shape (grid, chunk sizes, partial-fold and
+# finisher regions): a change to any of them can change the DRAM traffic the committed launch list shows
+KERNEL_SOURCES = ("sfft_exact.cu", "sfft_device.cuh", "sfft_internal.h", "philox.cuh", "sfft_api.cu", "sfft_host.cu")
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_exact_step_n22_k64_b256_launches.md")
 
 

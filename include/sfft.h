@@ -432,6 +432,48 @@ sfft_status sfft_locate_votes(sfft_plan plan, uint32_t r, uint64_t sigma, uint64
                               uint8_t* d_valid, uint32_t* d_votes, void* stream);
 
 /*
+ * Trace of one general-mode round (Algorithm 2's loop body: LocateSignal, then EstimateValues and
+ * zhat += w_J), for checking the pipeline's decisions against a replay of Algorithms 2 and 3 on the
+ * pipeline's own bins.  Every pointer is caller-owned device memory of the sizes below, with B, D_max
+ * from sfft_plan_general_round_info for `round` and nhash = 2 D_max R_loc + R_est:
+ *   d_bins          batch x nhash x B (re, im) doubles: the round's bins after zhat was subtracted
+ *                   (HashToBins step 4); rows 2g and 2g + 1 are LocateInner round q of level D + 1
+ *                   (g = D R_loc + q, hashings at a_q and a_q + beta_q under the round's sigma, b);
+ *                   row 2 D_max R_loc + q is EstimateValues hashing q
+ *   d_regions       batch x D_max x B: each bin's region start after each level, fixed point with 16
+ *                   fraction bits, modulo n 2^16
+ *   d_valid         batch x D_max x B: 1 where the bin still has a region after that level, 0 (bottom)
+ *   d_cand          batch x B: each bin's candidate pi^{-1}(tau) after the last level (0xFFFFFFFF for
+ *                   bottom), before L is sorted and de-duplicated
+ *   d_zidx_before, d_zval_before, d_zcount_before   zhat when the round starts (batch x z_cap
+ *                   indices, batch x z_cap (re, im) doubles, batch counts)
+ *   d_zidx_after, d_zval_after, d_zcount_after      zhat when the round ends
+ */
+typedef struct sfft_general_trace {
+    uint32_t round;
+    uint32_t reserved;         /* 0 */
+    double* d_bins;
+    uint64_t* d_regions;
+    uint8_t* d_valid;
+    uint32_t* d_cand;
+    uint32_t* d_zidx_before;
+    double* d_zval_before;
+    uint32_t* d_zcount_before;
+    uint32_t* d_zidx_after;
+    double* d_zval_after;
+    uint32_t* d_zcount_after;
+} sfft_general_trace;
+
+/*
+ * sfft_execute of a general-mode plan that also records round trace->round into *trace.  The batch
+ * runs as one stream group on `stream` (results are those of sfft_execute, bit for bit: requests are
+ * independent).  Errors: INVALID_ARG (an exact-mode plan, a null pointer, round out of range), CUDA.
+ */
+sfft_status sfft_execute_trace(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, void* stream,
+                               uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag,
+                               const sfft_general_trace* trace);
+
+/*
  * EstimateValues (Algorithm 2, after its hashing loop) on caller bins: for each candidate i of the
  * ascending list d_L (nL <= B), w_i = median_q Re e_q + i median_q Im e_q over the nrep hashings
  * (sigma_q, a_q, b_q) whose window gain W(-o_q(i)) reaches est_gmin, e_q = u^{(q)}_{h_q(i)}

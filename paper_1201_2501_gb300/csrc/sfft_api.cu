@@ -405,7 +405,8 @@ sfft_status sfft_plan_taps(sfft_plan plan, uint32_t t, double* h_taps, uint64_t 
 
 static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDesc* d_reqs, uint32_t batch,
                                    uint64_t seed, cudaStream_t st,
-                                   uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag) {
+                                   uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag,
+                                   const sfft_general_trace* tr = nullptr) {
     const sfft_params& p = plan->p;
     SFFT_CUDA(cudaMemsetAsync(plan->d_zcount, 0, batch * sizeof(uint32_t), st), "clear zhat");
     SFFT_CUDA(cudaMemsetAsync(plan->d_zflag, 0, batch * sizeof(int32_t), st), "clear flags");
@@ -422,16 +423,28 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
     }
     uint32_t groups = plan->nstreams;
     if (groups > batch) groups = batch;
+    if (tr) groups = 1;  // a trace records the whole batch's round on the caller's stream
     if (groups > 1) {
         SFFT_CUDA(cudaEventRecord(plan->ev_fork, st), "fork");
         for (uint32_t g = 0; g < groups; ++g) SFFT_CUDA(cudaStreamWaitEvent(plan->aux[g], plan->ev_fork, 0), "fork");
     }
+    const size_t zc = p.z_cap;
     for (uint32_t g = 0; g < groups; ++g) {
         const uint32_t r0 = (uint32_t)((uint64_t)batch * g / groups);
         const uint32_t r1 = (uint32_t)((uint64_t)batch * (g + 1) / groups);
         cudaStream_t gs = groups > 1 ? plan->aux[g] : st;
         for (uint32_t r = 0; r < R; ++r) {
             const GeneralRound& gr = plan->grounds[r];
+            const bool traced = tr && tr->round == r;
+            if (traced) {
+                SFFT_CUDA(cudaMemcpyAsync(tr->d_zidx_before, plan->d_zidx, batch * zc * 4, cudaMemcpyDeviceToDevice, gs),
+                          "trace");
+                SFFT_CUDA(cudaMemcpyAsync(tr->d_zval_before, plan->d_zval, batch * zc * 16, cudaMemcpyDeviceToDevice,
+                                          gs),
+                          "trace");
+                SFFT_CUDA(cudaMemcpyAsync(tr->d_zcount_before, plan->d_zcount, batch * 4, cudaMemcpyDeviceToDevice, gs),
+                          "trace");
+            }
             GenArgs a;
             std::memset(&a, 0, sizeof(a));
             a.x = reinterpret_cast<const float2*>(d_x);
@@ -496,7 +509,25 @@ static sfft_status execute_general(sfft_plan plan, const void* d_x, const ReqDes
             a.out_cap = cap;
             a.out_count = d_count;
             a.out_flag = d_flag;
+            if (traced) {
+                a.dbg_lfp = tr->d_regions;
+                a.dbg_valid = tr->d_valid;
+            }
             SFFT_CUDA(launch_general_round(a, r1 - r0, gr, gs), "general round");
+            if (traced) {
+                const size_t row = (size_t)gr.nhash * gr.B * sizeof(double2);
+                SFFT_CUDA(cudaMemcpy2DAsync(tr->d_bins, row, plan->d_bins, plan->bins_stride * sizeof(double2), row,
+                                            batch, cudaMemcpyDeviceToDevice, gs),
+                          "trace");
+                SFFT_CUDA(cudaMemcpyAsync(tr->d_cand, a.L, (size_t)batch * gr.B * 4, cudaMemcpyDeviceToDevice, gs),
+                          "trace");
+                SFFT_CUDA(cudaMemcpyAsync(tr->d_zidx_after, plan->d_zidx, batch * zc * 4, cudaMemcpyDeviceToDevice, gs),
+                          "trace");
+                SFFT_CUDA(cudaMemcpyAsync(tr->d_zval_after, plan->d_zval, batch * zc * 16, cudaMemcpyDeviceToDevice, gs),
+                          "trace");
+                SFFT_CUDA(cudaMemcpyAsync(tr->d_zcount_after, plan->d_zcount, batch * 4, cudaMemcpyDeviceToDevice, gs),
+                          "trace");
+            }
         }
         if (groups > 1) {
             SFFT_CUDA(cudaEventRecord(plan->ev_join[g], gs), "join");
@@ -564,6 +595,19 @@ sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64
     if (!plan || !d_x || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
     if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
     return execute_batch(plan, d_x, nullptr, batch, seed, (cudaStream_t)stream, d_idx, d_val, cap, d_count, d_flag);
+}
+
+sfft_status sfft_execute_trace(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, void* stream,
+                               uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count, int32_t* d_flag,
+                               const sfft_general_trace* tr) {
+    if (!plan || !d_x || !d_idx || !d_val || !d_count || !d_flag || cap == 0 || !tr) return SFFT_ERR_INVALID_ARG;
+    if (batch == 0 || batch > plan->max_batch || plan->p.mode != SFFT_GENERAL) return SFFT_ERR_INVALID_ARG;
+    if (tr->round >= plan->grounds.size() || !tr->d_bins || !tr->d_regions || !tr->d_valid || !tr->d_cand ||
+        !tr->d_zidx_before || !tr->d_zval_before || !tr->d_zcount_before || !tr->d_zidx_after || !tr->d_zval_after ||
+        !tr->d_zcount_after)
+        return SFFT_ERR_INVALID_ARG;
+    return execute_general(plan, d_x, nullptr, batch, seed, (cudaStream_t)stream, d_idx, d_val, cap, d_count, d_flag,
+                           tr);
 }
 
 sfft_status sfft_plan_set_requests(sfft_plan plan, const sfft_request* h_reqs, uint32_t batch, void* stream) {

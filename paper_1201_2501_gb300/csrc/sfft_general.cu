@@ -330,13 +330,22 @@ __global__ void __launch_bounds__(kThreads) k_gen_finish(const GenArgs a) {
 struct VoteBounds {
     uint64_t ilo, len;    // e is inside iff (e - ilo) mod M <= len
     uint64_t amb0, amb1;  // integers within 0.25 of a boundary (or ~0 when none)
+    uint64_t g0, g1;      // starts of the guard windows around the two arc ends (glen = 0: none)
+    uint64_t glen;        // e with (e - g0) mod M <= glen or (e - g1) mod M <= glen is in a window
     double c;
 };
 constexpr int kVoteGuard = 16;  // extra fraction bits of the fixed-point boundaries
+// Guard band of an FP32 phase.  The pipeline's c comes from an FP32 arctangent of the FP64
+// product u_j conj(u'_j): rounding the product to float and atan2f's few-ulp error move it by less
+// than 2e-7 of a turn from the FP64 phase.  A vote whose e lies within 2^-20 of a turn (about 1e-6)
+// of an arc end of c is decided by the FP64 test on the FP64 phase instead; every other e is at
+// least 2^-20 - 2e-7 of a turn from the arc ends of either phase, so both give the same vote.
+constexpr int kPhaseGuardLog = 20;
 // Boundaries of the vote arc (c - s/2, c + s/2) in units of 1/M, as 64-bit fixed point with
 // kVoteGuard fraction bits: c M 2^G is one exact scaling of c (truncated to an integer, an error
-// below 2^-G units), so only one double operation is spent per (bin, round).
-__device__ __forceinline__ VoteBounds vote_bounds(double c, int64_t hw_fix, uint32_t logM) {
+// below 2^-G units), so only one double operation is spent per (bin, round).  guard: half width of
+// the guard windows in units of 1/M (0 for an FP64 phase, which needs none).
+__device__ __forceinline__ VoteBounds vote_bounds(double c, int64_t hw_fix, uint32_t logM, uint64_t guard = 0) {
     VoteBounds v;
     const int64_t one = int64_t(1) << kVoteGuard, frac_mask = one - 1;
     const int64_t xfix = (int64_t)(c * ldexp(1.0, (int)logM + kVoteGuard));
@@ -351,20 +360,30 @@ __device__ __forceinline__ VoteBounds vote_bounds(double c, int64_t hw_fix, uint
                           : (fl > 3 * (one / 4) ? ((uint64_t)((blf >> kVoteGuard) + 1) & mask) : ~0ull);
     v.amb1 = fh < one / 4 ? ((uint64_t)(bhf >> kVoteGuard) & mask)
                           : (fh > 3 * (one / 4) ? ((uint64_t)((bhf >> kVoteGuard) + 1) & mask) : ~0ull);
+    v.g0 = (uint64_t)((blf >> kVoteGuard) - (int64_t)guard) & mask;
+    v.g1 = (uint64_t)((bhf >> kVoteGuard) - (int64_t)guard) & mask;
+    v.glen = 2 * guard + 1;
+    if (guard == 0) v.glen = 0;
     v.c = c;
     return v;
+}
+__device__ __forceinline__ bool in_guard(const VoteBounds& v, uint64_t e, uint64_t mask) {
+    return v.glen != 0 && (((e - v.g0) & mask) <= v.glen || ((e - v.g1) & mask) <= v.glen);
+}
+// The vote test on a given phase c, as written in Algorithm 3 (circular distance below s pi), in
+// double precision: the decision of a guarded e.
+__device__ __forceinline__ bool vote_hit_exact(double c, uint64_t e, uint64_t M, double s) {
+    const double f = (double)e / (double)M;
+    double dist = fabs(f - c);
+    if (dist > 0.5) dist = 1.0 - dist;
+    return dist < s / 2.0;
 }
 // half width s M / 2 of the vote arc in the same fixed point
 __device__ __forceinline__ int64_t vote_halfwidth(double s, uint32_t logM) {
     return (int64_t)llrint(0.5 * s * ldexp(1.0, (int)logM + kVoteGuard));
 }
 __device__ __forceinline__ bool vote_hit(const VoteBounds& v, uint64_t e, uint64_t M, double s) {
-    if (e == v.amb0 || e == v.amb1) {
-        const double f = (double)e / (double)M;
-        double dist = fabs(f - v.c);
-        if (dist > 0.5) dist = 1.0 - dist;
-        return dist < s / 2.0;
-    }
+    if (e == v.amb0 || e == v.amb1) return vote_hit_exact(v.c, e, M, s);
     return ((e - v.ilo) & (M - 1)) <= v.len;
 }
 
@@ -527,7 +546,9 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
     const uint32_t logM = (uint32_t)(63 - __clzll((long long)n)) + kFracBits;
     const uint64_t M = uint64_t(1) << logM, mask = M - 1;
     const int64_t hw_fix = vote_halfwidth(a.s, logM);
+    const uint64_t guard = M >> kPhaseGuardLog;
     const uint64_t sb_fp = ((uint64_t)((sigma * b) & a.nmask)) << kFracBits;
+    const double2* rbins = a.bins + (size_t)s * a.bins_stride;
     if (q == 0) {
         // the region of bin j starts centred on the bin: [j n/B - n/2B, + n/B)
         s_l[lb] = ((((uint64_t)j * Np) + n - Np / 2) & (n - 1)) << kFracBits;
@@ -545,7 +566,8 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
         const bool valid = s_valid[lb] != 0;
         const double* ph = phase + (size_t)D * a.R_loc * B;
         if (valid)
-            for (uint32_t r = q; r < a.R_loc; r += t) s_vb[lb][r] = vote_bounds(ph[(size_t)r * B + j], hw_fix, logM);
+            for (uint32_t r = q; r < a.R_loc; r += t)
+                s_vb[lb][r] = vote_bounds(ph[(size_t)r * B + j], hw_fix, logM, guard);
         __syncthreads();
         const uint64_t w_fp = (Np << kFracBits) >> ((uint64_t)D * a.logtp);
         const uint64_t half_step = w_fp / (2 * (uint64_t)t), step = w_fp / t;
@@ -556,7 +578,17 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
                 // e_q = beta (m_q + sigma b) mod M, m_q = l + (2q - 1) w / 2t
                 const uint64_t e0 = (s_beta[r] * ((l_fp + half_step + sb_fp) & mask)) & mask;
                 const uint64_t de = (s_beta[r] * step) & mask;
-                if (vote_hit(s_vb[lb][r], (e0 + (uint64_t)q * de) & mask, M, a.s)) ++v;
+                const uint64_t e = (e0 + (uint64_t)q * de) & mask;
+                const VoteBounds& vb = s_vb[lb][r];
+                bool hit;
+                if (in_guard(vb, e, mask)) {
+                    // near an arc end of the FP32 phase: the FP64 phase of the pair's stored bins
+                    const double2* pb = rbins + (size_t)2 * (D * a.R_loc + r) * B;
+                    hit = vote_hit_exact(phase01<double>(mul_conj_rn(pb[j], pb[B + j])), e, M, a.s);
+                } else {
+                    hit = vote_hit(vb, e, M, a.s);
+                }
+                if (hit) ++v;
             }
         }
         s_votes[tid] = v;
@@ -578,6 +610,10 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
                 }
                 s_l[lb] = (s_l[lb] + (uint64_t)best * step) & mask;
             }
+        }
+        if (q == 0 && j < B && a.dbg_lfp) {  // trace: the region and flag after this level
+            a.dbg_lfp[((size_t)s * a.dmax + D) * B + j] = s_l[lb];
+            a.dbg_valid[((size_t)s * a.dmax + D) * B + j] = (uint8_t)(s_valid[lb] != 0);
         }
     }
     __syncthreads();

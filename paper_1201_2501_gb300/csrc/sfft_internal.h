@@ -233,6 +233,8 @@ struct GenArgs {
     uint32_t out_cap;
     uint32_t* out_count;
     int32_t* out_flag;
+    uint64_t* dbg_lfp;     // trace (or null): [batch][dmax][B] region starts after each LocateInner level
+    uint8_t* dbg_valid;    // trace (or null): [batch][dmax][B] 0 where the bin is bottom after that level
 };
 
 // One LocateInner level on caller bins (sfft_locate_votes).

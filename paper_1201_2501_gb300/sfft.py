@@ -111,6 +111,16 @@ class SfftTuneEntry(ctypes.Structure):
                 ("chosen", ctypes.c_uint32), ("rel_err", ctypes.c_double)]
 
 
+class SfftGeneralTrace(ctypes.Structure):
+    """Mirror of ``sfft_general_trace`` (device pointers of one traced general round)."""
+
+    _fields_ = [("round", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("d_bins", ctypes.c_void_p),
+                ("d_regions", ctypes.c_void_p), ("d_valid", ctypes.c_void_p), ("d_cand", ctypes.c_void_p),
+                ("d_zidx_before", ctypes.c_void_p), ("d_zval_before", ctypes.c_void_p),
+                ("d_zcount_before", ctypes.c_void_p), ("d_zidx_after", ctypes.c_void_p),
+                ("d_zval_after", ctypes.c_void_p), ("d_zcount_after", ctypes.c_void_p)]
+
+
 class SfftError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -167,6 +177,8 @@ _SIGS = {
     "sfft_poll": (ctypes.c_int, [_vp, _u64]),
     "sfft_wait": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(SfftJobResult)]),
     "sfft_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(SfftServerStats)]),
+    "sfft_execute_trace": (ctypes.c_int, [_vp, _vp, _u32, _u64, _vp, _vp, _vp, _u32, _vp, _vp,
+                                          ctypes.POINTER(SfftGeneralTrace)]),
 }
 
 SFFT_STATIC_SCRATCH_BYTES = 4 * 1024 * 1024
@@ -595,6 +607,16 @@ def sfft_philox(key0: int, key1: int, ctr, count: int, out, stream=None):
     return out
 
 
+def _need(t, what, numel, dtypes):
+    """A device tensor of at least ``numel`` elements of one of ``dtypes``, contiguous (the C side cannot
+    check the sizes of raw pointers)."""
+    ok = (t is not None and getattr(t, "is_cuda", False) and t.is_contiguous() and t.dtype in dtypes
+          and t.numel() >= numel)
+    if not ok:
+        raise SfftError(SFFT_ERR_INVALID_ARG, f"{what}: need a contiguous CUDA tensor of >= {numel} "
+                                              f"elements of {[str(d) for d in dtypes]}")
+
+
 def sfft_hash_to_bins_static(n: int, B: int, T: int, taps, wtab, x, sigma: int, a: int, b: int, zidx=None, zval=None,
                              out=None, stream=None):
     """HashToBins that allocates nothing (``sfft_hash_to_bins_static`` in include/sfft.h).
@@ -602,11 +624,64 @@ def sfft_hash_to_bins_static(n: int, B: int, T: int, taps, wtab, x, sigma: int, 
     For callers that must not call the CUDA allocator: every buffer is the caller's device tensor
     (``taps`` float32 [T+1], ``wtab`` float64 [n/(2B)+1] or None when there is no zhat, ``x``
     complex64 [n], ``out`` float64 [B, 2]); scratch comes from an array compiled into the library.
-    Calls that overlap on the GPU share that scratch and race: serialise them."""
+    Calls that overlap on the GPU share that scratch and race: serialise them.  The tensors' devices,
+    types, sizes and layouts are checked here (SfftError INVALID_ARG), since the C side only sees
+    pointers."""
+    import torch
+
     nz = 0 if zidx is None else int(zidx.numel())
+    if B <= 0 or n <= 0 or T < 0 or n % (2 * B):
+        raise SfftError(SFFT_ERR_INVALID_ARG, "sfft_hash_to_bins_static: bad n, B or T")
+    _need(taps, "taps", T + 1, (torch.float32,))
+    if x is not None and x.dtype == torch.float32:  # interleaved (re, im) pairs
+        _need(x, "x", 2 * n, (torch.float32,))
+    else:
+        _need(x, "x", n, (torch.complex64,))
+    _need(out, "out", 2 * B, (torch.float64,))
+    if nz > 0:
+        _need(wtab, "wtab", n // (2 * B) + 1, (torch.float64,))
+        _need(zidx, "zidx", nz, (torch.int32,))
+        _need(zval, "zval", 2 * nz, (torch.float64,))
     _check(lib().sfft_hash_to_bins_static(n, B, T, _ptr(taps), _ptr(wtab), _ptr(x), sigma, a, b, _ptr(zidx),
                                           _ptr(zval), nz, _ptr(out), _stream_ptr(stream)), "sfft_hash_to_bins_static")
     return out
+
+
+def sfft_execute_trace(plan: Plan, x, seed: int, cap: int, round_: int, stream=None):
+    """sfft_execute of a general-mode batch that also records round ``round_`` (sfft_execute_trace).
+
+    Returns (outputs as sfft_execute, trace dict of device tensors: bins [batch, nhash, B, 2] float64,
+    regions [batch, dmax, B] int64 (uint64 bits), valid [batch, dmax, B] uint8, cand [batch, B] int32
+    (uint32 bits), zidx/zval/zcount before and after the round)."""
+    import torch
+
+    batch = x.shape[0] if x.dim() == 2 else 1
+    dev = x.device
+    g = general_round_info(plan, round_)
+    B, dmax = g["B"], g["dmax"]
+    nhash = 2 * dmax * plan.params.R_loc + plan.params.R_est
+    zc = plan.params.z_cap
+    tr = dict(bins=torch.zeros((batch, nhash, B, 2), dtype=torch.float64, device=dev),
+              regions=torch.zeros((batch, dmax, B), dtype=torch.int64, device=dev),
+              valid=torch.zeros((batch, dmax, B), dtype=torch.uint8, device=dev),
+              cand=torch.zeros((batch, B), dtype=torch.int32, device=dev),
+              zidx_before=torch.zeros((batch, zc), dtype=torch.int32, device=dev),
+              zval_before=torch.zeros((batch, zc, 2), dtype=torch.float64, device=dev),
+              zcount_before=torch.zeros((batch,), dtype=torch.int32, device=dev),
+              zidx_after=torch.zeros((batch, zc), dtype=torch.int32, device=dev),
+              zval_after=torch.zeros((batch, zc, 2), dtype=torch.float64, device=dev),
+              zcount_after=torch.zeros((batch,), dtype=torch.int32, device=dev))
+    st = SfftGeneralTrace(round_, 0, *[tr[k].data_ptr() for k in ("bins", "regions", "valid", "cand", "zidx_before",
+                                                                  "zval_before", "zcount_before", "zidx_after",
+                                                                  "zval_after", "zcount_after")])
+    outputs = (torch.empty((batch, cap), dtype=torch.int32, device=dev),
+               torch.empty((batch, cap, 2), dtype=torch.float64, device=dev),
+               torch.empty((batch,), dtype=torch.int32, device=dev),
+               torch.empty((batch,), dtype=torch.int32, device=dev))
+    idx, val, count, flag = outputs
+    _check(lib().sfft_execute_trace(plan.handle, _ptr(x), batch, seed, _stream_ptr(stream), _ptr(idx), _ptr(val), cap,
+                                    _ptr(count), _ptr(flag), ctypes.byref(st)), "sfft_execute_trace")
+    return outputs, tr
 
 
 def general_round_info(plan: Plan, r: int) -> dict:

@@ -301,3 +301,144 @@ def test_permuted_copy_gives_the_same_results(sf, n, k, batch):
         assert fa == fb == 0
         assert np.array_equal(ia, ib)
         assert np.array_equal(va, vb)
+
+
+# ------------------------------------------------------------------------------------------------
+# Element-wise parity of the pipeline: its decisions replayed by the oracle on its own bins
+# ------------------------------------------------------------------------------------------------
+def _c(a):
+    return a[..., 0] + 1j * a[..., 1]
+
+
+@pytest.mark.parametrize("m,k,batch", [(14, 8, 4), (16, 32, 3), (18, 64, 2)])
+def test_general_pipeline_decisions_replay_bit_exact(sf, m, k, batch):
+    """Every round of the pipeline is traced (sfft_execute_trace) and its decisions replayed by the
+    oracle on the pipeline's own subtracted FP64 bins:
+      * LocateSignal (Algorithm 3): each level's regions and bottom flags and each bin's candidate,
+        bit for bit (the FP32 phases of the pipeline decide like the FP64 phases, through the guard
+        band around every vote arc end);
+      * EstimateValues (Algorithm 2): the kept indices bit for bit and their estimates within 1e-12,
+        and zhat after the round = zhat before + w_J;
+    and the bins themselves are within the FP32 tolerance (2e-5 of the hashing's largest bin) of the
+    oracle's FP64 HashToBins of the same signal, draws and zhat.  The traced run returns what
+    sfft_execute returns."""
+    n = 1 << m
+    f = general_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f), batch)
+    sigs = [workloads.general_noisy(n, k, workloads.seed_for(3, 80 + i)) for i in range(batch)]
+    x = torch.as_tensor(np.stack([s.x for s in sigs])).cuda()
+    seed = 4242
+    ref = _run_gpu(sf, plan, [s.x for s in sigs], seed, f["z_cap"])
+    ks, Bs = oracle.general_rounds(P)
+    for r in range(len(Bs)):
+        (idx, val, cnt, flag), tr = sf.sfft_execute_trace(plan, x, seed, f["z_cap"], r)
+        torch.cuda.synchronize()
+        cnt = cnt.cpu().numpy()
+        for s_ in range(batch):
+            c = int(cnt[s_])
+            assert np.array_equal(idx[s_, :c].cpu().numpy().view(np.uint32).astype(np.int64), ref[s_][0])
+            assert np.array_equal(_c(val[s_, :c].cpu().numpy()), ref[s_][1])
+        B = Bs[r]
+        t, tp, dmax = oracle.locate_geometry(P, B)
+        npairs = dmax * P.R_loc
+        bins = _c(tr["bins"].cpu().numpy())
+        regions = tr["regions"].cpu().numpy().view(np.uint64)
+        valid = tr["valid"].cpu().numpy()
+        cand = tr["cand"].cpu().numpy().view(np.uint32)
+        zb = (tr["zidx_before"].cpu().numpy().view(np.uint32), _c(tr["zval_before"].cpu().numpy()),
+              tr["zcount_before"].cpu().numpy())
+        za = (tr["zidx_after"].cpu().numpy().view(np.uint32), _c(tr["zval_after"].cpu().numpy()),
+              tr["zcount_after"].cpu().numpy())
+        for s_ in range(batch):
+            betas, draws = [], []
+            for D in range(1, dmax + 1):
+                for q in range(P.R_loc):
+                    d = oracle.locate_draws(P, seed, s_, r, B, D, q)
+                    betas.append(d["beta"])
+                    draws.append(d)
+            sigma, b = draws[0]["sigma"], draws[0]["b"]
+            u, up = bins[s_, 0:2 * npairs:2], bins[s_, 1:2 * npairs:2]
+            olfp, ovalid, ocand = oracle.locate_replay(P, B, sigma, b, betas, u, up)
+            assert np.array_equal(valid[s_], ovalid), (r, s_)
+            assert np.array_equal(regions[s_], olfp), (r, s_)
+            ocand32 = np.where(ocand == oracle.BOTTOM, np.uint64(0xFFFFFFFF), ocand).astype(np.uint32)
+            assert np.array_equal(cand[s_], ocand32), (r, s_)
+            L = np.unique(ocand[ocand != oracle.BOTTOM])
+            ed = [oracle.estimate_draws(P, seed, s_, r, q) for q in range(P.R_est)]
+            ue = bins[s_, 2 * npairs:2 * npairs + P.R_est]
+            wi, wv = oracle.estimate_from_bins(P, B, P.alpha0, [e["sigma"] for e in ed], [e["b"] for e in ed],
+                                               [e["a"] for e in ed], ue, L, 3 * ks[r])
+            nzb = int(zb[2][s_])
+            merged = {int(i): v for i, v in zip(zb[0][s_, :nzb], zb[1][s_, :nzb])}
+            for i, v in zip(wi.astype(np.int64), wv):
+                merged[int(i)] = merged[int(i)] + v if int(i) in merged else v
+            keys = sorted(merged)[:f["z_cap"]]
+            nza = int(za[2][s_])
+            assert nza == len(keys), (r, s_)
+            assert np.array_equal(za[0][s_, :nza].astype(np.int64), np.array(keys, dtype=np.int64))
+            want = np.array([merged[i] for i in keys])
+            got = za[1][s_, :nza]
+            assert np.max(np.abs(got - want), initial=0.0) <= 1e-12 * max(1.0, np.max(np.abs(want), initial=0.0))
+            # the bins: FP32 pipeline against the oracle's FP64 HashToBins (first pair of each level,
+            # first estimation hashing)
+            zi_b = zb[0][s_, :nzb].astype(np.uint64)
+            zv_b = zb[1][s_, :nzb]
+            x128 = sigs[s_].x.astype(np.complex128)
+            for row, (sg, aa, bb) in [(2 * D * P.R_loc, (draws[D * P.R_loc]["sigma"], draws[D * P.R_loc]["a"],
+                                                         draws[D * P.R_loc]["b"])) for D in range(dmax)] + \
+                    [(2 * npairs, (ed[0]["sigma"], ed[0]["a"], ed[0]["b"]))]:
+                ob = oracle.hash_to_bins(x128, sg, aa, bb, B, P.alpha0, P.delta, zi_b, zv_b)
+                scale = max(1.0, float(np.max(np.abs(ob))))
+                assert np.max(np.abs(bins[s_, row] - ob)) <= 2e-5 * scale, (r, s_, row)
+    plan.close()
+
+
+@pytest.mark.parametrize("m,k,batch", [(14, 8, 6), (16, 32, 4), (18, 64, 2)])
+def test_sfft_general_matches_oracle_elementwise(sf, m, k, batch):
+    """Whole transforms (FP32 data path) against the FP64 oracle on the same signals and draws: the
+    recovered supports are identical and the values agree within 1e-5 relative to the largest
+    recovered magnitude on the shared support."""
+    n = 1 << m
+    f = general_fields(n, k)
+    P = oracle_params(f)
+    plan = sf.Plan(gpu_params(sf, f), batch)
+    sigs = [workloads.general_noisy(n, k, workloads.seed_for(3, 40 + i)) for i in range(batch)]
+    seed = 555
+    got = _run_gpu(sf, plan, [s.x for s in sigs], seed, f["z_cap"])
+    for r, s in enumerate(sigs):
+        oi, ov, of = oracle.sfft_general(P, s.x.astype(np.complex128), seed, r)
+        assert got[r][2] == of == 0
+        assert np.array_equal(got[r][0], oi.astype(np.int64)), (r, len(got[r][0]), len(oi))
+        scale = max(1.0, float(np.max(np.abs(ov), initial=0.0)))
+        assert np.max(np.abs(got[r][1] - ov), initial=0.0) <= 1e-5 * scale
+    plan.close()
+
+
+def test_sfft_general_large_k_stream_groups(sf):
+    """General k = 512 (B = z_cap = 4096: the finish arrays of the first rounds live in device memory,
+    one region per round) with a batch of 8 over 4 stream groups, which run different rounds at the
+    same time: every request's output is bit-identical to the one-group run, and the mean l2/l2 ratio
+    is within 1.05x of the oracle's on the requests checked."""
+    n, k, batch = 1 << 18, 512, 8
+    f = general_fields(n, k)
+    P = oracle_params(f)
+    sigs = [workloads.general_noisy(n, k, workloads.seed_for(3, 90 + i)) for i in range(batch)]
+    res = []
+    for streams in (1, 4):
+        p = gpu_params(sf, f)
+        p.streams = streams
+        plan = sf.Plan(p, batch)
+        res.append(_run_gpu(sf, plan, [s.x for s in sigs], 31, f["z_cap"]))
+        plan.close()
+    for (ia, va, fa), (ib, vb, fb) in zip(*res):
+        assert fa == fb == 0
+        assert np.array_equal(ia, ib) and np.array_equal(va, vb)
+    rg, ro = [], []
+    for r in (0, batch - 1):
+        x128 = sigs[r].x.astype(np.complex128)
+        X = np.fft.fft(x128)
+        oi, ov, _ = oracle.sfft_general(P, x128, 31, r)
+        rg.append(_l2l2(X, res[1][r][0], res[1][r][1], k))
+        ro.append(_l2l2(X, oi, ov, k))
+    assert abs(np.mean(rg) / np.mean(ro) - 1.0) <= 0.05, (rg, ro)

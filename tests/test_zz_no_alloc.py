@@ -1,14 +1,16 @@
-"""sfft_hash_to_bins_static, the HashToBins entry point that allocates nothing, against sfft_hash_to_bins.
+"""sfft_hash_to_bins_static, the HashToBins entry point that allocates nothing, against sfft_hash_to_bins
+and against the FP64 oracle.
 
 The static entry point serves callers that may not use the CUDA allocator; its scratch is an array
-compiled into the library.  Both entry points launch the same kernel, so on the same inputs the bins
-must agree within the tolerance of the FP32 parity tests (2e-5 of the largest bin), on two calls in a
-row (the second call finds the first call's leftovers in the shared scratch).  This file is collected
-last so that a failure here leaves every other test already run.
+compiled into the library.  On the same inputs its bins must agree with the plan's entry point and
+with the oracle's HashToBins within the tolerance of the FP32 parity tests (2e-5 of the largest bin),
+on two calls in a row (the second call finds the first call's leftovers in the shared scratch).  This
+file is collected last so that a failure here leaves every other test already run.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1201_2501_gb300 import workloads
 from tests.common import exact_fields
 
@@ -57,6 +59,9 @@ def test_static_hash_to_bins_matches_plan_entry_point(n, k, nz):
         torch.cuda.synchronize()
         ref = ref.cpu().numpy()
         scale = max(1.0, float(np.max(np.abs(ref))))
+        zi_o = None if zi is None else zi.cpu().numpy().astype(np.uint64)
+        zv_o = None if zv is None else zv.cpu().numpy() @ np.array([1.0, 1.0j])
+        ora = oracle.hash_to_bins(sig.x.astype(np.complex128), sigma, a, b, B, info["alpha"], f["delta"], zi_o, zv_o)
         for call in range(2):  # two calls in a row share the static scratch
             out = torch.full((B, 2), float("nan"), dtype=torch.float64, device="cuda")
             sfft.sfft_hash_to_bins_static(n, B, T, taps, wtab, x, sigma, a, b, zi, zv, out)
@@ -64,11 +69,20 @@ def test_static_hash_to_bins_matches_plan_entry_point(n, k, nz):
             got = out.cpu().numpy()
             assert np.all(np.isfinite(got))
             assert np.max(np.abs(got - ref)) <= 2e-5 * scale, f"call {call} of round {t}"
+            assert np.max(np.abs((got[:, 0] + 1j * got[:, 1]) - ora)) <= 2e-5 * scale, f"oracle, call {call}"
     # a window whose partial sums exceed the static scratch is refused before any launch
     big_T = (sfft.SFFT_STATIC_SCRATCH_BYTES // (8 * 4096) + 1) * 2048
-    dummy = torch.zeros(1, dtype=torch.float32, device="cuda")
+    dummy = torch.zeros(big_T + 1, dtype=torch.float32, device="cuda")
     with pytest.raises(sfft.SfftError) as ei:
         sfft.sfft_hash_to_bins_static(n, 4096, big_T, dummy, None, x, 1, 0, 0, None, None,
                                       torch.empty((4096, 2), dtype=torch.float64, device="cuda"))
     assert ei.value.status == sfft.SFFT_ERR_CAPACITY
     plan.close()
+    # buffers the C side cannot size-check are refused by the binding before the call
+    with pytest.raises(sfft.SfftError) as ei:
+        sfft.sfft_hash_to_bins_static(n, 16, 100, torch.zeros(50, dtype=torch.float32, device="cuda"), None, x, 1, 0,
+                                      0, None, None, torch.empty((16, 2), dtype=torch.float64, device="cuda"))
+    assert ei.value.status == sfft.SFFT_ERR_INVALID_ARG
+    with pytest.raises(sfft.SfftError):
+        sfft.sfft_hash_to_bins_static(n, 16, 100, torch.zeros(101, dtype=torch.float32), None, x, 1, 0, 0, None, None,
+                                      torch.empty((16, 2), dtype=torch.float64, device="cuda"))
