@@ -184,7 +184,6 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
     size_t part_elems = 0, max_smem = 0, gs_max = 0, fs_max = 0, ls_max = 0, es_max = 0;
     uint32_t maxB = 0, max_groups = 0;
     size_t sum_groups = 0, sum_B = 0;  // general: hashing groups and bins over all rounds
-    size_t fin_rounds = 0;             // exact: rounds whose finisher arrays live in d_fin
     // exact mode: every round's partial folds live at once (the one-launch path gathers all rounds
     // before their finishers), round t at part_off[t] of a request's region
     std::vector<size_t> part_off;
@@ -199,7 +198,6 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         if (r.smem > max_smem) max_smem = r.smem;
         if (r.B > maxB) maxB = r.B;
         if (r.fin_global && r.fin_bytes > pl->fin_stride) pl->fin_stride = (r.fin_bytes + 255) & ~size_t(255);
-        if (r.fin_global) ++fin_rounds;
     }
     for (const GeneralRound& r : pl->grounds) {
         pl->samples += (uint64_t)r.nhash * (2 * (uint64_t)r.T + 1);
@@ -263,9 +261,10 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
             return SFFT_ERR_OOM;
         }
     }
-    // one region per such round: in the one-launch path a round's bins and the previous round's decode
-    // may run at once for the same request
-    if (pl->fin_stride) SFFT_ALLOC(pl->d_fin, pl->fin_stride * max_batch * fin_rounds);
+    // one slice per request serves every such round: only the decode part of a finisher uses it (the
+    // one-launch path forms a round's bins in the CTA's shared memory), and a request's decodes run one
+    // after another (round t + 1's waits for round t's arrival on the request's second counter)
+    if (pl->fin_stride) SFFT_ALLOC(pl->d_fin, pl->fin_stride * max_batch);
     if (pl->gfin_stride) SFFT_ALLOC(pl->d_gfin, pl->gfin_stride * pl->gfin_groups * max_batch);
     if (pl->gest_stride) SFFT_ALLOC(pl->d_gest, pl->gest_stride * max_batch);
     if (general) {
@@ -304,11 +303,9 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         return fail(e, "clear counters");
     if (!general) {  // the round blocks of the one-launch path (each launch fills in its own fields)
         const size_t csize = fp64 ? 16 : 8;
-        size_t fin_index = 0;
         for (uint32_t t = 0; t < (uint32_t)pl->rounds.size(); ++t) {
             ExactArgs a = base_args(pl, pl->rounds[t], t);
             a.part = static_cast<unsigned char*>(pl->d_part) + part_off[t] * csize;
-            if (pl->rounds[t].fin_global) a.fin_scratch = pl->d_fin + fin_index++ * max_batch * pl->fin_stride;
             a.counter = pl->d_counter + (size_t)t * max_batch;
             a.counter2 = pl->d_counter + (size_t)(pl->rounds.size() + t) * max_batch;
             a.first_round = t == 0;
