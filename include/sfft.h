@@ -172,6 +172,31 @@ sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, u
                               uint32_t* h_idx, double* h_val, uint32_t cap, uint32_t* h_count, int32_t* h_flag);
 
 /*
+ * Multi-channel batch with shared hashing (exact mode, SFFT_FP32 plans).  C = `channels` signals
+ * sampled at the same times are stored interleaved: d_x holds n rows of C complex64 values, row m
+ * holding sample m of every channel (device memory, 16-byte aligned).  Every channel is transformed
+ * with the same random hashings, those of request index `id` under `seed` (Algorithm 1's sigma, b of
+ * each round are drawn once and shared), so one sigma-strided sample index reads C contiguous values
+ * instead of C scattered 32-byte sectors.  Channel c's result equals that of sfft_execute_requests on
+ * signal x[.][c] with {seed, id} (up to FP32 rounding of the fold, done in another order); each
+ * result on its own is a draw of the algorithm, but the channels' failures are not independent
+ * (they share the hashings).  Outputs per channel slot c as for sfft_execute (slot r = channel r).
+ * channels: a multiple of 32, at most 256 and at most the plan's max_batch.  The gather stages the
+ * sample rows in shared memory with bulk asynchronous copies; should one not land within a bounded
+ * wait (never expected), every channel's d_flag reads SFFT_ERR_TIMEOUT and its count 0.
+ * Errors: INVALID_ARG (a general-mode or FP64 plan, null pointer, channels out of range, misaligned
+ * d_x, cap == 0), CUDA.
+ */
+sfft_status sfft_execute_channels(sfft_plan plan, const void* d_x, uint32_t channels, uint64_t seed, uint32_t id,
+                                  void* stream, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
+                                  int32_t* d_flag);
+/* The same, recording the CUDA event `between` (a cudaEvent_t) on `stream` after the gather kernel
+ * and before the finish, so that a caller can time the gather alone. */
+sfft_status sfft_execute_channels_timed(sfft_plan plan, const void* d_x, uint32_t channels, uint64_t seed, uint32_t id,
+                                        void* stream, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
+                                        int32_t* d_flag, void* between);
+
+/*
  * One request of sfft_execute_requests: its own signal, seed and request index.  The result depends
  * on (signal, params, seed, id) only, not on the batch or slot the request runs in: request r of
  * sfft_execute with seed s equals a request {row r, s, r}.

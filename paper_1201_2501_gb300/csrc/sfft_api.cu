@@ -199,6 +199,18 @@ sfft_status sfft::plan_create(const sfft_params* p, uint32_t max_batch, const sf
         if (r.B > maxB) maxB = r.B;
         if (r.fin_global && r.fin_bytes > pl->fin_stride) pl->fin_stride = (r.fin_bytes + 255) & ~size_t(255);
     }
+    if (!general && !fp64) {  // the partial folds of a multi-channel batch (sfft_execute_channels)
+        size_t chan_elems = 0;
+        for (const ExactRound& r : pl->rounds) {
+            const uint64_t cnt = 2 * (uint64_t)r.T + 1 + r.shift[r.nshift - 1];
+            const uint64_t rows = (cnt + r.B - 1) / r.B;  // rows of the largest residue class
+            const uint32_t chunks = (uint32_t)((rows + kChanRows - 1) / kChanRows);
+            pl->chan_off.push_back(chan_elems);
+            pl->chan_chunks.push_back(chunks);
+            chan_elems += (size_t)chunks * (1 + r.nshift) * r.B;
+        }
+        if (chan_elems > part_elems) part_elems = chan_elems;
+    }
     for (const GeneralRound& r : pl->grounds) {
         pl->samples += (uint64_t)r.nhash * (2 * (uint64_t)r.T + 1);
         const size_t e = (size_t)r.ngroups * r.ctas * 2 * r.B;
@@ -592,6 +604,52 @@ sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64
     if (!plan || !d_x || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
     if (batch == 0 || batch > plan->max_batch) return SFFT_ERR_INVALID_ARG;
     return execute_batch(plan, d_x, nullptr, batch, seed, (cudaStream_t)stream, d_idx, d_val, cap, d_count, d_flag);
+}
+
+static sfft_status execute_channels(sfft_plan plan, const void* d_x, uint32_t channels, uint64_t seed, uint32_t id,
+                                   cudaStream_t st, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
+                                   int32_t* d_flag, cudaEvent_t between) {
+    if (!plan || !d_x || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
+    if (plan->p.mode != SFFT_EXACT || plan->p.precision != SFFT_FP32 || plan->chan_off.empty())
+        return SFFT_ERR_INVALID_ARG;
+    if (channels == 0 || channels % 32 || channels > kChanMaxC || channels > plan->max_batch || ((uintptr_t)d_x & 15))
+        return SFFT_ERR_INVALID_ARG;
+    SFFT_CUDA(cudaMemsetAsync(plan->d_zcount, 0, channels * sizeof(uint32_t), st), "clear zhat");
+    SFFT_CUDA(cudaMemsetAsync(plan->d_zflag, 0, channels * sizeof(int32_t), st), "clear flags");
+    const uint32_t R = (uint32_t)plan->rounds.size();
+    ExactArgs rounds[kMaxRounds];
+    for (uint32_t t = 0; t < R; ++t) {
+        ExactArgs& a = rounds[t];
+        a = plan->rdesc[t];
+        a.x = d_x;
+        a.reqs = nullptr;
+        a.seed = seed;
+        a.req_base = 0;
+        a.part = static_cast<unsigned char*>(plan->d_part) + plan->chan_off[t] * sizeof(float2);
+        a.chunks = plan->chan_chunks[t];
+        a.out_idx = d_idx;
+        a.out_val = reinterpret_cast<double2*>(d_val);
+        a.out_cap = cap;
+        a.out_count = d_count;
+        a.out_flag = d_flag;
+    }
+    SFFT_CUDA(launch_exact_channels(rounds, R, channels, d_x, seed, id, plan->step_smem, plan->d_aux, st, between),
+              "channel batch");
+    return SFFT_OK;
+}
+
+sfft_status sfft_execute_channels(sfft_plan plan, const void* d_x, uint32_t channels, uint64_t seed, uint32_t id,
+                                  void* stream, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
+                                  int32_t* d_flag) {
+    return execute_channels(plan, d_x, channels, seed, id, (cudaStream_t)stream, d_idx, d_val, cap, d_count, d_flag,
+                            nullptr);
+}
+
+sfft_status sfft_execute_channels_timed(sfft_plan plan, const void* d_x, uint32_t channels, uint64_t seed, uint32_t id,
+                                        void* stream, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
+                                        int32_t* d_flag, void* between) {
+    return execute_channels(plan, d_x, channels, seed, id, (cudaStream_t)stream, d_idx, d_val, cap, d_count, d_flag,
+                            (cudaEvent_t)between);
 }
 
 sfft_status sfft_execute_trace(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, void* stream,

@@ -769,6 +769,26 @@ __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_round
 // ------------------------------------------------------------------------------------------------
 // One launch per batch: all rounds' chunks, finishers chained by arrival counters
 // ------------------------------------------------------------------------------------------------
+// Round t's bins of request s are ready: arrive at its second counter; the later of (these bins,
+// round t - 1's decode) runs round t's decode, then arrives at round t + 1's, and so on.  (seed, id)
+// name the request's draws.
+template <typename R, int NR>
+__device__ __forceinline__ void decode_chain(const StepParams<NR>& sp, uint32_t t, const ExactArgs* a, uint32_t s,
+                                             uint64_t seed, uint32_t id, uint32_t sigma, uint32_t b,
+                                             unsigned char* smem) {
+    if (arrive(a->counter2 + s, t > 0 ? 2u : 1u) == 0) return;
+    for (;;) {
+        finish_round<R>(*a, s, sigma, b, a->fin_scratch ? a->fin_scratch + (size_t)s * a->fin_stride : smem,
+                        kFinDecode);
+        if (threadIdx.x == 0) a->counter2[s] = 0;  // both arrivals of round t have happened
+        if (t + 1 >= sp.R) break;
+        a = &sp.r[++t];
+        // zhat of round t is published by the arrival at round t + 1's second counter
+        if (arrive(a->counter2 + s, 2u) == 0) break;
+        exact_hash(seed, id, t, a->nmask, &sigma, &b);
+    }
+}
+
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_step(const __grid_constant__ StepParams<NR> sp) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -787,16 +807,129 @@ __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_step(
     // the round's bins, in this CTA's shared memory (the gather's staging area holds H B values)
     finish_round<R>(*a, s, sigma, b, smem, kFinBins);
     if (tid == 0) a->counter[s] = 0;  // every chunk of round t has arrived
-    if (arrive(a->counter2 + s, t > 0 ? 2u : 1u) == 0) return;
-    for (;;) {
-        finish_round<R>(*a, s, sigma, b, a->fin_scratch ? a->fin_scratch + (size_t)s * a->fin_stride : smem,
-                        kFinDecode);
-        if (tid == 0) a->counter2[s] = 0;  // both arrivals of round t have happened
-        if (t + 1 >= sp.R) break;
-        a = &sp.r[++t];
-        // zhat of round t is published by the arrival at round t + 1's second counter
-        if (arrive(a->counter2 + s, 2u) == 0) break;
-        exact_hash(rq.seed, rq.id, t, a->nmask, &sigma, &b);
+    decode_chain<R, NR>(sp, t, a, s, rq.seed, rq.id, sigma, b, smem);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Multi-channel batches with shared hashing (see ChanParams)
+// ------------------------------------------------------------------------------------------------
+// Gather and fold: CTA (t, rho, c) sums, for each hashing h of round t and every channel, the terms
+// G_{s + a_h} w^{sigma b (s + a_h)} x_{sigma s} over the samples s = s0 + i, i = rho' + j B (rho' the
+// first index of residue class rho), j in chunk c: bin rho of hashing h.  Warp 0 issues one bulk copy
+// per row (C contiguous complex values) into shared memory, then forms the rows' coefficients (one
+// row per lane) while the copies are in flight; once they have landed, thread ch folds channel ch in
+// row order.
+constexpr uint32_t kChanWaitLimit = 1u << 22;  // tries of a bounded wait (far beyond a second)
+template <int NR>
+__global__ void __launch_bounds__(kThreads) k_chan_gather(const __grid_constant__ ChanParams<NR> cp) {
+    extern __shared__ __align__(16) unsigned char smem[];  // bulk copies need 16-byte alignment
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t C = cp.C, tid = threadIdx.x;
+    float2* rows = reinterpret_cast<float2*>(smem);                                       // [kChanRows][C]
+    float2* coef = reinterpret_cast<float2*>(smem + (size_t)kChanRows * C * sizeof(float2));  // [kChanRows][kMaxHash]
+    uint32_t t = 0;
+    while (t + 1 < cp.R && blockIdx.x >= cp.cseg[t + 1]) ++t;
+    const ExactArgs& a = cp.r[t];
+    const uint32_t local = blockIdx.x - cp.cseg[t];
+    const uint32_t rho = local & (a.B - 1), c = local / a.B;
+    const int64_t s0 = -a.T - (int64_t)a.maxshift;
+    const uint32_t cnt = (uint32_t)(2 * a.T + 1) + a.maxshift;
+    const uint32_t i_first = (rho - (uint32_t)s0) & (a.B - 1);
+    const uint32_t nrows = i_first < cnt ? (cnt - 1 - i_first) / a.B + 1 : 0;
+    const uint32_t j_beg = c * kChanRows;
+    const uint32_t m = nrows > j_beg ? min(kChanRows, nrows - j_beg) : 0u;  // rows of this chunk
+    if (tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (tid < 32) {
+        uint32_t sigma, b;
+        exact_hash(cp.seed, cp.id, t, a.nmask, &sigma, &b);
+        const uint32_t sb = sigma * b;
+        const bool ok = tid < m;
+        const int32_t sl = (int32_t)(s0 + (int64_t)i_first + (int64_t)(j_beg + tid) * a.B);
+        // the copies first, the coefficients while they are in flight
+        if (tid == 0) mbar_arrive_expect_tx(&bar, m * C * (uint32_t)sizeof(float2));
+        __syncwarp();
+        if (ok) {
+            const uint32_t row = (sigma * (uint32_t)sl) & a.nmask;
+            bulk_copy_g2s(rows + (size_t)tid * C, static_cast<const float2*>(cp.x) + (size_t)row * C,
+                          C * (uint32_t)sizeof(float2), &bar);
+        }
+#pragma unroll
+        for (int h = 0; h < kMaxHash; ++h) {
+            float2 co = make_float2(0.0f, 0.0f);
+            const int32_t th = sl + (int32_t)a.a[h];
+            if ((uint32_t)h < a.H && ok && th >= -a.T && th <= a.T) {
+                const float gt = a.taps32[th < 0 ? -th : th];
+                const uint32_t e = (sb * (uint32_t)th) & a.nmask;
+                const int32_t es = e > (a.nmask >> 1) ? (int32_t)((int64_t)e - (int64_t)a.n) : (int32_t)e;
+                float sn, cs;
+                sincospif((float)es * (2.0f / (float)a.n), &sn, &cs);
+                co = make_float2(gt * cs, -gt * sn);
+            }
+            coef[tid * kMaxHash + h] = co;
+        }
+    }
+    __syncthreads();  // the coefficients
+    if (!mbar_wait(&bar, 0, kChanWaitLimit)) {
+        // never expected: flag it, give the copies a second bounded wait, leave the partial sums alone
+        if (tid == 0) atomicExch(cp.error, 1u);
+        mbar_wait(&bar, 0, kChanWaitLimit);
+        return;
+    }
+    for (uint32_t ch = tid; ch < C; ch += kThreads) {
+        float2 acc[kMaxHash];
+#pragma unroll
+        for (int h = 0; h < kMaxHash; ++h) acc[h] = make_float2(0.0f, 0.0f);
+        for (uint32_t j = 0; j < m; ++j) {
+            const float2 v = rows[(size_t)j * C + ch];
+#pragma unroll
+            for (int h = 0; h < kMaxHash; ++h) acc[h] = cfma(coef[j * kMaxHash + h], v, acc[h]);
+        }
+        float2* area = static_cast<float2*>(a.part) + (size_t)ch * a.part_stride;
+#pragma unroll
+        for (int h = 0; h < kMaxHash; ++h)
+            if ((uint32_t)h < a.H) area[((size_t)c * a.H + h) * a.B + rho] = acc[h];
+    }
+}
+
+// The bins of every (round, slot) at once: partial folds summed in chunk order, bit-reversed, B-point
+// FFT, left at the start of the slot's area of the round.
+template <int NR>
+__global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_chan_bins(const __grid_constant__ StepParams<NR> sp,
+                                                                              uint64_t seed, uint32_t id) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t t = 0;
+    while (t + 1 < sp.R && blockIdx.x >= sp.seg[t + 1]) ++t;
+    const ExactArgs& a = sp.r[t];
+    const uint32_t s = blockIdx.x - sp.seg[t];
+    uint32_t sigma, b;
+    exact_hash(seed, id, t, a.nmask, &sigma, &b);
+    finish_round<float>(a, s, sigma, b, smem, kFinBins);
+}
+
+// The decodes: one CTA per channel slot runs them in round order (zhat of round t feeds round t + 1).
+// If the gather flagged a copy that never landed, every slot reports SFFT_ERR_TIMEOUT instead.
+template <int NR>
+__global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_chan_decode(const __grid_constant__ StepParams<NR> sp,
+                                                                                uint64_t seed, uint32_t id,
+                                                                                const uint32_t* error) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t s = blockIdx.x;
+    if (*error) {
+        if (threadIdx.x == 0) {
+            const ExactArgs& a = sp.r[sp.R - 1];
+            a.out_count[s] = 0;
+            a.out_flag[s] = SFFT_ERR_TIMEOUT;
+        }
+        return;
+    }
+    for (uint32_t t = 0; t < sp.R; ++t) {
+        const ExactArgs& a = sp.r[t];
+        uint32_t sigma, b;
+        exact_hash(seed, id, t, a.nmask, &sigma, &b);
+        finish_round<float>(a, s, sigma, b, a.fin_scratch ? a.fin_scratch + (size_t)s * a.fin_stride : smem,
+                            kFinDecode);
+        __syncthreads();  // zhat of round t is read by round t + 1 (same CTA)
     }
 }
 
@@ -1016,6 +1149,61 @@ __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uin
 // ------------------------------------------------------------------------------------------------
 // The dynamic shared-memory ceiling of a kernel is process-wide: it is only ever raised, so a plan
 // created later with smaller rounds cannot lower it under another plan's feet.
+template <int NR>
+static cudaError_t launch_chan_nr(const ExactArgs* rounds, uint32_t R, uint32_t C, const void* x, uint64_t seed,
+                                  uint32_t id, size_t smem, uint32_t* error, cudaStream_t st, cudaEvent_t between) {
+    ChanParams<NR> cp;
+    StepParams<NR> sp;
+    cp.R = sp.R = R;
+    cp.C = C;
+    cp.seed = seed;
+    cp.id = id;
+    cp.x = x;
+    cp.error = error;
+    cp.cseg[0] = 0;
+    sp.seg[0] = 0;
+    for (uint32_t t = 0; t < R; ++t) {
+        const uint64_t w = (uint64_t)cp.cseg[t] + (uint64_t)rounds[t].chunks * rounds[t].B;
+        if (w > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
+        cp.cseg[t + 1] = (uint32_t)w;
+        sp.seg[t + 1] = sp.seg[t] + C;
+        cp.r[t] = sp.r[t] = rounds[t];
+    }
+    const size_t gsmem = (size_t)kChanRows * C * sizeof(float2) + (size_t)kChanRows * kMaxHash * sizeof(float2);
+    static std::mutex mu;
+    static size_t set_to = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (set_to < kChanRows * kChanMaxC * sizeof(float2) + kChanRows * kMaxHash * sizeof(float2)) {
+            const int full = (int)(kChanRows * kChanMaxC * sizeof(float2) + kChanRows * kMaxHash * sizeof(float2));
+            cudaError_t e = cudaFuncSetAttribute(k_chan_gather<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, full);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_chan_gather<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, full);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_chan_gather<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, full);
+            if (e != cudaSuccess) return e;
+            set_to = (size_t)full;
+        }
+    }
+    cudaError_t e = cudaMemsetAsync(error, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    k_chan_gather<NR><<<cp.cseg[R], kThreads, gsmem, st>>>(cp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (between && (e = cudaEventRecord(between, st)) != cudaSuccess) return e;
+    k_chan_bins<NR><<<sp.seg[R], kThreads, smem, st>>>(sp, seed, id);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_chan_decode<NR><<<C, kThreads, smem, st>>>(sp, seed, id, error);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_channels(const ExactArgs* rounds, uint32_t R, uint32_t C, const void* x, uint64_t seed,
+                                  uint32_t id, size_t smem, uint32_t* error, cudaStream_t st, cudaEvent_t between) {
+    if (R == 0 || R > kMaxRounds || C == 0 || C % 32 || C > kChanMaxC || !error) return cudaErrorInvalidValue;
+    if (R <= 8) return launch_chan_nr<8>(rounds, R, C, x, seed, id, smem, error, st, between);
+    if (R <= 16) return launch_chan_nr<16>(rounds, R, C, x, seed, id, smem, error, st, between);
+    return launch_chan_nr<32>(rounds, R, C, x, seed, id, smem, error, st, between);
+}
+
 cudaError_t set_exact_smem_limit(size_t bytes, bool fp64) {
     static std::mutex mu;  // plans may be created from several threads
     std::lock_guard<std::mutex> lk(mu);
@@ -1034,6 +1222,12 @@ cudaError_t set_exact_smem_limit(size_t bytes, bool fp64) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_exact_step<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_exact_step<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_exact_step<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chan_bins<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chan_bins<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chan_bins<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chan_decode<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chan_decode<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chan_decode<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     }
     if (e == cudaSuccess) cur = bytes;
     return e;

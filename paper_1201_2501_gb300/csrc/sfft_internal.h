@@ -113,6 +113,30 @@ struct StepParams {
     ExactArgs r[NR];
 };
 
+// Multi-channel batches with shared hashing (sfft_execute_channels): C signals sampled at the same
+// times and stored interleaved, x[m][c], all transformed with the draws of one request (seed, id).
+// One CTA gathers the samples s = s0 + i (s0 = -T - maxshift) of round t whose index i falls in
+// residue class rho mod B_t, chunk c of kChanRows consecutive rows of that class: the rows (C
+// contiguous values each) are staged in shared memory by bulk copies, and thread ch folds channel
+// ch.  The ladder's shifts are multiples of B_t, so every hashing of the round puts sample s in bin
+// s mod B_t: a channel's H_t sums are one bin each.  The partial folds go to the channel slot's
+// partial-fold area laid out as the one-launch path's ([chunk][H][B] per round, round t at
+// chan_off[t]); then every (round, slot) forms its bins at once, and one CTA per slot runs the
+// decodes in order.
+constexpr uint32_t kChanRows = 32;   // rows of a residue class per CTA
+constexpr uint32_t kChanMaxC = 256;  // channels of one batch (a row of the stage holds them all)
+template <int NR>
+struct ChanParams {
+    uint32_t R;               // rounds
+    uint32_t C;               // channels (a multiple of 32, at most kChanMaxC)
+    uint32_t cseg[NR + 1];    // first CTA of each round's segment; cseg[R] = CTAs
+    uint64_t seed;
+    uint32_t id;              // request index of the shared draws
+    const void* x;            // n x C complex64, 16-byte aligned
+    uint32_t* error;          // set when a bulk copy did not complete within the wait limit
+    ExactArgs r[NR];          // round blocks; part at the round's channel layout, chunks = its chunks
+};
+
 // The persistent exact path: requests of different plans (n, k, schedule) in one launch, their
 // rounds driven by a device work queue.  Item = (request, round, chunk); the CTA that finishes a
 // request's round publishes the chunks of its next round.  rdesc holds one argument block per
@@ -302,6 +326,8 @@ struct sfft_plan_s {
     // [max_batch][ngroups_r] for the gather, then [max_batch] for the estimate
     uint32_t* d_counter = nullptr;
     std::vector<sfft::ExactArgs> rdesc;  // [R] round blocks of the one-launch exact path
+    std::vector<size_t> chan_off;        // exact FP32: round t's partial folds in a channel slot's area
+    std::vector<uint32_t> chan_chunks;   // exact FP32: chunks of kChanRows rows per residue class
     size_t step_smem = 0;                // its dynamic shared memory (largest round)
     uint32_t* d_zidx = nullptr;
     double2* d_zval = nullptr;
@@ -374,6 +400,12 @@ cudaError_t launch_exact_round(const ExactArgs& a, uint32_t batch, size_t smem, 
 // rounds[0..R) with this launch's fields filled in; grid = sum over rounds of chunks x batch
 cudaError_t launch_exact_step(const ExactArgs* rounds, uint32_t R, uint32_t batch, size_t smem, cudaStream_t st,
                               bool fp64);
+// multi-channel batch with shared hashing: the gather (one CTA per round, residue and chunk), an
+// optional event recorded after it, the bins of every (round, slot), then one CTA per slot for the
+// decodes; rounds[t].part and .chunks give each round's channel layout; error: a device word the
+// gather sets when a bulk copy times out (cleared here first)
+cudaError_t launch_exact_channels(const ExactArgs* rounds, uint32_t R, uint32_t C, const void* x, uint64_t seed,
+                                  uint32_t id, size_t smem, uint32_t* error, cudaStream_t st, cudaEvent_t between);
 // persistent path: CTAs that fit on the device at `smem`, and the launch
 int exact_persistent_ctas(size_t smem, bool fp64);
 cudaError_t launch_exact_persistent(const PersistArgs& a, uint32_t ctas, size_t smem, cudaStream_t st, bool fp64);

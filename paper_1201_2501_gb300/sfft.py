@@ -177,6 +177,8 @@ _SIGS = {
     "sfft_poll": (ctypes.c_int, [_vp, _u64]),
     "sfft_wait": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(SfftJobResult)]),
     "sfft_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(SfftServerStats)]),
+    "sfft_execute_channels": (ctypes.c_int, [_vp, _vp, _u32, _u64, _u32, _vp, _vp, _vp, _u32, _vp, _vp]),
+    "sfft_execute_channels_timed": (ctypes.c_int, [_vp, _vp, _u32, _u64, _u32, _vp, _vp, _vp, _u32, _vp, _vp, _vp]),
     "sfft_execute_trace": (ctypes.c_int, [_vp, _vp, _u32, _u64, _vp, _vp, _vp, _u32, _vp, _vp,
                                           ctypes.POINTER(SfftGeneralTrace)]),
 }
@@ -645,6 +647,33 @@ def sfft_hash_to_bins_static(n: int, B: int, T: int, taps, wtab, x, sigma: int, 
     _check(lib().sfft_hash_to_bins_static(n, B, T, _ptr(taps), _ptr(wtab), _ptr(x), sigma, a, b, _ptr(zidx),
                                           _ptr(zval), nz, _ptr(out), _stream_ptr(stream)), "sfft_hash_to_bins_static")
     return out
+
+
+def sfft_execute_channels(plan: Plan, x, seed: int, id: int, cap: int, outputs=None, stream=None, between=None):
+    """Multi-channel batch with shared hashing (sfft_execute_channels): ``x`` is a torch tensor [n, C]
+    complex64 on the GPU (row m = sample m of every channel), every channel transformed with the draws
+    of request ``id`` under ``seed``.  ``between`` (a torch.cuda.Event) is recorded after the gather.
+    Returns (idx [C, cap], val [C, cap, 2], count [C], flag [C]) device tensors, slot c = channel c."""
+    import torch
+
+    if x.dim() != 2 or x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+        raise SfftError(SFFT_ERR_INVALID_ARG, "sfft_execute_channels: need a contiguous [n, C] complex64 CUDA tensor")
+    C = x.shape[1]
+    if outputs is None:
+        dev = x.device
+        outputs = (torch.empty((C, cap), dtype=torch.int32, device=dev),
+                   torch.empty((C, cap, 2), dtype=torch.float64, device=dev),
+                   torch.empty((C,), dtype=torch.int32, device=dev),
+                   torch.empty((C,), dtype=torch.int32, device=dev))
+    idx, val, count, flag = outputs
+    if between is None:
+        _check(lib().sfft_execute_channels(plan.handle, _ptr(x), C, seed, id, _stream_ptr(stream), _ptr(idx), _ptr(val),
+                                           cap, _ptr(count), _ptr(flag)), "sfft_execute_channels")
+    else:
+        _check(lib().sfft_execute_channels_timed(plan.handle, _ptr(x), C, seed, id, _stream_ptr(stream), _ptr(idx),
+                                                 _ptr(val), cap, _ptr(count), _ptr(flag),
+                                                 ctypes.c_void_p(between.cuda_event)), "sfft_execute_channels_timed")
+    return outputs
 
 
 def sfft_execute_trace(plan: Plan, x, seed: int, cap: int, round_: int, stream=None):

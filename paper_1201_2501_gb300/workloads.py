@@ -147,6 +147,18 @@ def exact_sparse_batch_device(n: int, k: int, seeds, device, chunk: int = 16, dt
     return out, sup, val
 
 
+def exact_sparse_channels_device(n: int, k: int, seeds, device, chunk: int = 16):
+    """C = len(seeds) exactly k-sparse signals as one interleaved multi-channel array [n, C] complex64
+    on a torch device (row m holds sample m of every channel); channel c is ``exact_sparse_batch_device``'s
+    row c.  Returns (x, supports, values)."""
+    import torch
+
+    x, sup, val = exact_sparse_batch_device(n, k, seeds, device, chunk=chunk)
+    xt = x.t().contiguous()
+    del x
+    return xt, sup, val
+
+
 def sparse_signal_device(n: int, k: int, seed: int, device, snr_db=None):
     """One signal built on a torch device (complex64 [n]): the spectrum of ``exact_sparse`` (snr_db
     None) or of ``general_noisy`` (heavy coefficients; complex Gaussian time noise at snr_db, drawn on
