@@ -608,12 +608,14 @@ def run_ours(args):
             "cpu_baseline": cpu,
         }
         line.update(extra)
-        ceil = extra.get("random_gather_ceiling")
-        if ceil:  # the same step against the random 32-byte-sector rate measured in this run
+        ceil = extra.get("gather_ceilings")
+        if ceil:  # the step's sector rate against the same reads issued by a kernel that only reads
             sectors = achieved * 1e9 / 32.0
-            line["roofline"]["random_sector_rate"] = {"achieved_sectors_per_s": sectors,
-                                                      "ceiling_sectors_per_s": ceil["sectors_per_s"],
-                                                      "frac": sectors / ceil["sectors_per_s"]}
+            line["roofline"]["sector_rate"] = {
+                "achieved_sectors_per_s": sectors,
+                "vs_same_reads_step_order": sectors / ceil["step_order"]["sectors_per_s"],
+                "vs_same_reads_random_order": sectors / ceil["random_order"]["sectors_per_s"],
+                "vs_same_reads_address_order": sectors / ceil["address_order"]["sectors_per_s"]}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
@@ -691,28 +693,8 @@ def context_measurements(sfft, plan, x, cap, stream, args):
     out["cufft"] = {"value": reps_c / (e0.elapsed_time(e1) / 1000), "unit": "transforms/s",
                     "what": f"cuFFT C2C forward n=2^22 complex64, batches of {chunk} (torch.fft.fft)"}
     del y
-    # ceiling of a plain random gather on this GPU: 8-byte elements at uniformly random positions of
-    # the same 8 GiB batch (torch.index_select), in 32-byte sectors per second
-    flat = x.view(-1).view(torch.int64)
-    m = 1 << 24
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(1)
-    idx = torch.randint(0, flat.numel(), (m,), device="cuda", generator=gen)
-    dst = torch.empty(m, dtype=torch.int64, device="cuda")
-    for _ in range(3):
-        torch.index_select(flat, 0, idx, out=dst)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    reps_g = 10
-    for _ in range(reps_g):
-        torch.index_select(flat, 0, idx, out=dst)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    sec = e0.elapsed_time(e1) / 1000 / reps_g
-    out["random_gather_ceiling"] = {"sectors_per_s": m / sec, "gbs_at_32B_per_sector": m * 32 / sec / 1e9,
-                                    "what": "torch.index_select of 2^24 random int64 from the 8 GiB batch; "
-                                            "includes the coalesced index read and output write"}
-    del idx, dst
+    out["gather_ceilings"] = gather_ceilings(sfft, plan, x, stream)
+    out["channels"] = channels_measurement(sfft, x, stream, args)
     if not args.no_general:
         out["general_case"] = general_measurement(sfft, stream, args)
     if not args.no_serving:
@@ -720,6 +702,125 @@ def context_measurements(sfft, plan, x, cap, stream, args):
     if args.mixed:
         out["mixed_batch"] = mixed_batch_measurement(sfft, args)
     return out
+
+
+def step_sample_addresses(sfft, plan, batch, n):
+    """The permuted sample index x[(sigma s) mod n] of every sample the one-launch step gathers, per
+    request and in the step's own order (round by round, s ascending): uint32 [batch, samples]."""
+    rows = []
+    for r in range(batch):
+        per = []
+        for t in range(plan.rounds):
+            ri = plan.round_info(t, SEED, r)
+            T, shift = ri["T"], max(ri["shifts"])
+            s_ = np.arange(-T - shift, T + 1, dtype=np.int64)
+            per.append((ri["sigma"] * s_) % n)
+        rows.append(np.concatenate(per))
+    return np.stack(rows).astype(np.uint32)
+
+
+def gather_ceilings(sfft, plan, x, stream, reps=10):
+    """The step's own sample reads (every request, every round) issued by a kernel that does nothing
+    else (sfft_gather_rate) on the same 8 GiB batch, in three orders: the step's (round by round, s
+    ascending), a random permutation of it, and sorted by address within each request.  Sectors per
+    second at one 32-byte sector per read."""
+    import torch
+
+    batch, n = x.shape
+    addr = step_sample_addresses(sfft, plan, batch, n)
+    rng = np.random.default_rng(7)
+    orders = {"step_order": addr,
+              "random_order": np.take_along_axis(addr, np.argsort(rng.random(addr.shape), axis=1), axis=1),
+              "address_order": np.sort(addr, axis=1)}
+    sink = torch.zeros(64, dtype=torch.int32, device="cuda")
+    out = {}
+    for name, a in orders.items():
+        d = torch.as_tensor(a.view(np.int32)).cuda()
+        for _ in range(3):
+            sfft.sfft_gather_rate(x, n, batch, d, a.shape[1], sink, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            sfft.sfft_gather_rate(x, n, batch, d, a.shape[1], sink, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1000 / reps
+        reads = a.size
+        out[name] = {"sectors_per_s": reads / sec, "gbs_at_32B_per_sector": reads * 32 / sec / 1e9}
+        del d
+    hbm, kind = _peaks()
+    for v in out.values():
+        v["frac_of_copy_peak"] = v["gbs_at_32B_per_sector"] / hbm
+    out["what"] = ("the step's own sample reads (all requests and rounds of a step, 8 GiB batch) issued by a "
+                   "read-only kernel of this library (sfft_gather_rate: 16 reads in flight per thread, L2 only, "
+                   "index list read coalesced), per order; copy peak " + kind)
+    return out
+
+
+CHAN_C = 256
+
+
+def channels_measurement(sfft, x, stream, args):
+    """The same transform on a multi-channel batch with shared hashing (sfft_execute_channels): the
+    batch's 256 signals interleaved as [n][256] complex64 (8 GiB), every channel with the draws of one
+    request index.  A second workload beside the headline, not in place of it: each channel's result is
+    a draw of the algorithm, but the channels share their hashings.  Back-to-back steps timed with CUDA
+    events; the gather kernel timed alone between events recorded around it."""
+    import torch
+
+    n = x.shape[1]
+    C = min(CHAN_C, x.shape[0])
+    params = sfft.sfft_params_default(n, K, sfft.SFFT_EXACT, delta=DELTA)
+    params.alpha0 = ALPHA0
+    plan = sfft.Plan(params, C)
+    xc = x[:C].t().contiguous()
+    cap = params.z_cap
+    outs = (torch.empty((C, cap), dtype=torch.int32, device="cuda"),
+            torch.empty((C, cap, 2), dtype=torch.float64, device="cuda"),
+            torch.empty((C,), dtype=torch.int32, device="cuda"), torch.empty((C,), dtype=torch.int32, device="cuda"))
+    for _ in range(5):
+        sfft.sfft_execute_channels(plan, xc, SEED, 0, cap, outs, stream)
+    torch.cuda.synchronize()
+    from paper_1201_2501_gb300 import workloads
+
+    sup, _ = workloads.exact_sparse_batch_spectra(n, K, [workloads.seed_for(2, c) for c in range(C)])
+    cnt = outs[2].cpu().numpy()
+    idx = outs[0].cpu().numpy()
+    exact = sum(np.array_equal(np.sort(idx[c, :cnt[c]].astype(np.int64)), sup[c]) for c in range(C))
+    steps = max(20, min(args.steps, 500))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sfft.sfft_execute_channels(plan, xc, SEED, 0, cap, outs, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    N = 50
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(N)]
+    for pair in evs:
+        for e in pair:
+            e.record(stream)
+    torch.cuda.synchronize()
+    for i in range(N):
+        sfft.sfft_execute_channels(plan, xc, SEED, 0, cap, outs, stream, before=evs[i][0], after=evs[i][1])
+    torch.cuda.synchronize()
+    g_ms = statistics.median(a.elapsed_time(b) for a, b in evs[5:])
+    samples = sum(2 * plan.round_info(t)["T"] + 1 + max(plan.round_info(t)["shifts"]) for t in range(plan.rounds))
+    bytes_launch = samples * C * 8
+    hbm, kind = _peaks()
+    achieved = bytes_launch / (g_ms / 1000) / 1e9
+    plan.close()
+    del xc
+    return {"workload": f"{C} channels interleaved [n][{C}] complex64, n=2^22, k=64 per channel, shared hashing "
+                        "(one request index), B=4k, delta=1e-6, alpha0=5/8",
+            "value": C / (ms / 1000), "unit": "transforms/s", "ms_per_step": ms, "steps": steps,
+            "support_exact_fraction": exact / C,
+            "gpu_launches_per_step": 3,
+            "roofline": {"bound": "hbm", "kernel": "k_chan_gather", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_kind": kind, "bytes_per_launch": bytes_launch,
+                         "what": "gathered rows x C x 8 B (every byte read is used) / the gather kernel's "
+                                 "median event time"}}
 
 
 SERVE_EXPS = (16, 18, 20, 22, 24, 26)

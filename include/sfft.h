@@ -190,11 +190,25 @@ sfft_status sfft_execute_host(sfft_plan plan, const void* h_x, uint32_t batch, u
 sfft_status sfft_execute_channels(sfft_plan plan, const void* d_x, uint32_t channels, uint64_t seed, uint32_t id,
                                   void* stream, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
                                   int32_t* d_flag);
-/* The same, recording the CUDA event `between` (a cudaEvent_t) on `stream` after the gather kernel
- * and before the finish, so that a caller can time the gather alone. */
+/* The same, recording the CUDA events `before` and `after` (cudaEvent_t, either may be NULL) on
+ * `stream` right before and right after the gather kernel, so that a caller can time the gather
+ * alone. */
 sfft_status sfft_execute_channels_timed(sfft_plan plan, const void* d_x, uint32_t channels, uint64_t seed, uint32_t id,
                                         void* stream, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
-                                        int32_t* d_flag, void* between);
+                                        int32_t* d_flag, void* before, void* after);
+
+/*
+ * Measurement, no part of the transform: read d_x[r][d_idx[r][i]] (complex64, row r of row_elems
+ * values, a power of two <= 2^31; each index taken mod row_elems) for r < rows, i < per_row, in the
+ * order given, with nothing else done: 16 reads in flight per thread, each through L2 only (one
+ * 32-byte sector per read, as in the transform's gathers), the values folded into d_sink[0..64)
+ * (caller-owned device words).  Timed around by the caller, it gives the rate at which this device
+ * serves a list of sample reads -- for instance a transform's own sample addresses in its own order,
+ * in random order, or sorted by address.
+ * Errors: INVALID_ARG (null pointer, zero sizes, row_elems not a power of two), CUDA.
+ */
+sfft_status sfft_gather_rate(const void* d_x, uint64_t row_elems, uint32_t rows, const uint32_t* d_idx,
+                             uint32_t per_row, uint32_t* d_sink, void* stream);
 
 /*
  * One request of sfft_execute_requests: its own signal, seed and request index.  The result depends

@@ -608,7 +608,7 @@ sfft_status sfft_execute(sfft_plan plan, const void* d_x, uint32_t batch, uint64
 
 static sfft_status execute_channels(sfft_plan plan, const void* d_x, uint32_t channels, uint64_t seed, uint32_t id,
                                    cudaStream_t st, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
-                                   int32_t* d_flag, cudaEvent_t between) {
+                                   int32_t* d_flag, cudaEvent_t before, cudaEvent_t after) {
     if (!plan || !d_x || !d_idx || !d_val || !d_count || !d_flag || cap == 0) return SFFT_ERR_INVALID_ARG;
     if (plan->p.mode != SFFT_EXACT || plan->p.precision != SFFT_FP32 || plan->chan_off.empty())
         return SFFT_ERR_INVALID_ARG;
@@ -633,7 +633,8 @@ static sfft_status execute_channels(sfft_plan plan, const void* d_x, uint32_t ch
         a.out_count = d_count;
         a.out_flag = d_flag;
     }
-    SFFT_CUDA(launch_exact_channels(rounds, R, channels, d_x, seed, id, plan->step_smem, plan->d_aux, st, between),
+    SFFT_CUDA(launch_exact_channels(rounds, R, channels, d_x, seed, id, plan->step_smem, plan->d_aux, st, before,
+                                    after),
               "channel batch");
     return SFFT_OK;
 }
@@ -642,14 +643,14 @@ sfft_status sfft_execute_channels(sfft_plan plan, const void* d_x, uint32_t chan
                                   void* stream, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
                                   int32_t* d_flag) {
     return execute_channels(plan, d_x, channels, seed, id, (cudaStream_t)stream, d_idx, d_val, cap, d_count, d_flag,
-                            nullptr);
+                            nullptr, nullptr);
 }
 
 sfft_status sfft_execute_channels_timed(sfft_plan plan, const void* d_x, uint32_t channels, uint64_t seed, uint32_t id,
                                         void* stream, uint32_t* d_idx, double* d_val, uint32_t cap, uint32_t* d_count,
-                                        int32_t* d_flag, void* between) {
+                                        int32_t* d_flag, void* before, void* after) {
     return execute_channels(plan, d_x, channels, seed, id, (cudaStream_t)stream, d_idx, d_val, cap, d_count, d_flag,
-                            (cudaEvent_t)between);
+                            (cudaEvent_t)before, (cudaEvent_t)after);
 }
 
 sfft_status sfft_execute_trace(sfft_plan plan, const void* d_x, uint32_t batch, uint64_t seed, void* stream,

@@ -866,7 +866,7 @@ __global__ void __launch_bounds__(kThreads) k_chan_gather(const __grid_constant_
                 sincospif((float)es * (2.0f / (float)a.n), &sn, &cs);
                 co = make_float2(gt * cs, -gt * sn);
             }
-            coef[tid * kMaxHash + h] = co;
+            if (tid < kChanRows) coef[tid * kMaxHash + h] = co;
         }
     }
     __syncthreads();  // the coefficients
@@ -1151,7 +1151,8 @@ __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uin
 // created later with smaller rounds cannot lower it under another plan's feet.
 template <int NR>
 static cudaError_t launch_chan_nr(const ExactArgs* rounds, uint32_t R, uint32_t C, const void* x, uint64_t seed,
-                                  uint32_t id, size_t smem, uint32_t* error, cudaStream_t st, cudaEvent_t between) {
+                                  uint32_t id, size_t smem, uint32_t* error, cudaStream_t st, cudaEvent_t before,
+                                  cudaEvent_t after) {
     ChanParams<NR> cp;
     StepParams<NR> sp;
     cp.R = sp.R = R;
@@ -1187,9 +1188,10 @@ static cudaError_t launch_chan_nr(const ExactArgs* rounds, uint32_t R, uint32_t 
     }
     cudaError_t e = cudaMemsetAsync(error, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
+    if (before && (e = cudaEventRecord(before, st)) != cudaSuccess) return e;
     k_chan_gather<NR><<<cp.cseg[R], kThreads, gsmem, st>>>(cp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (between && (e = cudaEventRecord(between, st)) != cudaSuccess) return e;
+    if (after && (e = cudaEventRecord(after, st)) != cudaSuccess) return e;
     k_chan_bins<NR><<<sp.seg[R], kThreads, smem, st>>>(sp, seed, id);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_chan_decode<NR><<<C, kThreads, smem, st>>>(sp, seed, id, error);
@@ -1197,11 +1199,12 @@ static cudaError_t launch_chan_nr(const ExactArgs* rounds, uint32_t R, uint32_t 
 }
 
 cudaError_t launch_exact_channels(const ExactArgs* rounds, uint32_t R, uint32_t C, const void* x, uint64_t seed,
-                                  uint32_t id, size_t smem, uint32_t* error, cudaStream_t st, cudaEvent_t between) {
+                                  uint32_t id, size_t smem, uint32_t* error, cudaStream_t st, cudaEvent_t before,
+                                  cudaEvent_t after) {
     if (R == 0 || R > kMaxRounds || C == 0 || C % 32 || C > kChanMaxC || !error) return cudaErrorInvalidValue;
-    if (R <= 8) return launch_chan_nr<8>(rounds, R, C, x, seed, id, smem, error, st, between);
-    if (R <= 16) return launch_chan_nr<16>(rounds, R, C, x, seed, id, smem, error, st, between);
-    return launch_chan_nr<32>(rounds, R, C, x, seed, id, smem, error, st, between);
+    if (R <= 8) return launch_chan_nr<8>(rounds, R, C, x, seed, id, smem, error, st, before, after);
+    if (R <= 16) return launch_chan_nr<16>(rounds, R, C, x, seed, id, smem, error, st, before, after);
+    return launch_chan_nr<32>(rounds, R, C, x, seed, id, smem, error, st, before, after);
 }
 
 cudaError_t set_exact_smem_limit(size_t bytes, bool fp64) {

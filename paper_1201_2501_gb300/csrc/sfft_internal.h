@@ -123,7 +123,8 @@ struct StepParams {
 // partial-fold area laid out as the one-launch path's ([chunk][H][B] per round, round t at
 // chan_off[t]); then every (round, slot) forms its bins at once, and one CTA per slot runs the
 // decodes in order.
-constexpr uint32_t kChanRows = 32;   // rows of a residue class per CTA
+constexpr uint32_t kChanRows = 16;   // rows of a residue class per CTA (one lane of warp 0 each)
+static_assert(kChanRows <= 32, "warp 0 issues one row copy per lane");
 constexpr uint32_t kChanMaxC = 256;  // channels of one batch (a row of the stage holds them all)
 template <int NR>
 struct ChanParams {
@@ -400,12 +401,13 @@ cudaError_t launch_exact_round(const ExactArgs& a, uint32_t batch, size_t smem, 
 // rounds[0..R) with this launch's fields filled in; grid = sum over rounds of chunks x batch
 cudaError_t launch_exact_step(const ExactArgs* rounds, uint32_t R, uint32_t batch, size_t smem, cudaStream_t st,
                               bool fp64);
-// multi-channel batch with shared hashing: the gather (one CTA per round, residue and chunk), an
-// optional event recorded after it, the bins of every (round, slot), then one CTA per slot for the
+// multi-channel batch with shared hashing: the gather (one CTA per round, residue and chunk) between
+// two optional events, the bins of every (round, slot), then one CTA per slot for the
 // decodes; rounds[t].part and .chunks give each round's channel layout; error: a device word the
 // gather sets when a bulk copy times out (cleared here first)
 cudaError_t launch_exact_channels(const ExactArgs* rounds, uint32_t R, uint32_t C, const void* x, uint64_t seed,
-                                  uint32_t id, size_t smem, uint32_t* error, cudaStream_t st, cudaEvent_t between);
+                                  uint32_t id, size_t smem, uint32_t* error, cudaStream_t st, cudaEvent_t before,
+                                  cudaEvent_t after);
 // persistent path: CTAs that fit on the device at `smem`, and the launch
 int exact_persistent_ctas(size_t smem, bool fp64);
 cudaError_t launch_exact_persistent(const PersistArgs& a, uint32_t ctas, size_t smem, cudaStream_t st, bool fp64);

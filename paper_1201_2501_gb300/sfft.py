@@ -178,7 +178,9 @@ _SIGS = {
     "sfft_wait": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(SfftJobResult)]),
     "sfft_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(SfftServerStats)]),
     "sfft_execute_channels": (ctypes.c_int, [_vp, _vp, _u32, _u64, _u32, _vp, _vp, _vp, _u32, _vp, _vp]),
-    "sfft_execute_channels_timed": (ctypes.c_int, [_vp, _vp, _u32, _u64, _u32, _vp, _vp, _vp, _u32, _vp, _vp, _vp]),
+    "sfft_execute_channels_timed": (ctypes.c_int, [_vp, _vp, _u32, _u64, _u32, _vp, _vp, _vp, _u32, _vp, _vp, _vp,
+                                                   _vp]),
+    "sfft_gather_rate": (ctypes.c_int, [_vp, _u64, _u32, _vp, _u32, _vp, _vp]),
     "sfft_execute_trace": (ctypes.c_int, [_vp, _vp, _u32, _u64, _vp, _vp, _vp, _u32, _vp, _vp,
                                           ctypes.POINTER(SfftGeneralTrace)]),
 }
@@ -649,10 +651,12 @@ def sfft_hash_to_bins_static(n: int, B: int, T: int, taps, wtab, x, sigma: int, 
     return out
 
 
-def sfft_execute_channels(plan: Plan, x, seed: int, id: int, cap: int, outputs=None, stream=None, between=None):
+def sfft_execute_channels(plan: Plan, x, seed: int, id: int, cap: int, outputs=None, stream=None, before=None,
+                          after=None):
     """Multi-channel batch with shared hashing (sfft_execute_channels): ``x`` is a torch tensor [n, C]
     complex64 on the GPU (row m = sample m of every channel), every channel transformed with the draws
-    of request ``id`` under ``seed``.  ``between`` (a torch.cuda.Event) is recorded after the gather.
+    of request ``id`` under ``seed``.  ``before`` / ``after`` (torch.cuda.Event, already recorded once
+    so that torch has created them) are recorded around the gather kernel.
     Returns (idx [C, cap], val [C, cap, 2], count [C], flag [C]) device tensors, slot c = channel c."""
     import torch
 
@@ -666,14 +670,22 @@ def sfft_execute_channels(plan: Plan, x, seed: int, id: int, cap: int, outputs=N
                    torch.empty((C,), dtype=torch.int32, device=dev),
                    torch.empty((C,), dtype=torch.int32, device=dev))
     idx, val, count, flag = outputs
-    if between is None:
+    if before is None and after is None:
         _check(lib().sfft_execute_channels(plan.handle, _ptr(x), C, seed, id, _stream_ptr(stream), _ptr(idx), _ptr(val),
                                            cap, _ptr(count), _ptr(flag)), "sfft_execute_channels")
     else:
+        ev = lambda e: ctypes.c_void_p(e.cuda_event if e is not None else None)
         _check(lib().sfft_execute_channels_timed(plan.handle, _ptr(x), C, seed, id, _stream_ptr(stream), _ptr(idx),
-                                                 _ptr(val), cap, _ptr(count), _ptr(flag),
-                                                 ctypes.c_void_p(between.cuda_event)), "sfft_execute_channels_timed")
+                                                 _ptr(val), cap, _ptr(count), _ptr(flag), ev(before), ev(after)),
+               "sfft_execute_channels_timed")
     return outputs
+
+
+def sfft_gather_rate(x, row_elems: int, rows: int, idx, per_row: int, sink, stream=None):
+    """Measurement: read x[r][idx[r][i]] in the order given (sfft_gather_rate); ``x`` and ``idx`` (int32
+    [rows, per_row]) and ``sink`` (int32 [64]) are device tensors."""
+    _check(lib().sfft_gather_rate(_ptr(x), row_elems, rows, _ptr(idx), per_row, _ptr(sink), _stream_ptr(stream)),
+           "sfft_gather_rate")
 
 
 def sfft_execute_trace(plan: Plan, x, seed: int, cap: int, round_: int, stream=None):
