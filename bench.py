@@ -761,6 +761,36 @@ def gather_ceilings(sfft, plan, x, stream, reps=10):
 CHAN_C = 256
 
 
+def run_channels(args):
+    """The multi-channel workload alone, as a bench line of its own (rank 0; replicas under torchrun)."""
+    import torch
+
+    rank, world, local = dist_setup(args.gpus)
+    from paper_1201_2501_gb300 import build, sfft, workloads
+
+    if rank == 0 or world > 1:
+        build.build()
+    barrier(world)
+    n = 1 << args.n_log2
+    x, _, _ = workloads.exact_sparse_batch_device(n, K, [workloads.seed_for(2, i) for i in range(CHAN_C)], "cuda")
+    stream = torch.cuda.current_stream()
+    with ClockSampler(local) as clk:
+        ch = channels_measurement(sfft, x, stream, args)
+    barrier(world)
+    if rank == 0:
+        line = {"metric": "sFFT transforms/s, multi-channel batch with shared hashing (second workload)",
+                "value": ch["value"] * world, "unit": "transforms/s", "n_gpus": world, "steps": ch["steps"],
+                "warmup": 5, "ms_per_step": ch["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": ch["workload"].replace("n=2^22", f"n=2^{args.n_log2}"), "n": n, "k": K,
+                           "channels": CHAN_C, "support_exact_fraction": ch["support_exact_fraction"],
+                           "l2": "inputs exceed L2; no flush" if n >= 1 << 20 else "inputs fit L2"},
+                "roofline": ch["roofline"], "clocks": clk.summary(),
+                "gpu_launches": ch["gpu_launches_per_step"] * ch["steps"]}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def channels_measurement(sfft, x, stream, args):
     """The same transform on a multi-channel batch with shared hashing (sfft_execute_channels): the
     batch's 256 signals interleaved as [n][256] complex64 (8 GiB), every channel with the draws of one
@@ -770,6 +800,7 @@ def channels_measurement(sfft, x, stream, args):
     import torch
 
     n = x.shape[1]
+    n_log2 = n.bit_length() - 1
     C = min(CHAN_C, x.shape[0])
     params = sfft.sfft_params_default(n, K, sfft.SFFT_EXACT, delta=DELTA)
     params.alpha0 = ALPHA0
@@ -812,7 +843,7 @@ def channels_measurement(sfft, x, stream, args):
     achieved = bytes_launch / (g_ms / 1000) / 1e9
     plan.close()
     del xc
-    return {"workload": f"{C} channels interleaved [n][{C}] complex64, n=2^22, k=64 per channel, shared hashing "
+    return {"workload": f"{C} channels interleaved [n][{C}] complex64, n=2^{n_log2}, k=64 per channel, shared hashing "
                         "(one request index), B=4k, delta=1e-6, alpha0=5/8",
             "value": C / (ms / 1000), "unit": "transforms/s", "ms_per_step": ms, "steps": steps,
             "support_exact_fraction": exact / C,
@@ -1157,8 +1188,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-general", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--workload", default="exact", choices=["exact", "general"],
-                    help="exact: the n=2^22, k=64 benchmark; general: the noisy n=2^22, k=256 case as the timed step")
+    ap.add_argument("--workload", default="exact", choices=["exact", "general", "channels"],
+                    help="exact: the n=2^22, k=64 benchmark; general: the noisy n=2^22, k=256 case as the timed step; "
+                         "channels: the multi-channel batch with shared hashing (256 interleaved signals) alone")
+    ap.add_argument("--n-log2", type=int, default=N_LOG2, help="channels workload: log2 n (22 by default)")
     ap.add_argument("--mixed", action="store_true", help="also time the uneven mixed batch (1024 requests)")
     ap.add_argument("--mixed-requests", type=int, default=1024)
     ap.add_argument("--path", default="step", choices=["step", "persistent"],
@@ -1177,6 +1210,8 @@ def main():
         if args.batch == 256:
             args.batch = 32
         return run_general(args)
+    if args.workload == "channels":
+        return run_channels(args)
     return run_ours(args)
 
 
