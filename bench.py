@@ -358,6 +358,11 @@ def run_general(args):
                "sample": f"{len(res)} transforms (one per process) of the same workload, {wall:.1f} s wall, "
                          f"{busy:.1f} s oracle CPU time; oracle l2/l2 ratio mean "
                          f"{float(np.mean([r[1] for r in res])):.3f}"}
+        # the accuracy gate on the same requests (signal r, request index r, same seed) as the GPU batch
+        same = min(batch, len(res))
+        gpu_m, ora_m = float(np.mean(ratios[:same])), float(np.mean([r[1] for r in res[:same]]))
+        cpu["l2l2_gate"] = {"requests": same, "gpu_mean": gpu_m, "oracle_mean": ora_m, "gpu_over_oracle": gpu_m / ora_m,
+                            "target": "<= 1.05"}
     if rank == 0:
         line = {
             "metric": GEN_METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": args.steps,
