@@ -375,4 +375,26 @@ __device__ __forceinline__ uint32_t arrive(uint32_t* counter, uint32_t target) {
     return s_arrive_last;
 }
 
+// Arrival of one of two parties.  When an acquire load already sees the other party's arrival, this
+// CTA is the last: the other party's writes are visible through the load, and nobody reads this CTA's
+// writes through the counter, so the release fence and the atomic are skipped (the counter stays at 1
+// until the caller clears it).  Otherwise as arrive(counter, 2).
+__device__ __forceinline__ uint32_t arrive_pair(uint32_t* counter) {
+    __shared__ uint32_t s_pair_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t seen;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(counter) : "memory");
+        uint32_t last = 1u;
+        if (seen != 1u) {
+            __threadfence();
+            last = atomicAdd(counter, 1u) + 1u == 2u ? 1u : 0u;
+            if (last) __threadfence();
+        }
+        s_pair_last = last;
+    }
+    __syncthreads();
+    return s_pair_last;
+}
+
 }  // namespace sfft

@@ -524,7 +524,7 @@ enum FinPart { kFinBins = 1, kFinDecode = 2, kFinAll = 3 };
 
 template <typename R>
 __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uint32_t b, unsigned char* smem,
-                             int part = kFinAll) {
+                             int part = kFinAll, bool carry = false) {
     using C = typename Cx<R>::T;
     const uint32_t tid = threadIdx.x;
     const uint32_t B = a.B, H = a.H;
@@ -567,14 +567,25 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     // zhat of this request and its per-entry subtraction terms
     // zhat is read through L2 only: in the one-launch path another CTA of this launch wrote it
     // (the first entry of each thread is fetched together with the count)
+    // zhat of the previous round stays in this CTA's shared memory (up to kCarry entries) when the
+    // previous round's decode of this request ran here (carry): no global load for it then
+    __shared__ uint32_t c_idx[kCarry];
+    __shared__ double2 c_val[kCarry];
+    __shared__ uint32_t c_n;
+    const bool use_carry = carry && !a.bins_only && a.zcap <= kCarry;
     const uint32_t zlim = a.bins_only ? a.e_nz : a.zcap;
     uint32_t zi0 = 0;
     double2 zv0 = make_double2(0.0, 0.0);
-    if (tid < zlim) {
+    if (use_carry) {
+        if (tid < c_n) {
+            zi0 = c_idx[tid];
+            zv0 = c_val[tid];
+        }
+    } else if (tid < zlim) {
         zi0 = __ldcg(a.zidx + (size_t)s * a.zcap + tid);
         zv0 = __ldcg(a.zval + (size_t)s * a.zcap + tid);
     }
-    const uint32_t nz = a.bins_only ? a.e_nz : min(__ldcg(a.zcount + s), a.zcap);
+    const uint32_t nz = a.bins_only ? a.e_nz : (use_carry ? c_n : min(__ldcg(a.zcount + s), a.zcap));
     // the decode context is the same for every thread: one copy in shared memory (registers would
     // hold it only by spilling it to local memory)
     __shared__ DecodeCtx d;
@@ -586,9 +597,9 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     }
     __syncthreads();
     for (uint32_t e = tid; e < nz; e += kThreads) {
-        const uint32_t i = e == tid ? zi0 : __ldcg(a.zidx + (size_t)s * a.zcap + e);
+        const uint32_t i = e == tid ? zi0 : (use_carry ? c_idx[e] : __ldcg(a.zidx + (size_t)s * a.zcap + e));
         ent_idx[e] = i;
-        ent_val[e] = e == tid ? zv0 : __ldcg(a.zval + (size_t)s * a.zcap + e);
+        ent_val[e] = e == tid ? zv0 : (use_carry ? c_val[e] : __ldcg(a.zval + (size_t)s * a.zcap + e));
         uint32_t jb;
         const int32_t o = offset_of((sigma * (i - b)) & a.nmask, d, &jb);
         ent_bin[e] = jb;
@@ -644,22 +655,24 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
             cand_idx[slot] = oi;
             cand_bin[slot] = j;
             cand_gain[slot] = gain;
+            // its value: u_0 (step 4 in FP64) / W(-o)
+            const double2 u0 = subtracted_u0(U, H, j, list, nbin, ent_sub);
+            cand_val[slot] = make_double2(u0.x / gain, u0.y / gain);
         }
     }
     __syncthreads();
-    // values of the decoded bins: u_0 (step 4 in FP64) / W(-o), for the candidates only
     const uint32_t nw = s_nw;
-    for (uint32_t c = tid; c < nw; c += kThreads) {
-        const uint32_t j = cand_bin[c];
-        const double2 u0 = subtracted_u0(U, H, j, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_sub);
-        const double g = cand_gain[c];
-        cand_val[c] = make_double2(u0.x / g, u0.y / g);
-    }
-    __syncthreads();
 
     const bool last = a.last_round != 0;
     if (nw == 0) {
         // nothing decoded: zhat stays as it is (its entries passed the same prune test when merged)
+        if (!a.bins_only && a.zcap <= kCarry && !use_carry) {  // this CTA keeps it for the next round
+            for (uint32_t e = tid; e < nz; e += kThreads) {
+                c_idx[e] = ent_idx[e];
+                c_val[e] = ent_val[e];
+            }
+            if (tid == 0) c_n = nz;
+        }
         if (last) {
             for (uint32_t e = tid; e < nz && e < a.out_cap; e += kThreads) {
                 a.out_idx[(size_t)s * a.out_cap + e] = ent_idx[e];
@@ -720,6 +733,10 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         if (pos < a.zcap) {
             zi[pos] = idx;
             zv[pos] = v;
+            if (a.zcap <= kCarry) {
+                c_idx[pos] = idx;
+                c_val[pos] = v;
+            }
         }
         if (last && pos < a.out_cap) {
             a.out_idx[(size_t)s * a.out_cap + pos] = idx;
@@ -730,6 +747,7 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         const bool overflow = newcount > a.zcap;
         if (overflow) a.zflag[s] = 1;
         a.zcount[s] = overflow ? a.zcap : newcount;
+        c_n = overflow ? a.zcap : newcount;
         if (last) {
             const uint32_t kept_count = overflow ? a.zcap : newcount;
             a.out_count[s] = kept_count < a.out_cap ? kept_count : a.out_cap;
@@ -776,15 +794,15 @@ template <typename R, int NR>
 __device__ __forceinline__ void decode_chain(const StepParams<NR>& sp, uint32_t t, const ExactArgs* a, uint32_t s,
                                              uint64_t seed, uint32_t id, uint32_t sigma, uint32_t b,
                                              unsigned char* smem) {
-    if (arrive(a->counter2 + s, t > 0 ? 2u : 1u) == 0) return;
-    for (;;) {
+    if ((t > 0 ? arrive_pair(a->counter2 + s) : arrive(a->counter2 + s, 1u)) == 0) return;
+    for (bool carried = false;; carried = true) {
         finish_round<R>(*a, s, sigma, b, a->fin_scratch ? a->fin_scratch + (size_t)s * a->fin_stride : smem,
-                        kFinDecode);
+                        kFinDecode, carried);
         if (threadIdx.x == 0) a->counter2[s] = 0;  // both arrivals of round t have happened
         if (t + 1 >= sp.R) break;
         a = &sp.r[++t];
         // zhat of round t is published by the arrival at round t + 1's second counter
-        if (arrive(a->counter2 + s, 2u) == 0) break;
+        if (arrive_pair(a->counter2 + s) == 0) break;
         exact_hash(seed, id, t, a->nmask, &sigma, &b);
     }
 }
@@ -928,7 +946,7 @@ __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_chan_decode
         uint32_t sigma, b;
         exact_hash(seed, id, t, a.nmask, &sigma, &b);
         finish_round<float>(a, s, sigma, b, a.fin_scratch ? a.fin_scratch + (size_t)s * a.fin_stride : smem,
-                            kFinDecode);
+                            kFinDecode, t > 0);
         __syncthreads();  // zhat of round t is read by round t + 1 (same CTA)
     }
 }

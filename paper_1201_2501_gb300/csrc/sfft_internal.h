@@ -14,6 +14,7 @@ namespace sfft {
 constexpr int kThreads = 256;     // threads per CTA of every kernel
 constexpr int kChunkTaps = 2048;  // taps per CTA in the gather phase (8 per thread)
 constexpr int kMaxHash = 4;       // hashings per exact round: a = 0 plus up to 3 ladder shifts
+constexpr uint32_t kCarry = 256;  // zhat entries an exact finisher keeps on chip for the next round
 constexpr uint32_t kMaxB = 4096;  // largest B of the fused exact round
 constexpr uint32_t kNoIndex = 0xFFFFFFFFu;
 constexpr size_t kFinSmemMax = 160 * 1024;  // largest on-chip finisher of the exact round
