@@ -859,9 +859,31 @@ def channels_measurement(sfft, x, stream, args):
                                  "median event time"}}
 
 
-SERVE_EXPS = (16, 18, 20, 22, 24, 26)
-SERVE_K_EXACT = (8, 32, 128, 512, 1024)
-SERVE_K_GENERAL = (8, 32, 128)
+SERVE_TYPES = 48                   # parameter sets of the serving stream
+SERVE_EXACT_LOG2 = (16, 26)         # n = 2^e, e uniform on these bounds (exactly k-sparse half)
+SERVE_GENERAL_LOG2 = (16, 24)       # (noisy half)
+SERVE_GENERAL_COPY_MAX_LOG2 = 22    # largest n whose general plans keep the permuted copy
+
+
+def serving_types(sfft):
+    """The serving stream's parameter sets, drawn from the serving configuration's distributions: half
+    exactly k-sparse, half k heavy coefficients + noise at SNR 20 dB; n = 2^e with e uniform on the
+    integers of SERVE_*_LOG2 (log-uniform n); k = floor(2^U[3, 10]) (log-uniform on 8..1024) for the
+    exact half and floor(2^U[3, 9]) (8..512, the general mode's range here) for the noisy half, redrawn
+    while k > n / 64.  Requests then pick a set uniformly."""
+    rng = np.random.default_rng(0x5EED5005)
+    types = []
+    for i in range(SERVE_TYPES):
+        mode = sfft.SFFT_EXACT if i % 2 == 0 else sfft.SFFT_GENERAL
+        lo, hi = SERVE_EXACT_LOG2 if mode == sfft.SFFT_EXACT else SERVE_GENERAL_LOG2
+        kmax_log2 = 10.0 if mode == sfft.SFFT_EXACT else 9.0  # general mode: B = 8k <= 4096 in this library
+        while True:
+            e = int(rng.integers(lo, hi + 1))
+            k = int(np.floor(2.0 ** rng.uniform(3.0, kmax_log2)))
+            if k <= (1 << e) // 64:
+                break
+        types.append((e, k, mode))
+    return types
 
 
 def _serve_stream(srv, sigs, params, seq, rate, seed):
@@ -873,29 +895,42 @@ def _serve_stream(srv, sigs, params, seq, rate, seed):
 
     q = queue.Queue()
     lat = []
+    failed = []
 
     def waiter():
-        for _ in range(len(seq)):
-            t = q.get()
-            _, _, info = srv.wait(t, timeout_s=300)
-            lat.append(info["latency_us"])
+        try:
+            for _ in range(len(seq)):
+                t = q.get()
+                if t is None:  # the submitter failed: stop
+                    return
+                _, _, info = srv.wait(t, timeout_s=300)
+                lat.append(info["latency_us"])
+        except BaseException as ex:  # reported by the submitting thread
+            failed.append(ex)
 
-    th = threading.Thread(target=waiter)
+    th = threading.Thread(target=waiter, daemon=True)
     th.start()
     st0 = srv.stats()
     gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=len(seq)) if rate else np.zeros(len(seq))
     t0 = time.perf_counter()
     due = t0
-    for r, (ti, i) in enumerate(seq):
-        due += gaps[r]
-        while True:
-            d = due - time.perf_counter()
-            if d <= 0:
-                break
-            if d > 2e-4:
-                time.sleep(d - 1e-4)
-        q.put(srv.submit(params[ti], sigs[(ti, i)], SEED, id=r))
+    try:
+        for r, (ti, i) in enumerate(seq):
+            due += gaps[r]
+            while True:
+                d = due - time.perf_counter()
+                if d <= 0:
+                    break
+                if d > 2e-4:
+                    time.sleep(d - 1e-4)
+            q.put(srv.submit(params[ti], sigs[(ti, i)], SEED, id=r))
+    except BaseException:
+        q.put(None)
+        th.join(timeout=60)
+        raise
     th.join()
+    if failed:
+        raise failed[0]
     el = time.perf_counter() - t0
     st1 = srv.stats()
     launches = st1["launches"] - st0["launches"]
@@ -917,15 +952,19 @@ def serving_measurement(sfft, args):
 
     from paper_1201_2501_gb300 import workloads
 
-    types = [(e, k, sfft.SFFT_EXACT) for e in SERVE_EXPS for k in SERVE_K_EXACT]
-    types += [(e, k, sfft.SFFT_GENERAL) for e in SERVE_EXPS for k in SERVE_K_GENERAL]
+    types = serving_types(sfft)
     per_type = 2
     sigs = {}
     for ti, (e, k, mode) in enumerate(types):
         for i in range(per_type):
             sigs[(ti, i)] = workloads.sparse_signal_device(1 << e, k, workloads.seed_for(5, 100 * ti + i), "cuda",
                                                            snr_db=None if mode == sfft.SFFT_EXACT else 20.0)[0]
-    params = [sfft.sfft_params_default(1 << e, k, mode, delta=DELTA) for (e, k, mode) in types]
+    params = []
+    for e, k, mode in types:
+        p_ = sfft.sfft_params_default(1 << e, k, mode, delta=DELTA)
+        if mode == sfft.SFFT_GENERAL and e >= SERVE_GENERAL_COPY_MAX_LOG2 + 1:
+            p_.permuted_copy = 1  # a per-request copy of n samples x max_batch would take gigabytes
+        params.append(p_)
     rng = np.random.default_rng(0x5EED5000)
     seq = [(int(rng.integers(len(types))), int(rng.integers(per_type))) for _ in range(args.serve_requests)]
     srv = sfft.Server(max_batch=64, instances=2, max_plans=len(types) + 4)
@@ -971,11 +1010,13 @@ def serving_measurement(sfft, args):
     del sigs
     torch.cuda.empty_cache()
     return {
-        "workload": "n = 2^e, e uniform on {16,18,20,22,24,26}; k uniform on {8,32,128,512,1024} for the exactly "
-                    "k-sparse half, on {8,32,128} for the half with k heavy coefficients + complex Gaussian time "
-                    "noise at SNR 20 dB; "
-                    f"{len(types)} parameter sets x {per_type} resident signals; Poisson arrivals; "
+        "workload": f"{len(types)} parameter sets drawn from the serving configuration: half exactly k-sparse "
+                    f"(n = 2^e, e uniform on {SERVE_EXACT_LOG2[0]}..{SERVE_EXACT_LOG2[1]}), half k heavy coefficients "
+                    f"+ complex Gaussian time noise at SNR 20 dB (e on {SERVE_GENERAL_LOG2[0]}..{SERVE_GENERAL_LOG2[1]}); "
+                    "k = floor(2^U[3,10]) (log-uniform 8..1024) exact, floor(2^U[3,9]) (8..512) general, k <= n/64; "
+                    f"{per_type} resident signals per set; Poisson arrivals; general batches replayed as CUDA graphs; "
                     "latency = submission to completion on the host clock",
+        "types": [{"n_log2": e, "k": k, "mode": "exact" if m == sfft.SFFT_EXACT else "general"} for e, k, m in types],
         "requests": len(seq),
         "all_at_once": {"throughput_per_s": thr_all, "p50_us": _pct(lat_all, 0.5), "p99_us": _pct(lat_all, 0.99),
                         "mean_batch": mb_all},

@@ -109,6 +109,10 @@ struct Instance {
     uint32_t* d_count = nullptr;
     int32_t* d_flag = nullptr;
     size_t bytes = 0;              // device bytes (plan + outputs)
+    // general-mode plans: one CUDA graph per batch size, made on first use, that replays the whole
+    // transform of the plan's request table into this instance's outputs (a general batch is tens of
+    // launches; the dispatcher then issues one)
+    std::map<uint32_t, sfft_graph> graphs;
 };
 
 struct ParamSet {
@@ -136,6 +140,8 @@ struct BuildResult {
 
 void destroy_instance(Instance* in) {
     if (!in) return;
+    for (auto& g : in->graphs) sfft_graph_destroy(g.second);
+    in->graphs.clear();
     if (in->plan) sfft_plan_destroy(in->plan);
     if (in->stream) cudaStreamDestroy(in->stream);
     if (in->done) cudaEventDestroy(in->done);
@@ -554,7 +560,21 @@ void launch(sfft_server_s* S) {
                 e = cudaMemcpyAsync(in->plan->d_reqs, in->h_table, (size_t)batch * sizeof(ReqDesc),
                                     cudaMemcpyHostToDevice, in->stream);
             sfft_status st = e == cudaSuccess ? SFFT_OK : SFFT_ERR_CUDA;
-            if (st == SFFT_OK)
+            sfft_graph g = nullptr;
+            if (st == SFFT_OK && ps.p.mode == SFFT_GENERAL) {
+                auto it = in->graphs.find(batch);
+                if (it != in->graphs.end()) {
+                    g = it->second;
+                } else if (sfft_graph_create(in->plan, nullptr, batch, 0, in->d_idx, in->d_val, zc, in->d_count,
+                                             in->d_flag, &g) == SFFT_OK) {
+                    in->graphs[batch] = g;
+                } else {
+                    g = nullptr;  // run it as plain launches
+                }
+            }
+            if (st == SFFT_OK && g)
+                st = sfft_graph_launch(g, in->stream);
+            else if (st == SFFT_OK)
                 st = execute_batch(in->plan, nullptr, in->plan->d_reqs, batch, 0, in->stream, in->d_idx, in->d_val,
                                    zc, in->d_count, in->d_flag);
             if (st == SFFT_OK) {

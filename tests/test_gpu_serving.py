@@ -147,6 +147,13 @@ def test_server_results_equal_alone_and_in_the_mix(sf):
             assert np.array_equal(idx, oi.astype(np.int64)), j
             assert np.max(np.abs(val - ov)) < 1e-5, j
             assert np.array_equal(idx, s.support)
+        else:
+            # general jobs (served as CUDA-graph batches): the oracle's support, values within 1e-5
+            P = oracle_params(fields)
+            oi, ov, of = oracle.sfft_general(P, s.x.astype(np.complex128), SEED + j, j)
+            assert np.array_equal(idx, oi.astype(np.int64)), j
+            scale = max(1.0, float(np.max(np.abs(ov), initial=0.0)))
+            assert np.max(np.abs(val - ov), initial=0.0) <= 1e-5 * scale, j
 
 
 def test_server_admits_by_device_memory(sf):
