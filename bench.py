@@ -630,6 +630,28 @@ def run_ours(args):
     return 0
 
 
+def device_latencies(launch, stream, runs, chunk=64, sleep_cycles=20_000_000):
+    """Device time of `runs` calls of launch(i), each between two events on `stream`.  Every chunk of
+    calls is queued behind a short sleep kernel (about 10 ms), so the host has queued the whole chunk
+    before the device reaches it: no host time (argument marshalling, launch calls) falls between an
+    event pair, and the calls run back to back as a loaded device would run them."""
+    import torch
+
+    lat = []
+    for c0 in range(0, runs, chunk):
+        m = min(chunk, runs - c0)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(m)]
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(sleep_cycles)
+        for i, (a, b) in enumerate(ev):
+            a.record(stream)
+            launch(c0 + i)
+            b.record(stream)
+        torch.cuda.synchronize()
+        lat += [a.elapsed_time(b) * 1000 for a, b in ev]
+    return sorted(lat)
+
+
 def context_measurements(sfft, plan, x, cap, stream, args):
     """cuFFT dense FFT of the same signals, the plain one-request-at-a-time GPU sFFT and latency."""
     import torch
@@ -641,36 +663,40 @@ def context_measurements(sfft, plan, x, cap, stream, args):
     o1 = (torch.empty((1, cap), dtype=torch.int32, device="cuda"),
           torch.empty((1, cap, 2), dtype=torch.float64, device="cuda"),
           torch.empty((1,), dtype=torch.int32, device="cuda"), torch.empty((1,), dtype=torch.int32, device="cuda"))
-    lat = []
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.lat_runs)]
     for i in range(10):
         sfft.sfft_execute(p1, x[i % x.shape[0]: i % x.shape[0] + 1], SEED, cap, o1, stream)
     torch.cuda.synchronize()
-    for i, (a, b) in enumerate(ev):
+
+    def one(i):
         r = i % x.shape[0]
-        a.record(stream)
         sfft.sfft_execute(p1, x[r:r + 1], SEED, cap, o1, stream)
-        b.record(stream)
-    torch.cuda.synchronize()
-    lat = sorted(a.elapsed_time(b) * 1000 for a, b in ev)
+
+    lat = device_latencies(one, stream, args.lat_runs)
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
-    out["latency_us"] = {"p50": p50, "p99": p99, "runs": len(lat), "what": "one request per call, device time"}
+    out["latency_us"] = {"p50": p50, "p99": p99, "runs": len(lat),
+                         "what": "one request per call, device time (calls queued ahead of the device)"}
     # the same single request replayed as a CUDA graph (every round's launches in one graph launch)
     g1 = sfft.Graph(p1, x[0:1], 1, SEED, cap, o1)
     for _ in range(10):
         g1.launch(stream)
     torch.cuda.synchronize()
-    for i, (a, b) in enumerate(ev):
-        a.record(stream)
-        g1.launch(stream)
-        b.record(stream)
-    torch.cuda.synchronize()
-    lat_g = sorted(a.elapsed_time(b) * 1000 for a, b in ev)
+    lat_g = device_latencies(lambda i: g1.launch(stream), stream, args.lat_runs)
     g1.close()
     out["latency_graph_us"] = {"p50": lat_g[len(lat_g) // 2],
                                "p99": lat_g[min(len(lat_g) - 1, int(math.ceil(0.99 * len(lat_g))) - 1)],
                                "runs": len(lat_g), "what": "one request per graph launch (sfft_graph_launch), device time"}
+    # cuFFT of one signal, the same way: device time of a single dense transform
+    y1 = torch.empty((1, n), dtype=torch.complex64, device="cuda")
+    for _ in range(3):
+        torch.fft.fft(x[0:1], out=y1)
+    torch.cuda.synchronize()
+    lat_c = device_latencies(lambda i: torch.fft.fft(x[i % x.shape[0]: i % x.shape[0] + 1], out=y1), stream,
+                             args.lat_runs)
+    del y1
+    out["latency_cufft_us"] = {"p50": lat_c[len(lat_c) // 2],
+                               "p99": lat_c[min(len(lat_c) - 1, int(math.ceil(0.99 * len(lat_c))) - 1)],
+                               "runs": len(lat_c), "what": "cuFFT C2C forward of one signal (torch.fft.fft), device time"}
     # plain GPU sFFT: the same kernels, one request at a time, no batching
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = min(x.shape[0], 256)

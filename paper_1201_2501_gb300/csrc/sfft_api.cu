@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <string>
 
@@ -112,6 +113,7 @@ ExactArgs base_args(const sfft_plan_s* pl, const ExactRound& r, uint32_t t) {
     a.taps32 = pl->d_taps32 + r.taps_off;
     a.taps64 = pl->d_taps64 + r.taps_off;
     a.wtab = pl->d_wtab + r.wtab_off;
+    a.winv = a.wtab + (p.n / r.B) / 2 + 1;  // the exact schedule stores 1 / W(o) after W(o)
     a.part = pl->d_part;
     a.part_stride = pl->part_stride;
     a.fin_scratch = r.fin_global ? pl->d_fin : nullptr;
@@ -129,6 +131,14 @@ ExactArgs base_args(const sfft_plan_s* pl, const ExactRound& r, uint32_t t) {
     a.ref_lo = p.ref_lo;
     a.ref_hi = p.ref_hi;
     a.ref_tol = p.ref_tol;
+    a.thr_f = (float)p.thr;
+    a.iso_tol_f = (float)p.iso_tol;
+    a.ref_lo_f = (float)(p.ref_lo * p.thr);
+    a.ref_hi_f = (float)(p.ref_hi * p.thr);
+    a.ref_tol_f = (float)p.ref_tol;
+    const double drop = p.prune * p.thr;
+    a.drop_f = (float)drop;
+    if ((double)a.drop_f < drop) a.drop_f = std::nextafter(a.drop_f, std::numeric_limits<float>::infinity());
     return a;
 }
 

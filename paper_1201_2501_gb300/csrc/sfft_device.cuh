@@ -176,6 +176,25 @@ __device__ inline uint32_t block_exclusive_scan(uint32_t* v, uint32_t len, uint3
     return total;
 }
 
+// The same for 0/1 flags, len <= kThreads (one per thread): warp ballots, one barrier for the warps'
+// counts and one after the result.
+__device__ inline uint32_t block_exclusive_scan_flags(uint32_t* v, uint32_t len, uint32_t* tmp) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, tid < len && v[tid] != 0u);
+    if (lane == 0) tmp[warp] = (uint32_t)__popc((int)bal);
+    __syncthreads();
+    uint32_t off = 0, total = 0;
+#pragma unroll
+    for (uint32_t w = 0; w < (uint32_t)kThreads / 32u; ++w) {
+        const uint32_t c = tmp[w];
+        off += w < warp ? c : 0u;
+        total += c;
+    }
+    if (tid < len) v[tid] = off + (uint32_t)__popc((int)(bal & ((1u << lane) - 1u)));
+    __syncthreads();
+    return total;
+}
+
 // number of entries of the ascending array a[0..len) that are < key (lower) or <= key (upper)
 __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t len, uint32_t key) {
     uint32_t lo = 0, hi = len;
@@ -373,6 +392,13 @@ __device__ __forceinline__ uint32_t arrive(uint32_t* counter, uint32_t target) {
     }
     __syncthreads();
     return s_arrive_last;
+}
+
+// an acquire load of *p (gpu scope) compared with v
+__device__ __forceinline__ bool acquire_is(const uint32_t* p, uint32_t v) {
+    uint32_t seen;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(p) : "memory");
+    return seen == v;
 }
 
 // Arrival of one of two parties.  When an acquire load already sees the other party's arrival, this

@@ -92,21 +92,26 @@ struct DecodeCtx {
     uint32_t shift[kMaxHash];  // ladder shifts beta_l (hashing l + 1)
     uint32_t logR[kMaxHash];   // log2(beta_l / B)
     const double* wtab;
+    const double* winv;        // 1 / W(o) beside wtab, or null
     double thr, iso_tol, gmin, ref_lo, ref_hi, ref_tol;
     // the same thresholds for the FP32 decisions (ref_lo_f, ref_hi_f already scaled by thr)
     float thr_f, iso_tol_f, ref_lo_f, ref_hi_f, ref_tol_f, inv_n_f;
 };
 
-__device__ __forceinline__ int32_t offset_of(uint32_t p, const DecodeCtx& d, uint32_t* jbin) {
-    const uint32_t jj = ((p + (d.Np >> 1)) & d.nmask) >> d.logNp;
-    const uint32_t dd = (p - jj * d.Np) & d.nmask;
+// bin j = round(p / Np) mod B of permuted position p, and the offset o = p - j Np in (-Np/2, Np/2]
+__device__ __forceinline__ int32_t offset_of(uint32_t p, uint32_t Np, uint32_t logNp, uint32_t nmask, uint32_t* jbin) {
+    const uint32_t jj = ((p + (Np >> 1)) & nmask) >> logNp;
+    const uint32_t dd = (p - jj * Np) & nmask;
     *jbin = jj;
-    return dd > (d.nmask >> 1) ? (int32_t)((int64_t)dd - (int64_t)d.n) : (int32_t)dd;
+    return dd > (nmask >> 1) ? (int32_t)((int64_t)dd - (int64_t)nmask - 1) : (int32_t)dd;
+}
+__device__ __forceinline__ int32_t offset_of(uint32_t p, const DecodeCtx& d, uint32_t* jbin) {
+    return offset_of(p, d.Np, d.logNp, d.nmask, jbin);
 }
 
-__device__ void fill_ctx(DecodeCtx& d, uint64_t n, uint32_t nmask, uint32_t B, uint32_t logB, uint32_t H,
-                         const uint64_t* ladder, uint32_t sigma, uint32_t b, const double* wtab, double thr,
-                         double iso_tol, double gmin, double ref_lo, double ref_hi, double ref_tol) {
+// the index part of the decode context: sizes, the hashing (sigma, sigma^-1, b) and the ladder
+__device__ void fill_ctx_index(DecodeCtx& d, uint64_t n, uint32_t nmask, uint32_t B, uint32_t logB, uint32_t H,
+                               const uint64_t* ladder, uint32_t sigma, uint32_t b) {
     d.n = (uint32_t)n;
     d.nmask = nmask;
     d.B = B;
@@ -121,7 +126,16 @@ __device__ void fill_ctx(DecodeCtx& d, uint64_t n, uint32_t nmask, uint32_t B, u
         d.shift[l] = (uint32_t)ladder[l];
         d.logR[l] = ladder[l] >= B ? ilog2_u32((uint32_t)(ladder[l] / B)) : 0u;
     }
+    d.inv_n_f = __int_as_float((127 - (int)ilog2_u32(d.n)) << 23);  // 2^-log2 n, exact
+}
+
+// decode context of a caller-bins decode: thresholds rounded to FP32 here, values divided by W(o)
+__device__ void fill_ctx(DecodeCtx& d, uint64_t n, uint32_t nmask, uint32_t B, uint32_t logB, uint32_t H,
+                         const uint64_t* ladder, uint32_t sigma, uint32_t b, const double* wtab, double thr,
+                         double iso_tol, double gmin, double ref_lo, double ref_hi, double ref_tol) {
+    fill_ctx_index(d, n, nmask, B, logB, H, ladder, sigma, b);
     d.wtab = wtab;
+    d.winv = nullptr;
     d.thr = thr;
     d.iso_tol = iso_tol;
     d.gmin = gmin;
@@ -133,13 +147,34 @@ __device__ void fill_ctx(DecodeCtx& d, uint64_t n, uint32_t nmask, uint32_t B, u
     d.ref_lo_f = (float)(ref_lo * thr);
     d.ref_hi_f = (float)(ref_hi * thr);
     d.ref_tol_f = (float)ref_tol;
-    d.inv_n_f = __int_as_float((127 - (int)ilog2_u32(d.n)) << 23);  // 2^-log2 n, exact
+}
+
+// decode context of a round of the transform: the round block carries the FP32 thresholds (rounded
+// on the host, so that no FP64 conversion runs here) and the table of 1 / W(o)
+__device__ void fill_ctx_round(DecodeCtx& d, const ExactArgs& a, uint32_t sigma, uint32_t b) {
+    uint64_t ladder[kMaxHash];
+    for (int l = 0; l < kMaxHash; ++l) ladder[l] = l + 1 < kMaxHash ? a.shift64[l + 1] : 0;
+    fill_ctx_index(d, a.n, a.nmask, a.B, a.logB, a.H, ladder, sigma, b);
+    d.wtab = a.wtab;
+    d.winv = a.winv;
+    d.thr = a.thr;
+    d.iso_tol = a.iso_tol;
+    d.gmin = a.gmin;
+    d.ref_lo = a.ref_lo;
+    d.ref_hi = a.ref_hi;
+    d.ref_tol = a.ref_tol;
+    d.thr_f = a.thr_f;
+    d.iso_tol_f = a.iso_tol_f;
+    d.ref_lo_f = a.ref_lo_f;
+    d.ref_hi_f = a.ref_hi_f;
+    d.ref_tol_f = a.ref_tol_f;
 }
 
 // Decode of one bin (NoiselessSparseFFTInner's loop body).  u[0..H) are the bin's hashings after the
 // subtraction of zhat, in the precision R of the data path.  Returns 0 (nothing), 1 (a decode of J
 // kept) or 2 (a re-estimate of a known entry), with the index in *oi and the window gain that divides
-// u_0 in *gain (the caller forms the FP64 value).  *above is set when |u_0| > thr.  The zhat entries
+// u_0 in *gain (the caller forms the FP64 value; for a decode of the FP32 path *ginv is 1 / gain from
+// the table beside W, else 0, and the caller divides).  *above is set when |u_0| > thr.  The zhat entries
 // hashed to bin j are list[0..nbin) (entry ids), with indices ent_idx[] and window gains ent_gain[].
 //
 // The FP64 data path decides in FP64.  The FP32 path takes every decision (magnitudes, phases, the
@@ -149,8 +184,9 @@ __device__ void fill_ctx(DecodeCtx& d, uint64_t n, uint32_t nmask, uint32_t B, u
 // measure-zero band at the thresholds.
 __device__ int decode_bin_fp64(const DecodeCtx& d, uint32_t j, const double2* u, const uint32_t* list, uint32_t nbin,
                                const uint32_t* ent_idx, const double* ent_gain, uint32_t* oi, double* gout,
-                               bool* above) {
+                               double* ginv, bool* above) {
     const double mag0 = cmag<double>(u[0]);
+    *ginv = 0.0;  // the FP64 path divides
     const uint32_t L = d.H - 1;
     *above = false;
     if (!(mag0 > d.thr)) {
@@ -232,8 +268,9 @@ __device__ __forceinline__ float pow2_f(int e) { return __int_as_float((127 + e)
 // phases stay in registers.
 __device__ __forceinline__ int decode_bin_fp32(const DecodeCtx& d, uint32_t j, const float2* u, const uint32_t* list,
                                                uint32_t nbin, const uint32_t* ent_idx, const double* ent_gain,
-                                               uint32_t* oi, double* gout, bool* above) {
+                                               uint32_t* oi, double* gout, double* ginv, bool* above) {
     const float mag0 = hypotf(u[0].x, u[0].y);
+    *ginv = 0.0;
     const uint32_t L = d.H - 1;
     *above = false;
     if (!(mag0 > d.thr_f)) {
@@ -311,22 +348,25 @@ __device__ __forceinline__ int decode_bin_fp32(const DecodeCtx& d, uint32_t j, c
 #pragma unroll
     for (int l = 0; l < kMaxHash - 1; ++l)
         if ((uint32_t)l < L && fabsf(hypotf(u[l + 1].x, u[l + 1].y) - mag0) > d.iso_tol_f * mag0) return 0;
-    const double gain = d.wtab[o < 0 ? -o : o];
+    const uint32_t oa = (uint32_t)(o < 0 ? -o : o);
+    const double gain = d.wtab[oa];
+    const double gi = d.winv ? d.winv[oa] : 0.0;  // loaded beside the gain: one memory latency for both
     if (!(gain >= d.gmin)) return 0;
     *oi = i;
     *gout = gain;
+    *ginv = gi;
     return 1;
 }
 
 __device__ __forceinline__ int decode_bin(const DecodeCtx& d, uint32_t j, const double2* u, const uint32_t* list,
                                           uint32_t nbin, const uint32_t* ent_idx, const double* ent_gain, uint32_t* oi,
-                                          double* gout, bool* above) {
-    return decode_bin_fp64(d, j, u, list, nbin, ent_idx, ent_gain, oi, gout, above);
+                                          double* gout, double* ginv, bool* above) {
+    return decode_bin_fp64(d, j, u, list, nbin, ent_idx, ent_gain, oi, gout, ginv, above);
 }
 __device__ __forceinline__ int decode_bin(const DecodeCtx& d, uint32_t j, const float2* u, const uint32_t* list,
                                           uint32_t nbin, const uint32_t* ent_idx, const double* ent_gain, uint32_t* oi,
-                                          double* gout, bool* above) {
-    return decode_bin_fp32(d, j, u, list, nbin, ent_idx, ent_gain, oi, gout, above);
+                                          double* gout, double* ginv, bool* above) {
+    return decode_bin_fp32(d, j, u, list, nbin, ent_idx, ent_gain, oi, gout, ginv, above);
 }
 
 // Bin j's hashings after the subtraction of zhat, for the decisions: u_h = U_h - sum over the bin's
@@ -361,16 +401,17 @@ __device__ __forceinline__ void subtracted_bin(const float2* U, uint32_t B, uint
             }
     }
 }
-// u_0 of bin j after the subtraction, in FP64 (the first row of subtracted_bin, same order)
+// u_0 of bin j after the subtraction, in FP64 (the first row of subtracted_bin, same order); entry e's
+// FP64 term of hashing 0 is sub[e * stride]
 template <typename C>
-__device__ __forceinline__ double2 subtracted_u0(const C* U, uint32_t H, uint32_t j, const uint32_t* list,
+__device__ __forceinline__ double2 subtracted_u0(const C* U, uint32_t stride, uint32_t j, const uint32_t* list,
                                                  uint32_t nbin, const double2* sub) {
     const C v = U[j];
     double2 w = make_double2((double)v.x, (double)v.y);
     for (uint32_t x = 0; x < nbin; ++x) {
         const uint32_t e = list[x];
-        w.x -= sub[e * H].x;
-        w.y -= sub[e * H].y;
+        w.x -= sub[e * stride].x;
+        w.y -= sub[e * stride].y;
     }
     return w;
 }
@@ -523,8 +564,9 @@ __device__ void sum_partials(const C* part, uint32_t chunks, uint32_t H, uint32_
 enum FinPart { kFinBins = 1, kFinDecode = 2, kFinAll = 3 };
 
 template <typename R>
-__device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uint32_t b, unsigned char* smem,
-                             int part = kFinAll, bool carry = false) {
+__device__ bool finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uint32_t b, unsigned char* smem,
+                             int part = kFinAll, bool carry = false, bool bins_here = false,
+                             const uint32_t* next_ctr = nullptr) {
     using C = typename Cx<R>::T;
     const uint32_t tid = threadIdx.x;
     const uint32_t B = a.B, H = a.H;
@@ -558,11 +600,23 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         block_fft_rows<R>(U, H, a.logB);  // starts and ends with a barrier
         if (!(part & kFinDecode)) {  // every partial fold has been read: the area takes the bins
             for (uint32_t i = tid; i < H * B; i += kThreads) area[i] = U[i];
-            return;
+            return false;
         }
-    } else {
-        for (uint32_t i = tid; i < H * B; i += kThreads) U[i] = __ldcg(area + i);
     }
+    // The round's bins, when another CTA formed them (bins_here: this CTA did, just before, in place),
+    // read through L2 only: each thread's first four are loaded here and stored after the entries'
+    // window gains below have been requested, so that both wait out one memory latency.  The last
+    // thread reads the next round's second counter (next_ctr) with an acquire load alongside: if that
+    // round's bins have arrived, the caller goes on to its decode without an arrival (next_ready).
+    __shared__ uint32_t s_next_ready;
+    const bool load_U = !(part & kFinBins) && !bins_here;
+    C uv[4];
+    if (load_U) {
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q)
+            if (tid + q * kThreads < H * B) uv[q] = __ldcg(area + tid + q * kThreads);
+    }
+    if (tid == kThreads - 1 && next_ctr != nullptr) s_next_ready = acquire_is(next_ctr, 1u) ? 1u : 0u;
 
     // zhat of this request and its per-entry subtraction terms
     // zhat is read through L2 only: in the one-launch path another CTA of this launch wrote it
@@ -589,45 +643,95 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
     // the decode context is the same for every thread: one copy in shared memory (registers would
     // hold it only by spilling it to local memory)
     __shared__ DecodeCtx d;
-    if (tid == 0) {
-        uint64_t ladder[kMaxHash];
-        for (int l = 0; l < kMaxHash; ++l) ladder[l] = l + 1 < kMaxHash ? a.shift64[l + 1] : 0;
-        fill_ctx(d, a.n, a.nmask, B, a.logB, H, ladder, sigma, b, a.wtab, a.thr, a.iso_tol, a.gmin, a.ref_lo,
-                 a.ref_hi, a.ref_tol);
-    }
-    __syncthreads();
+    if (tid == kThreads - 2) fill_ctx_round(d, a, sigma, b);
+    // (the entries need no part of d: their window gains are read while it is filled, by a thread that
+    // holds no entry unless zhat has more than kThreads - 2)
+    const uint32_t Np = (uint32_t)(a.n >> a.logB), logNp = ilog2_u32(Np);
+    // The FP32 data path keeps FP64 work (issued at a small fraction of the FP32 rate) to the values:
+    // entry e's FP64 term of hashing 0 goes to ent_sub[e] and its gain-scaled value, rounded to FP32,
+    // to ent_gz[e] (behind the first zcap entries of ent_sub; H >= 2 outside single-hashing mode); the
+    // terms of the decisions are formed in FP32 from there.  The FP64 path forms every term in FP64.
+    constexpr bool f32 = sizeof(C) == sizeof(float2);
+    float2* ent_gz = reinterpret_cast<float2*>(ent_sub + a.zcap);
+    const uint32_t a0 = a.a_base + a.a[0];
     for (uint32_t e = tid; e < nz; e += kThreads) {
         const uint32_t i = e == tid ? zi0 : (use_carry ? c_idx[e] : __ldcg(a.zidx + (size_t)s * a.zcap + e));
+        const double2 v = e == tid ? zv0 : (use_carry ? c_val[e] : __ldcg(a.zval + (size_t)s * a.zcap + e));
         ent_idx[e] = i;
-        ent_val[e] = e == tid ? zv0 : (use_carry ? c_val[e] : __ldcg(a.zval + (size_t)s * a.zcap + e));
+        ent_val[e] = v;
         uint32_t jb;
-        const int32_t o = offset_of((sigma * (i - b)) & a.nmask, d, &jb);
+        const int32_t o = offset_of((sigma * (i - b)) & a.nmask, Np, logNp, a.nmask, &jb);
         ent_bin[e] = jb;
-        ent_gain[e] = a.wtab[o < 0 ? -o : o];
+        const double gain = a.wtab[o < 0 ? -o : o];
+        ent_gain[e] = gain;
+        if (f32) {
+            const double2 gz = make_double2(gain * v.x, gain * v.y);
+            double2 t0 = gz;  // hashing 0 has offset 0 in the transform's rounds: w^0 = 1
+            const uint32_t e0 = (a0 * sigma * i) & a.nmask;
+            if (e0 != 0) {
+                const double2 w = root_pow<R>(e0, a.nmask);
+                t0 = make_double2(gz.x * w.x - gz.y * w.y, gz.x * w.y + gz.y * w.x);
+            }
+            ent_sub[e] = t0;
+            if (!a.bins_only) ent_gz[e] = make_float2((float)gz.x, (float)gz.y);
+        }
+    }
+    if (load_U) {
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q)
+            if (tid + q * kThreads < H * B) U[tid + q * kThreads] = uv[q];
+        for (uint32_t i0 = tid + 4 * kThreads; i0 < H * B; i0 += 4 * kThreads) {  // B > kThreads
+            C v[4];
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q)
+                if (i0 + q * kThreads < H * B) v[q] = __ldcg(area + i0 + q * kThreads);
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q)
+                if (i0 + q * kThreads < H * B) U[i0 + q * kThreads] = v[q];
+        }
     }
     if (tid == 0) {
         s_nw = 0;
         s_above = 0;
         s_kept = 0;
     }
-    __syncthreads();
-    // step 4 terms: W(-o(i)) zhat_i w^{a_h sigma i} for every (entry, hashing)
-    for (uint32_t q = tid; q < nz * H; q += kThreads) {
-        const uint32_t e = q / H, h = q - e * H;
-        const uint32_t i = ent_idx[e];
-        const double2 w = root_pow<R>(((a.a_base + a.a[h]) * sigma * i) & a.nmask, a.nmask);
-        const double2 gz = make_double2(ent_gain[e] * ent_val[e].x, ent_gain[e] * ent_val[e].y);
-        const double2 t = make_double2(gz.x * w.x - gz.y * w.y, gz.x * w.y + gz.y * w.x);
-        ent_sub[q] = t;
-        ent_sub_f[q] = make_float2((float)t.x, (float)t.y);
+    __syncthreads();  // d, the entries and the counts
+    // read here, before thread 0 can reach the next round's write
+    const bool next_ready = next_ctr != nullptr && s_next_ready != 0;
+    // step 4 terms: W(-o(i)) zhat_i w^{a_h sigma i} for every (entry, hashing).  No barrier after this
+    // loop: bucket_entries starts with one before anything reads the terms.
+    if (f32) {
+        if (!a.bins_only) {
+            const float two_over_n = 2.0f * d.inv_n_f;  // exact: n is a power of two
+            for (uint32_t q = tid; q < nz * H; q += kThreads) {
+                const uint32_t e = q / H, h = q - e * H;
+                const uint32_t ex = ((a.a_base + a.a[h]) * sigma * ent_idx[e]) & a.nmask;
+                const int32_t es = ex > (a.nmask >> 1) ? (int32_t)((int64_t)ex - (int64_t)a.n) : (int32_t)ex;
+                float sn, cs;
+                sincospif((float)es * two_over_n, &sn, &cs);
+                const float2 g = ent_gz[e];  // times w = (cs, -sn)
+                ent_sub_f[q] = make_float2(g.x * cs + g.y * sn, g.y * cs - g.x * sn);
+            }
+        }
+    } else {
+        for (uint32_t q = tid; q < nz * H; q += kThreads) {
+            const uint32_t e = q / H, h = q - e * H;
+            const uint32_t i = ent_idx[e];
+            const double2 w = root_pow<R>(((a.a_base + a.a[h]) * sigma * i) & a.nmask, a.nmask);
+            const double2 gz = make_double2(ent_gain[e] * ent_val[e].x, ent_gain[e] * ent_val[e].y);
+            const double2 t = make_double2(gz.x * w.x - gz.y * w.y, gz.x * w.y + gz.y * w.x);
+            ent_sub[q] = t;
+            ent_sub_f[q] = make_float2((float)t.x, (float)t.y);
+        }
     }
-    __syncthreads();
+    const uint32_t sub_stride = f32 ? 1u : H;  // where subtracted_u0 finds hashing 0's FP64 terms
     bucket_entries(ent_bin, nz, B, bin_cnt, bin_start, bin_list, scan);
 
     if (a.bins_only) {  // single-hashing mode: the subtracted bins u_0 in FP64, no decode
         for (uint32_t j = tid; j < B; j += kThreads)
-            a.ubins[j] = subtracted_u0(U, H, j, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_sub);
-        return;
+            a.ubins[j] =
+                subtracted_u0(U, sub_stride, j, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_sub);
+        return false;
     }
     // step 4 and the decode, one bin per thread: decisions in the data path's precision
     for (uint32_t j = tid; j < B; j += kThreads) {
@@ -636,9 +740,9 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
         const uint32_t nbin = bin_start[j + 1] - bin_start[j];
         subtracted_bin(U, B, H, j, list, nbin, ent_sub, ent_sub_f, u);
         uint32_t oi = 0;
-        double gain = 1.0;
+        double gain = 1.0, ginv = 0.0;
         bool above;
-        const int kind = decode_bin(d, j, u, list, nbin, ent_idx, ent_gain, &oi, &gain, &above);
+        const int kind = decode_bin(d, j, u, list, nbin, ent_idx, ent_gain, &oi, &gain, &ginv, &above);
         // counts and candidate slots, one shared-memory atomic per warp and counter
         const unsigned m = __activemask();
         const unsigned ma = __ballot_sync(m, above), mk = __ballot_sync(m, kind == 1), mw = __ballot_sync(m, kind != 0);
@@ -655,9 +759,13 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
             cand_idx[slot] = oi;
             cand_bin[slot] = j;
             cand_gain[slot] = gain;
-            // its value: u_0 (step 4 in FP64) / W(-o)
-            const double2 u0 = subtracted_u0(U, H, j, list, nbin, ent_sub);
-            cand_val[slot] = make_double2(u0.x / gain, u0.y / gain);
+            // its value: u_0 (step 4 in FP64) / W(-o), as a product with 1 / W(-o) from the table where
+            // the decode read one (FP32 path), else as a quotient
+            const double2 u0 = subtracted_u0(U, sub_stride, j, list, nbin, ent_sub);
+            if (f32 && kind == 1 && d.winv)
+                cand_val[slot] = make_double2(u0.x * ginv, u0.y * ginv);
+            else
+                cand_val[slot] = make_double2(u0.x / gain, u0.y / gain);
         }
     }
     __syncthreads();
@@ -688,24 +796,44 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
                 a.out_flag[s] = flag;
             }
         }
-        return;
+        return next_ready;
     }
     // merge what into zhat (NoiselessSparseFFT: zhat <- zhat + what), zhat first on equal indices,
     // then drop entries below prune * thr
     const uint32_t tot = nz + nw;
-    rank_sort(cand_idx, cand_val, nw, srt_idx, srt_val);
-    for (uint32_t e = tid; e < nz; e += kThreads) {
-        const uint32_t pos = e + lower_bound_u32(srt_idx, nw, ent_idx[e]);
-        out_idx[pos] = ent_idx[e];
-        out_val[pos] = ent_val[e];
-    }
-    for (uint32_t c = tid; c < nw; c += kThreads) {
-        const uint32_t pos = c + upper_bound_u32(ent_idx, nz, srt_idx[c]);
-        out_idx[pos] = srt_idx[c];
-        out_val[pos] = srt_val[c];
+    if (nw <= (uint32_t)kThreads) {
+        // positions by counting (the candidates' indices are distinct): zhat entry e goes to e + the
+        // number of candidates below its index, candidate c to the number of candidates below its
+        // index + the number of zhat entries at or below it
+        for (uint32_t e = tid; e < nz; e += kThreads) {
+            const uint32_t key = ent_idx[e];
+            uint32_t r = 0;
+            for (uint32_t q = 0; q < nw; ++q) r += cand_idx[q] < key ? 1u : 0u;
+            out_idx[e + r] = key;
+            out_val[e + r] = ent_val[e];
+        }
+        if (tid < nw) {
+            const uint32_t key = cand_idx[tid];
+            uint32_t r = 0;
+            for (uint32_t q = 0; q < nw; ++q) r += cand_idx[q] < key ? 1u : 0u;
+            const uint32_t pos = r + upper_bound_u32(ent_idx, nz, key);
+            out_idx[pos] = key;
+            out_val[pos] = cand_val[tid];
+        }
+    } else {  // many candidates: sorted first, then placed by binary searches
+        rank_sort(cand_idx, cand_val, nw, srt_idx, srt_val);
+        for (uint32_t e = tid; e < nz; e += kThreads) {
+            const uint32_t pos = e + lower_bound_u32(srt_idx, nw, ent_idx[e]);
+            out_idx[pos] = ent_idx[e];
+            out_val[pos] = ent_val[e];
+        }
+        for (uint32_t c = tid; c < nw; c += kThreads) {
+            const uint32_t pos = c + upper_bound_u32(ent_idx, nz, srt_idx[c]);
+            out_idx[pos] = srt_idx[c];
+            out_val[pos] = srt_val[c];
+        }
     }
     __syncthreads();
-    const double drop = a.prune * a.thr;
     for (uint32_t p = tid; p < tot; p += kThreads) {
         uint32_t kp = 0;
         const uint32_t idx = out_idx[p];
@@ -716,12 +844,17 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
                 v.y += out_val[p + 1].y;
                 out_val[p] = v;  // the duplicate at p + 1 is never a head and is not written
             }
-            kp = cmag<R>(v) < drop ? 0u : 1u;
+            // |v| < prune thr, in the data path's precision (FP32: against prune thr rounded up)
+            if (f32)
+                kp = hypotf((float)v.x, (float)v.y) < a.drop_f ? 0u : 1u;
+            else
+                kp = cmag<R>(v) < a.prune * a.thr ? 0u : 1u;
         }
         keep[p] = kp;
     }
     __syncthreads();
-    const uint32_t newcount = block_exclusive_scan(keep, tot, scan);
+    const uint32_t newcount =
+        tot <= (uint32_t)kThreads ? block_exclusive_scan_flags(keep, tot, scan) : block_exclusive_scan(keep, tot, scan);
     uint32_t* zi = a.zidx + (size_t)s * a.zcap;
     double2* zv = a.zval + (size_t)s * a.zcap;
     for (uint32_t p = tid; p < tot; p += kThreads) {
@@ -759,6 +892,7 @@ __device__ void finish_round(const ExactArgs& a, uint32_t s, uint32_t sigma, uin
             a.out_flag[s] = flag;
         }
     }
+    return next_ready;
 }
 
 #ifndef SFFT_ROUND_MIN_BLOCKS
@@ -787,22 +921,33 @@ __global__ void __launch_bounds__(kThreads, SFFT_ROUND_MIN_BLOCKS) k_exact_round
 // ------------------------------------------------------------------------------------------------
 // One launch per batch: all rounds' chunks, finishers chained by arrival counters
 // ------------------------------------------------------------------------------------------------
-// Round t's bins of request s are ready: arrive at its second counter; the later of (these bins,
-// round t - 1's decode) runs round t's decode, then arrives at round t + 1's, and so on.  (seed, id)
-// name the request's draws.
+// The decodes of request s from round t on, in this CTA, for as long as the next round's bins have
+// arrived.  Round t > 0's decode is the second of two arrivals at its counter2 (its bins, round t - 1's
+// decode); round 0's needs no zhat and follows its bins here.  Each decode also reads the next round's
+// counter2 (an acquire load that overlaps its own loads): when those bins have arrived, this chain is
+// the last party of that round and goes on without an arrival of its own.  (seed, id) name the
+// request's draws.
 template <typename R, int NR>
 __device__ __forceinline__ void decode_chain(const StepParams<NR>& sp, uint32_t t, const ExactArgs* a, uint32_t s,
                                              uint64_t seed, uint32_t id, uint32_t sigma, uint32_t b,
                                              unsigned char* smem) {
-    if ((t > 0 ? arrive_pair(a->counter2 + s) : arrive(a->counter2 + s, 1u)) == 0) return;
+    if (t > 0 && arrive_pair(a->counter2 + s) == 0) return;
+    bool bins_here = a->fin_scratch == nullptr;  // the bins just formed are in this CTA's shared memory
     for (bool carried = false;; carried = true) {
-        finish_round<R>(*a, s, sigma, b, a->fin_scratch ? a->fin_scratch + (size_t)s * a->fin_stride : smem,
-                        kFinDecode, carried);
-        if (threadIdx.x == 0) a->counter2[s] = 0;  // both arrivals of round t have happened
+        const uint32_t* next_ctr = t + 1 < sp.R ? sp.r[t + 1].counter2 + s : nullptr;
+        const bool next_ready =
+            finish_round<R>(*a, s, sigma, b, a->fin_scratch ? a->fin_scratch + (size_t)s * a->fin_stride : smem,
+                            kFinDecode, carried, bins_here, next_ctr);
+        if (threadIdx.x == 0) a->counter2[s] = 0;  // both arrivals of round t have happened (or none, t = 0)
         if (t + 1 >= sp.R) break;
         a = &sp.r[++t];
-        // zhat of round t is published by the arrival at round t + 1's second counter
-        if (arrive_pair(a->counter2 + s) == 0) break;
+        bins_here = false;
+        // zhat of round t - 1 is published by the arrival at round t's second counter (which also
+        // orders this round's shared-memory writes, the kept zhat among them, before the next reads)
+        if (next_ready)
+            __syncthreads();
+        else if (arrive_pair(a->counter2 + s) == 0)
+            break;
         exact_hash(seed, id, t, a->nmask, &sigma, &b);
     }
 }
@@ -1128,10 +1273,10 @@ __global__ void __launch_bounds__(kThreads) k_exact_decode(const DecodeArgs a) {
             u[h].y = U[h * B + j].y;
         }
         uint32_t oi = 0;
-        double gain = 1.0;
+        double gain = 1.0, ginv;  // this decode divides by the gain (its context has no 1 / W table)
         bool above;
         const int kind = decode_bin(d, j, u, bin_list + bin_start[j], bin_start[j + 1] - bin_start[j], ent_idx,
-                                    ent_gain, &oi, &gain, &above);
+                                    ent_gain, &oi, &gain, &ginv, &above);
         if (above) atomicAdd(&s_above, 1u);
         if (kind == 1) atomicAdd(&s_kept, 1u);
         if (kind != 0) {

@@ -314,13 +314,17 @@ sfft_status build_exact_schedule(sfft_plan_s* pl) {
         if (r.smem > 200 * 1024) return SFFT_ERR_K_RANGE;
         pl->taps_host.resize(taps_off + (size_t)r.T + 1);
         window_taps_host(p.n, r.B, r.alpha, p.delta, r.T, pl->taps_host.data() + taps_off);
-        pl->wtab_host.resize(wtab_off + Np / 2 + 1);
+        pl->wtab_host.resize(wtab_off + 2 * (Np / 2 + 1));
+        double* W = pl->wtab_host.data() + wtab_off;
         if (p.gain == 1)
-            window_gprime_host(p.n, r.B, r.alpha, p.delta, Np / 2 + 1, pl->wtab_host.data() + wtab_off);
+            window_gprime_host(p.n, r.B, r.alpha, p.delta, Np / 2 + 1, W);
         else
-            window_table_host(p.n, pl->taps_host.data() + taps_off, r.T, Np / 2 + 1, pl->wtab_host.data() + wtab_off);
+            window_table_host(p.n, pl->taps_host.data() + taps_off, r.T, Np / 2 + 1, W);
+        // 1 / W(o) beside W: the FP32 data path forms a decoded value as u_0 times this (the decode
+        // reads it only where W(o) >= gmin > 0)
+        for (uint64_t o = 0; o <= Np / 2; ++o) W[Np / 2 + 1 + o] = W[o] != 0.0 ? 1.0 / W[o] : 0.0;
         taps_off += (size_t)r.T + 1;
-        wtab_off += Np / 2 + 1;
+        wtab_off += 2 * (Np / 2 + 1);
         pl->rounds.push_back(r);
     }
     pl->wtab_len = wtab_off;

@@ -43,7 +43,8 @@ struct ExactRound {
     uint32_t ctaps = 0;       // taps per CTA (sfft_params.chunk_taps)
     uint32_t stage = 0;       // samples staged per CTA: ctaps + largest shift
     size_t taps_off = 0;      // offset of this round's taps in the tap arrays
-    size_t wtab_off = 0;      // offset of this round's W(o), o = 0..n/2B, in the W table
+    size_t wtab_off = 0;      // offset of this round's W(o), o = 0..n/2B, in the W table (exact rounds:
+                              // followed by 1 / W(o) for the same o)
     size_t smem = 0;          // dynamic shared memory of the round kernel
     bool fin_global = false;  // the finisher's arrays do not fit on chip: they live in d_fin
     size_t fin_bytes = 0;     // size of the finisher's arrays of one request
@@ -69,6 +70,7 @@ struct ExactArgs {
     const float* taps32;
     const double* taps64;
     const double* wtab;
+    const double* winv;        // 1 / W(o) for the same o (null: the decode divides by W(o))
     void* part;                // partial fold sums: request s owns [s part_stride, (s + 1) part_stride),
                                // laid out [chunks][H][B] complex R (requests may be in different rounds)
     size_t part_stride;
@@ -81,6 +83,9 @@ struct ExactArgs {
     int32_t* zflag;            // [batch] sticky capacity flag
     uint32_t zcap;
     double thr, iso_tol, gmin, prune, ref_lo, ref_hi, ref_tol;
+    // the FP32 data path's thresholds, rounded once on the host: thr, iso_tol, ref_lo thr, ref_hi thr,
+    // ref_tol, and prune thr rounded up (a float magnitude m is below prune thr iff m < drop_f)
+    float thr_f, iso_tol_f, ref_lo_f, ref_hi_f, ref_tol_f, drop_f;
     uint32_t first_round, last_round;
     // outputs written by the last round
     uint32_t* out_idx;
