@@ -968,7 +968,7 @@ static uint64_t region_candidate(uint64_t n, uint64_t Np, uint32_t tp, uint32_t 
  * u / up hold dmax x nrep rows of B bins, row D nrep + q being LocateInner round q of level D + 1
  * (hashings at a_q and a_q + beta_q under the call's sigma, b); beta the matching dmax x nrep shifts.
  * Outputs (each may be NULL): lfp_levels / valid_levels (dmax x B) the regions and bottom flags after
- * every level, cand (B) each bin's candidate (all ones for bottom), as the hashing driver forms them.
+ * every level, cand (B) each bin's candidate (all ones for bottom), as or_locate_signal_ex forms them.
  */
 void or_locate_replay(const or_params* P, uint32_t B, uint64_t sigma, uint64_t b, uint32_t nrep, const uint64_t* beta,
                       const double* u_re_im, const double* up_re_im, int paper, uint64_t* lfp_levels,

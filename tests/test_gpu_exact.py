@@ -5,7 +5,7 @@ floating point within the tolerance the arithmetic allows:
   * FP64 path: 1e-9 relative to the bin scale (double data, double FFT);
   * FP32 path: bins within 2e-5 of the largest bin (complex64 samples, FP32 fold and FFT of a few
     thousand terms: about 2^-24 * sqrt(terms) relative), recovered values within 1e-5 relative to
-    |X| = 1 (the benchmark spec's tolerance).
+    |X| = 1 (the stated tolerance of the FP32 path).
 """
 import numpy as np
 import pytest

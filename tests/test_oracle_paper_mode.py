@@ -191,7 +191,7 @@ def test_locate_min_qstar_and_best_four_on_isolated_tones():
     assert both >= N // 2, both
 
 
-def test_locate_replay_equals_the_hashing_driver():
+def test_locate_replay_equals_locate_signal():
     """The replay entry (the level loop on given bins) on the oracle's own bins gives the same
     candidates as LocateSignal, in both modes."""
     n, k = 1 << 14, 8
