@@ -725,6 +725,8 @@ def context_measurements(sfft, plan, x, cap, stream, args):
                     "what": f"cuFFT C2C forward n=2^22 complex64, batches of {chunk} (torch.fft.fft)"}
     del y
     out["gather_ceilings"] = gather_ceilings(sfft, plan, x, stream)
+    if not args.no_serving:
+        out["serving_headline"] = serving_headline(sfft, plan, x, args, out)
     out["channels"] = channels_measurement(sfft, x, stream, args)
     if not args.no_general:
         out["general_case"] = general_measurement(sfft, stream, args)
@@ -961,6 +963,40 @@ def _serve_stream(srv, sigs, params, seq, rate, seed):
     st1 = srv.stats()
     launches = st1["launches"] - st0["launches"]
     return len(seq) / el, lat, len(seq) / max(1, launches)
+
+
+def serving_headline(sfft, plan, x, args, ctx):
+    """The continuous-batching server at the headline configuration: requests for the resident batch of
+    n = 2^22, k = 64 signals (the bench's own), submitted all at once and as a Poisson stream at half
+    the rate that sustains, beside the same kernels called one request at a time and cuFFT's dense
+    FFTs (from the context, same signals).  A last pass submits every signal once and checks each
+    recovered support against the planted one.  Submission and completion go through the Python
+    binding one request at a time, so the host side bounds the rate."""
+    from paper_1201_2501_gb300 import workloads
+
+    n, batch = x.shape[1], x.shape[0]
+    params = plan.params
+    sup, _ = workloads.exact_sparse_batch_spectra(n, K, [workloads.seed_for(2, i) for i in range(batch)])
+    srv = sfft.Server(max_batch=64, instances=2, max_plans=4)
+    sigs = {(0, i): x[i] for i in range(batch)}
+    _serve_stream(srv, sigs, [params], [(0, i) for i in range(min(batch, 64))], None, 1)  # plan built
+    seq = [(0, r % batch) for r in range(args.serve_headline)]
+    thr_all, lat_all, mb_all = _serve_stream(srv, sigs, [params], seq, None, 2)
+    thr_half, lat_half, mb_half = _serve_stream(srv, sigs, [params], seq, 0.5 * thr_all, 3)
+    tickets = [srv.submit(params, x[i], SEED, id=i) for i in range(batch)]
+    exact = 0
+    for i, t in enumerate(tickets):
+        idx, _, info = srv.wait(t, timeout_s=300)
+        exact += int(info["flag"] == 0 and np.array_equal(np.sort(np.asarray(idx, dtype=np.int64)), sup[i]))
+    srv.close()
+    return {"workload": f"{len(seq)} requests for {batch} resident signals, n=2^22, k=64 (the headline batch and "
+                        "parameters); latency = submission to completion on the host clock",
+            "all_at_once": {"throughput_per_s": thr_all, "p50_us": _pct(lat_all, 0.5), "p99_us": _pct(lat_all, 0.99),
+                            "mean_batch": mb_all},
+            "poisson_half_rate": {"offered_per_s": 0.5 * thr_all, "throughput_per_s": thr_half,
+                                  "p50_us": _pct(lat_half, 0.5), "p99_us": _pct(lat_half, 0.99), "mean_batch": mb_half},
+            "support_exact_fraction": exact / batch,
+            "plain_gpu_sfft_per_s": ctx["plain_gpu_sfft"]["value"], "cufft_per_s": ctx["cufft"]["value"]}
 
 
 def _pct(v, q):
@@ -1287,6 +1323,7 @@ def main():
     ap.add_argument("--precision-batch", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-serial", type=int, default=400)
+    ap.add_argument("--serve-headline", type=int, default=4096, help="requests of the headline serving stream")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
