@@ -970,19 +970,35 @@ def serving_headline(sfft, plan, x, args, ctx):
     n = 2^22, k = 64 signals (the bench's own), submitted all at once and as a Poisson stream at half
     the rate that sustains, beside the same kernels called one request at a time and cuFFT's dense
     FFTs (from the context, same signals).  A last pass submits every signal once and checks each
-    recovered support against the planted one.  Submission and completion go through the Python
-    binding one request at a time, so the host side bounds the rate."""
+    recovered support against the planted one.  Those streams go through the Python binding one
+    request at a time, so the host side bounds their rate; a longer stream through the bulk calls
+    (sfft_submit_many / sfft_wait_many) shows what the server itself sustains."""
     from paper_1201_2501_gb300 import workloads
 
     n, batch = x.shape[1], x.shape[0]
     params = plan.params
     sup, _ = workloads.exact_sparse_batch_spectra(n, K, [workloads.seed_for(2, i) for i in range(batch)])
-    srv = sfft.Server(max_batch=64, instances=2, max_plans=4)
+    srv = sfft.Server(max_batch=batch, instances=2, max_plans=4)
     sigs = {(0, i): x[i] for i in range(batch)}
     _serve_stream(srv, sigs, [params], [(0, i) for i in range(min(batch, 64))], None, 1)  # plan built
     seq = [(0, r % batch) for r in range(args.serve_headline)]
     thr_all, lat_all, mb_all = _serve_stream(srv, sigs, [params], seq, None, 2)
     thr_half, lat_half, mb_half = _serve_stream(srv, sigs, [params], seq, 0.5 * thr_all, 3)
+    # a longer stream through the bulk calls: chunks of `batch` requests queued by sfft_submit_many as
+    # they are formed, then collected by sfft_wait_many, so the host's per-request cost is out of the way
+    nb = 4 * args.serve_headline
+    st0 = srv.stats()
+    t0 = time.perf_counter()
+    chunks = []
+    for c0 in range(0, nb, batch):
+        m = min(batch, nb - c0)
+        chunks.append(srv.submit_many(params, [x[(c0 + r) % batch] for r in range(m)], SEED, list(range(c0, c0 + m))))
+    lat_bulk = []
+    for tk in chunks:
+        lat_bulk += [info["latency_us"] for _, _, info in srv.wait_many(tk, timeout_s=300)]
+    el_bulk = time.perf_counter() - t0
+    st1 = srv.stats()
+    mb_bulk = (st1["submitted"] - st0["submitted"]) / max(1, st1["launches"] - st0["launches"])
     tickets = [srv.submit(params, x[i], SEED, id=i) for i in range(batch)]
     exact = 0
     for i, t in enumerate(tickets):
@@ -995,6 +1011,9 @@ def serving_headline(sfft, plan, x, args, ctx):
                             "mean_batch": mb_all},
             "poisson_half_rate": {"offered_per_s": 0.5 * thr_all, "throughput_per_s": thr_half,
                                   "p50_us": _pct(lat_half, 0.5), "p99_us": _pct(lat_half, 0.99), "mean_batch": mb_half},
+            "bulk": {"requests": nb, "throughput_per_s": nb / el_bulk, "p50_us": _pct(lat_bulk, 0.5),
+                     "p99_us": _pct(lat_bulk, 0.99), "mean_batch": mb_bulk,
+                     "what": f"chunks of {batch} requests through sfft_submit_many, collected by sfft_wait_many"},
             "support_exact_fraction": exact / batch,
             "plain_gpu_sfft_per_s": ctx["plain_gpu_sfft"]["value"], "cufft_per_s": ctx["cufft"]["value"]}
 

@@ -407,6 +407,16 @@ sfft_status sfft_server_destroy(sfft_server s);
  */
 sfft_status sfft_submit(sfft_server s, const sfft_params* p, const sfft_job* job, uint64_t* ticket);
 
+/*
+ * Queue count jobs of one parameter set at once: the same as count calls of sfft_submit in order,
+ * under one lock and with one wake-up of the dispatcher (a caller with many requests at hand pays the
+ * submission once).  tickets (count entries, caller-owned) receives job i's ticket in tickets[i].
+ * Every job is checked before any is queued: on an error status nothing was queued.  Errors: those
+ * of sfft_submit; INVALID_ARG also for count == 0 or null arrays.
+ */
+sfft_status sfft_submit_many(sfft_server s, const sfft_params* p, const sfft_job* jobs, uint32_t count,
+                             uint64_t* tickets);
+
 /* OK: done (results written); BUSY: not done yet; INVALID_ARG: unknown ticket; another status: the
  * job failed (e.g. CUDA, OOM at plan creation). */
 sfft_status sfft_poll(sfft_server s, uint64_t ticket);
@@ -417,6 +427,16 @@ sfft_status sfft_poll(sfft_server s, uint64_t ticket);
  * released).  INVALID_ARG: unknown ticket.
  */
 sfft_status sfft_wait(sfft_server s, uint64_t ticket, uint64_t timeout_us, sfft_job_result* res);
+
+/*
+ * Wait for count jobs, timeout_us in total.  status[i] (count entries, caller-owned) receives what
+ * sfft_wait would return for tickets[i], and res[i] (if res is not NULL) describes job i when that is
+ * OK; jobs that completed are released, pending ones (TIMEOUT) are kept.  Returns the first failing
+ * status in ticket order if a job failed (INVALID_ARG for an unknown ticket), else TIMEOUT if one is
+ * still pending, else OK.  INVALID_ARG with status untouched: null arrays or count == 0.
+ */
+sfft_status sfft_wait_many(sfft_server s, const uint64_t* tickets, uint32_t count, uint64_t timeout_us,
+                           sfft_job_result* res, int32_t* status);
 
 /* Counters and latency percentiles since creation. */
 sfft_status sfft_server_stats_get(sfft_server s, sfft_server_stats* st);

@@ -753,38 +753,77 @@ sfft_status sfft_server_destroy(sfft_server S) {
     return SFFT_OK;
 }
 
-sfft_status sfft_submit(sfft_server S, const sfft_params* p, const sfft_job* job, uint64_t* ticket) {
-    if (!S || !p || !job || !ticket) return SFFT_ERR_INVALID_ARG;
-    if (!job->x || !job->h_idx || !job->h_val || job->cap == 0) return SFFT_ERR_INVALID_ARG;
-    const sfft_status v = validate_params(p);
-    if (v != SFFT_OK) return v;
+// A checked job of validated params p, ready to queue (nullptr and *st set on an error)
+static Job* make_job(const sfft_server_s* S, const sfft_params* p, const sfft_job* job, sfft_status* st) {
+    *st = SFFT_ERR_INVALID_ARG;
+    if (!job->x || !job->h_idx || !job->h_val || job->cap == 0) return nullptr;
     const size_t elem = p->precision == SFFT_FP64 ? 16 : 8;
-    if (job->x_on_device && ((uintptr_t)job->x % elem) != 0) return SFFT_ERR_INVALID_ARG;
-    if (job->period != 0 && ((job->period & (job->period - 1)) != 0 || job->period > p->n)) return SFFT_ERR_INVALID_ARG;
+    if (job->x_on_device && ((uintptr_t)job->x % elem) != 0) return nullptr;
+    if (job->period != 0 && ((job->period & (job->period - 1)) != 0 || job->period > p->n)) return nullptr;
+    const size_t x_bytes = (size_t)(job->period ? job->period : p->n) * elem;
+    if (!job->x_on_device && x_bytes > S->cfg.mem_budget) {
+        *st = SFFT_ERR_OOM;
+        return nullptr;
+    }
     auto* j = new (std::nothrow) Job();
-    if (!j) return SFFT_ERR_OOM;
+    if (!j) {
+        *st = SFFT_ERR_OOM;
+        return nullptr;
+    }
     j->key = make_key(*p, &j->p);
     j->desc = *job;
-    j->x_bytes = (size_t)(job->period ? job->period : p->n) * elem;
-    if (!job->x_on_device && j->x_bytes > S->cfg.mem_budget) {
-        delete j;
-        return SFFT_ERR_OOM;
-    }
-    j->t_submit = Clock::now();
+    j->x_bytes = x_bytes;
+    *st = SFFT_OK;
+    return j;
+}
+
+// Queue checked jobs in order under one lock, one wake-up (BUSY, nothing queued: the server stops)
+static sfft_status queue_jobs(sfft_server_s* S, Job* const* js, uint32_t count, uint64_t* tickets) {
+    const auto now = Clock::now();
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        if (S->stopping) {
-            delete j;
-            return SFFT_ERR_BUSY;
+        if (S->stopping) return SFFT_ERR_BUSY;
+        for (uint32_t i = 0; i < count; ++i) {
+            Job* j = js[i];
+            j->t_submit = now;
+            j->ticket = S->next_ticket++;
+            S->jobs.emplace(j->ticket, j);
+            S->inbox.push_back(j);
+            ++S->submitted;
+            tickets[i] = j->ticket;
         }
-        j->ticket = S->next_ticket++;
-        S->jobs.emplace(j->ticket, j);
-        S->inbox.push_back(j);
-        ++S->submitted;
-        *ticket = j->ticket;
     }
     S->cv_work.notify_one();
     return SFFT_OK;
+}
+
+sfft_status sfft_submit(sfft_server S, const sfft_params* p, const sfft_job* job, uint64_t* ticket) {
+    if (!S || !p || !job || !ticket) return SFFT_ERR_INVALID_ARG;
+    const sfft_status v = validate_params(p);
+    if (v != SFFT_OK) return v;
+    sfft_status st;
+    Job* j = make_job(S, p, job, &st);
+    if (!j) return st;
+    if ((st = queue_jobs(S, &j, 1, ticket)) != SFFT_OK) delete j;
+    return st;
+}
+
+sfft_status sfft_submit_many(sfft_server S, const sfft_params* p, const sfft_job* jobs, uint32_t count,
+                             uint64_t* tickets) {
+    if (!S || !p || !jobs || !tickets || count == 0) return SFFT_ERR_INVALID_ARG;
+    const sfft_status v = validate_params(p);
+    if (v != SFFT_OK) return v;
+    std::vector<Job*> js;
+    js.reserve(count);
+    sfft_status st = SFFT_OK;
+    for (uint32_t i = 0; i < count && st == SFFT_OK; ++i) {
+        Job* j = make_job(S, p, jobs + i, &st);
+        if (j) js.push_back(j);
+    }
+    if (st == SFFT_OK) st = queue_jobs(S, js.data(), count, tickets);
+    if (st != SFFT_OK)
+        for (Job* j : js) delete j;
+    return st;
 }
 
 sfft_status sfft_poll(sfft_server S, uint64_t ticket) {
@@ -811,6 +850,38 @@ sfft_status sfft_wait(sfft_server S, uint64_t ticket, uint64_t timeout_us, sfft_
     S->jobs.erase(it);
     delete j;
     return st;
+}
+
+sfft_status sfft_wait_many(sfft_server S, const uint64_t* tickets, uint32_t count, uint64_t timeout_us,
+                           sfft_job_result* res, int32_t* status) {
+    if (!S || !tickets || !status || count == 0) return SFFT_ERR_INVALID_ARG;
+    const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us);
+    sfft_status first = SFFT_OK;
+    bool pending = false;
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (uint32_t i = 0; i < count; ++i) {
+        auto it = S->jobs.find(tickets[i]);
+        if (it == S->jobs.end()) {
+            status[i] = SFFT_ERR_INVALID_ARG;
+            if (first == SFFT_OK) first = SFFT_ERR_INVALID_ARG;
+            continue;
+        }
+        Job* j = it->second;
+        auto finished = [&] { return j->state == JobState::Done || j->state == JobState::Failed; };
+        if (!S->cv_done.wait_until(lk, deadline, finished)) {
+            status[i] = SFFT_ERR_TIMEOUT;
+            pending = true;
+            continue;
+        }
+        const sfft_status st = j->state == JobState::Done ? SFFT_OK : j->status;
+        status[i] = st;
+        if (res) res[i] = j->res;
+        if (st != SFFT_OK && first == SFFT_OK) first = st;
+        S->jobs.erase(j->ticket);
+        delete j;
+    }
+    if (first != SFFT_OK) return first;
+    return pending ? SFFT_ERR_TIMEOUT : SFFT_OK;
 }
 
 sfft_status sfft_server_stats_get(sfft_server S, sfft_server_stats* st) {

@@ -174,6 +174,9 @@ _SIGS = {
     "sfft_server_create": (ctypes.c_int, [ctypes.POINTER(SfftServerConfig), ctypes.POINTER(_vp)]),
     "sfft_server_destroy": (ctypes.c_int, [_vp]),
     "sfft_submit": (ctypes.c_int, [_vp, _P, ctypes.POINTER(SfftJob), _u64p]),
+    "sfft_submit_many": (ctypes.c_int, [_vp, _P, ctypes.POINTER(SfftJob), _u32, _u64p]),
+    "sfft_wait_many": (ctypes.c_int, [_vp, _u64p, _u32, _u64, ctypes.POINTER(SfftJobResult),
+                                      ctypes.POINTER(ctypes.c_int32)]),
     "sfft_poll": (ctypes.c_int, [_vp, _u64]),
     "sfft_wait": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(SfftJobResult)]),
     "sfft_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(SfftServerStats)]),
@@ -538,6 +541,59 @@ class Server:
         with self._mu:
             self._live[t.value] = (x, idx, val)
         return t.value
+
+    def submit_many(self, params: SfftParams, xs, seed: int, ids, cap: int = 0) -> list:
+        """sfft_submit_many: one job per signal of ``xs`` (device tensors, read in place), request
+        indices ``ids``; returns the tickets in order."""
+        import numpy as np
+
+        cap = cap or params.z_cap
+        xs, ids = list(xs), list(ids)
+        if not xs or len(xs) != len(ids):
+            raise SfftError(SFFT_ERR_INVALID_ARG, "submit_many: one request index per signal")
+        if not all(getattr(x, "is_cuda", False) and x.is_contiguous() for x in xs):
+            raise SfftError(SFFT_ERR_INVALID_ARG, "submit_many: contiguous device signals")
+        m = len(xs)
+        idx = np.empty((m, cap), dtype=np.uint32)
+        val = np.empty((m, cap, 2), dtype=np.float64)
+        jobs = (SfftJob * m)()
+        for r, (x, i) in enumerate(zip(xs, ids)):
+            jobs[r] = SfftJob(_ptr(x), 1, int(i), seed, idx[r].ctypes.data, val[r].ctypes.data, cap, 0)
+        t = (ctypes.c_uint64 * m)()
+        _check(lib().sfft_submit_many(self.handle, ctypes.byref(params), jobs, m, t), "sfft_submit_many")
+        tickets = [int(v) for v in t]
+        with self._mu:
+            for r, tk in enumerate(tickets):
+                self._live[tk] = (xs[r], idx[r], val[r])
+        return tickets
+
+    def wait_many(self, tickets, timeout_s: float = 60.0) -> list:
+        """sfft_wait_many: [(indices, values, result dict)] in ticket order; raises TimeoutError if a
+        job is still pending (its ticket stays valid) and SfftError if one failed."""
+        import numpy as np
+
+        tickets = list(tickets)
+        m = len(tickets)
+        t = (ctypes.c_uint64 * m)(*tickets)
+        res = (SfftJobResult * m)()
+        status = (ctypes.c_int32 * m)()
+        st = lib().sfft_wait_many(self.handle, t, m, int(timeout_s * 1e6), res, status)
+        out = []
+        with self._mu:
+            for r, tk in enumerate(tickets):
+                if status[r] == SFFT_ERR_TIMEOUT:
+                    continue
+                x, idx, val = self._live.pop(tk, (None, None, None))
+                if status[r] != SFFT_OK or idx is None:
+                    continue
+                c = res[r].count
+                out.append((idx[:c].astype(np.int64), val[:c, 0] + 1j * val[:c, 1],
+                            {"count": c, "flag": res[r].flag, "queued_us": res[r].queued_us,
+                             "latency_us": res[r].latency_us}))
+        if st == SFFT_ERR_TIMEOUT:
+            raise TimeoutError(f"sfft_wait_many: jobs still pending after {timeout_s} s")
+        _check(st, "sfft_wait_many")
+        return out
 
     def poll(self, ticket: int) -> int:
         return lib().sfft_poll(self.handle, ticket)

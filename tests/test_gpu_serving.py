@@ -177,3 +177,32 @@ def test_server_admits_by_device_memory(sf):
         assert np.array_equal(idx, s.support)
         assert np.max(np.abs(val - s.values)) < 1e-5
         assert info["flag"] == 0
+
+
+def test_submit_many_equals_submit(sf):
+    """sfft_submit_many / sfft_wait_many: a whole array of jobs queued in one call gives, job by job,
+    bit for bit the results of the same jobs submitted and waited for one at a time, in ticket order;
+    the planted supports are recovered; an unknown ticket and an empty array are argument errors."""
+    n, k, m = 1 << 16, 16, 40
+    p = gpu_params(sf, exact_fields(n, k))
+    seeds = [workloads.seed_for(7, i) for i in range(m)]
+    x, sup, _ = workloads.exact_sparse_batch_device(n, k, seeds, "cuda")
+    xs = [x[i] for i in range(m)]
+    srv = sf.Server(max_batch=16, instances=2)
+    try:
+        one = [srv.wait(srv.submit(p, xs[i], SEED, id=i), timeout_s=120) for i in range(m)]
+        tickets = srv.submit_many(p, xs, SEED, list(range(m)))
+        assert len(tickets) == m and len(set(tickets)) == m
+        many = srv.wait_many(tickets, timeout_s=120)
+        assert len(many) == m
+        for i in range(m):
+            assert np.array_equal(many[i][0], one[i][0]) and np.array_equal(many[i][1], one[i][1])
+            assert many[i][2]["flag"] == one[i][2]["flag"] == 0
+            assert np.array_equal(np.sort(many[i][0]), sup[i])
+        # a ticket already released, and an empty array, are rejected
+        with pytest.raises(sf.SfftError):
+            srv.wait_many([tickets[0]], timeout_s=1)
+        with pytest.raises(sf.SfftError):
+            srv.submit_many(p, [], SEED, [])
+    finally:
+        srv.close()
