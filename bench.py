@@ -995,7 +995,7 @@ def serving_headline(sfft, plan, x, args, ctx):
         chunks.append(srv.submit_many(params, [x[(c0 + r) % batch] for r in range(m)], SEED, list(range(c0, c0 + m))))
     lat_bulk = []
     for tk in chunks:
-        lat_bulk += [info["latency_us"] for _, _, info in srv.wait_many(tk, timeout_s=300)]
+        lat_bulk += srv.wait_many(tk, timeout_s=300, arrays=True)["latency_us"].tolist()
     el_bulk = time.perf_counter() - t0
     st1 = srv.stats()
     mb_bulk = (st1["submitted"] - st0["submitted"]) / max(1, st1["launches"] - st0["launches"])

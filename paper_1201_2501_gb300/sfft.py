@@ -556,20 +556,33 @@ class Server:
         m = len(xs)
         idx = np.empty((m, cap), dtype=np.uint32)
         val = np.empty((m, cap, 2), dtype=np.float64)
-        jobs = (SfftJob * m)()
-        for r, (x, i) in enumerate(zip(xs, ids)):
-            jobs[r] = SfftJob(_ptr(x), 1, int(i), seed, idx[r].ctypes.data, val[r].ctypes.data, cap, 0)
+        # the job array built as one structured array (the layout of sfft_job), not m ctypes objects
+        jobs = np.zeros(m, dtype=np.dtype({"names": [f for f, _ in SfftJob._fields_],
+                                           "formats": [np.uint64, np.uint32, np.uint32, np.uint64, np.uint64,
+                                                       np.uint64, np.uint32, np.uint32],
+                                           "offsets": [getattr(SfftJob, f).offset for f, _ in SfftJob._fields_],
+                                           "itemsize": ctypes.sizeof(SfftJob)}))
+        jobs["x"] = [x.data_ptr() for x in xs]
+        jobs["x_on_device"] = 1
+        jobs["id"] = np.asarray(ids, dtype=np.uint32)
+        jobs["seed"] = seed
+        jobs["h_idx"] = idx.ctypes.data + np.arange(m, dtype=np.uint64) * (cap * 4)
+        jobs["h_val"] = val.ctypes.data + np.arange(m, dtype=np.uint64) * (cap * 16)
+        jobs["cap"] = cap
         t = (ctypes.c_uint64 * m)()
-        _check(lib().sfft_submit_many(self.handle, ctypes.byref(params), jobs, m, t), "sfft_submit_many")
+        _check(lib().sfft_submit_many(self.handle, ctypes.byref(params), jobs.ctypes.data_as(ctypes.POINTER(SfftJob)),
+                                      m, t), "sfft_submit_many")
         tickets = [int(v) for v in t]
         with self._mu:
             for r, tk in enumerate(tickets):
                 self._live[tk] = (xs[r], idx[r], val[r])
         return tickets
 
-    def wait_many(self, tickets, timeout_s: float = 60.0) -> list:
+    def wait_many(self, tickets, timeout_s: float = 60.0, arrays: bool = False):
         """sfft_wait_many: [(indices, values, result dict)] in ticket order; raises TimeoutError if a
-        job is still pending (its ticket stays valid) and SfftError if one failed."""
+        job is still pending (its ticket stays valid) and SfftError if one failed.  arrays=True returns
+        instead one dict of arrays for the whole call: the jobs' output rows "idx" (m x cap uint32) and
+        "val" (m x cap x 2 float64), each valid up to "count", and "count", "flag", "latency_us"."""
         import numpy as np
 
         tickets = list(tickets)
@@ -578,21 +591,28 @@ class Server:
         res = (SfftJobResult * m)()
         status = (ctypes.c_int32 * m)()
         st = lib().sfft_wait_many(self.handle, t, m, int(timeout_s * 1e6), res, status)
-        out = []
+        done = []
         with self._mu:
             for r, tk in enumerate(tickets):
                 if status[r] == SFFT_ERR_TIMEOUT:
                     continue
                 x, idx, val = self._live.pop(tk, (None, None, None))
-                if status[r] != SFFT_OK or idx is None:
-                    continue
-                c = res[r].count
-                out.append((idx[:c].astype(np.int64), val[:c, 0] + 1j * val[:c, 1],
-                            {"count": c, "flag": res[r].flag, "queued_us": res[r].queued_us,
-                             "latency_us": res[r].latency_us}))
+                if status[r] == SFFT_OK and idx is not None:
+                    done.append((r, idx, val))
         if st == SFFT_ERR_TIMEOUT:
             raise TimeoutError(f"sfft_wait_many: jobs still pending after {timeout_s} s")
         _check(st, "sfft_wait_many")
+        if arrays:
+            rb = np.frombuffer(res, dtype=np.dtype([("count", np.uint32), ("flag", np.int32), ("queued_us", np.float64),
+                                                    ("latency_us", np.float64)]), count=m)
+            return {"idx": np.stack([d[1] for d in done]), "val": np.stack([d[2] for d in done]),
+                    "count": rb["count"].copy(), "flag": rb["flag"].copy(), "latency_us": rb["latency_us"].copy()}
+        out = []
+        for r, idx, val in done:
+            c = res[r].count
+            out.append((idx[:c].astype(np.int64), val[:c, 0] + 1j * val[:c, 1],
+                        {"count": c, "flag": res[r].flag, "queued_us": res[r].queued_us,
+                         "latency_us": res[r].latency_us}))
         return out
 
     def poll(self, ticket: int) -> int:
