@@ -842,12 +842,12 @@ sfft_status sfft_wait(sfft_server S, uint64_t ticket, uint64_t timeout_us, sfft_
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->jobs.find(ticket);
     if (it == S->jobs.end()) return SFFT_ERR_INVALID_ARG;
-    Job* j = it->second;
+    Job* j = it->second;  // (the node stays put while the lock is released; an iterator need not)
     auto finished = [&] { return j->state == JobState::Done || j->state == JobState::Failed; };
     if (!S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), finished)) return SFFT_ERR_TIMEOUT;
     const sfft_status st = j->state == JobState::Done ? SFFT_OK : j->status;
     if (res) *res = j->res;
-    S->jobs.erase(it);
+    S->jobs.erase(ticket);  // by key: submissions during the wait may have rehashed the map
     delete j;
     return st;
 }
