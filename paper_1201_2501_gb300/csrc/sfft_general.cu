@@ -523,17 +523,14 @@ __device__ uint32_t sort_unique_u32(uint32_t* key, uint32_t m, uint32_t P, uint3
 // LocateSignal with t threads per bin, thread q owning subregion q: a CTA holds kThreads / t bins of
 // one request (the bins are independent until L is formed).  Per level, the vote arcs of the R_loc
 // rounds are formed once per bin (by threads q < R_loc, in shared memory), every thread counts the
-// votes of its subregion over the rounds, and thread 0 of the bin takes the level's decision from
-// the t counts (the decision of locate_bin_t, on the same integers).  The candidate of bin j
+// votes of its subregion over the rounds, and the bin's t threads take the level's decision from the
+// t counts with warp shuffles (the decision of locate_bin_t, on the same integers).  The candidate of bin j
 // (pi^{-1} of the integer nearest the centre of its last region, or ~0 for bottom) goes to
 // L[s B + j]; EstimateValues sorts and de-duplicates them.
 constexpr int kLocBins = kThreads / 8;  // bins per CTA at the smallest t
 __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
     __shared__ uint64_t s_beta[kMaxRloc];
     __shared__ VoteBounds s_vb[kLocBins][kMaxRloc];
-    __shared__ uint64_t s_l[kLocBins];
-    __shared__ uint32_t s_valid[kLocBins];
-    __shared__ uint32_t s_votes[kThreads];
     const uint32_t s = a.req_base + blockIdx.y, tid = threadIdx.x;
     const uint32_t t = a.t;  // 8, 16 or 32 (the schedule checks it)
     const uint32_t q = tid & (t - 1), lb = tid / t, nb = kThreads / t;
@@ -549,21 +546,22 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
     const uint64_t guard = M >> kPhaseGuardLog;
     const uint64_t sb_fp = ((uint64_t)((sigma * b) & a.nmask)) << kFracBits;
     const double2* rbins = a.bins + (size_t)s * a.bins_stride;
-    if (q == 0) {
-        // the region of bin j starts centred on the bin: [j n/B - n/2B, + n/B)
-        s_l[lb] = ((((uint64_t)j * Np) + n - Np / 2) & (n - 1)) << kFracBits;
-        s_valid[lb] = j < B ? 1u : 0u;
-    }
+    // the bin's region (start l_fp, width w_D) and its bottom flag live in registers, the same in every
+    // lane of the bin's group: the t lanes of a bin share a warp (t divides 32), so the level's
+    // decision is taken with warp shuffles and ballots inside the group
+    uint64_t l_fp = ((((uint64_t)j * Np) + n - Np / 2) & (n - 1)) << kFracBits;  // centred on the bin
+    bool valid = j < B;
+    const uint32_t lane = tid & 31u, gbase = lane & ~(t - 1u);
+    const uint32_t gmask = t == 32u ? 0xFFFFFFFFu : ((1u << t) - 1u) << gbase;
     const double* phase = a.phase + (size_t)s * a.phase_stride;
     for (uint32_t D = 0; D < a.dmax; ++D) {
-        __syncthreads();
+        __syncthreads();  // the previous level's readers of s_beta and s_vb are done
         if (tid < a.R_loc) {
             uint32_t aa;
             uint64_t be;
             inner_a_beta(rq.seed, rq.id, a.round, D * a.R_loc + tid, a.nmask, a.beta_lo[D], a.beta_hi[D], &aa, &be);
             s_beta[tid] = be;
         }
-        const bool valid = s_valid[lb] != 0;
         const double* ph = phase + (size_t)D * a.R_loc * B;
         if (valid)
             for (uint32_t r = q; r < a.R_loc; r += t)
@@ -573,7 +571,6 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
         const uint64_t half_step = w_fp / (2 * (uint64_t)t), step = w_fp / t;
         uint32_t v = 0;
         if (valid) {
-            const uint64_t l_fp = s_l[lb];
             for (uint32_t r = 0; r < a.R_loc; ++r) {
                 // e_q = beta (m_q + sigma b) mod M, m_q = l + (2q - 1) w / 2t
                 const uint64_t e0 = (s_beta[r] * ((l_fp + half_step + sb_fp) & mask)) & mask;
@@ -591,37 +588,30 @@ __global__ void __launch_bounds__(kThreads) k_gen_locate(const GenArgs a) {
                 if (hit) ++v;
             }
         }
-        s_votes[tid] = v;
-        __syncthreads();
-        if (q == 0 && valid) {
-            const uint32_t* vv = s_votes + lb * t;
-            bool any = false;
-            for (uint32_t qq = 0; qq < t; ++qq) any = any || 2u * vv[qq] > a.R_loc;
-            if (!any) {
-                s_valid[lb] = 0;
-            } else {
-                uint32_t best = 0, best_sum = 0;
-                for (uint32_t q0 = 0; q0 + 4 <= t; ++q0) {
-                    const uint32_t sum = vv[q0] + vv[q0 + 1] + vv[q0 + 2] + vv[q0 + 3];
-                    if (q0 == 0 || sum > best_sum) {
-                        best = q0;
-                        best_sum = sum;
-                    }
-                }
-                s_l[lb] = (s_l[lb] + (uint64_t)best * step) & mask;
-            }
+        // the level's decision (every lane of the warp takes part; a group's lanes share `valid`):
+        // Q* nonempty iff some subregion has more than R_loc / 2 votes; then the window of 4
+        // consecutive subregions with the most votes, the first on ties, gives the new region
+        const bool any = (__ballot_sync(0xFFFFFFFFu, 2u * v > a.R_loc) & gmask) != 0u;
+        uint32_t sum = v + __shfl_down_sync(0xFFFFFFFFu, v, 1, (int)t) + __shfl_down_sync(0xFFFFFFFFu, v, 2, (int)t) +
+                       __shfl_down_sync(0xFFFFFFFFu, v, 3, (int)t);
+        uint32_t key = q + 4u <= t ? (sum << 8) | (255u - q) : 0u;  // larger sum, then smaller q
+        for (uint32_t off = t >> 1; off > 0; off >>= 1) key = max(key, __shfl_xor_sync(0xFFFFFFFFu, key, (int)off, (int)t));
+        if (valid) {
+            if (!any)
+                valid = false;
+            else
+                l_fp = (l_fp + (uint64_t)(255u - (key & 255u)) * step) & mask;
         }
         if (q == 0 && j < B && a.dbg_lfp) {  // trace: the region and flag after this level
-            a.dbg_lfp[((size_t)s * a.dmax + D) * B + j] = s_l[lb];
-            a.dbg_valid[((size_t)s * a.dmax + D) * B + j] = (uint8_t)(s_valid[lb] != 0);
+            a.dbg_lfp[((size_t)s * a.dmax + D) * B + j] = l_fp;
+            a.dbg_valid[((size_t)s * a.dmax + D) * B + j] = (uint8_t)(valid ? 1 : 0);
         }
     }
-    __syncthreads();
     if (q != 0 || j >= B) return;
     uint32_t cand = 0xFFFFFFFFu;
-    if (s_valid[lb]) {
+    if (valid) {
         const uint64_t wlast = (Np << kFracBits) >> ((uint64_t)a.dmax * a.logtp);
-        const uint32_t tau = (uint32_t)(((s_l[lb] + wlast / 2 + (1ull << (kFracBits - 1))) >> kFracBits) & (n - 1));
+        const uint32_t tau = (uint32_t)(((l_fp + wlast / 2 + (1ull << (kFracBits - 1))) >> kFracBits) & (n - 1));
         cand = ((inverse_odd(sigma) & a.nmask) * tau + b) & a.nmask;
     }
     a.L[(size_t)s * B + j] = cand;
